@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the tFFR adjoint on the 4096-pulse x 4096-frequency stripmap
+workload (16,714,266 Stolt-mapped samples -> 4096 x 4096 image), one JSON line.
+
+One step = one tFFR reconstruction of a batch of samples that is already in
+HBM: tffr_set_points (coordinate reduction + pulse rows), tffr_weights
+(frame weights + threshold) and tffr_adjoint (range spread, azimuth taps +
+row FFT, column FFT + deapodisation).  The forward twin is timed on its own
+(key "forward").  Inputs per step (402 MB of coordinates and samples) exceed
+the 129 MB L2, so no flush is inserted between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs its own copy of the workload (independent
+images, no collective on the data path); rank 0 prints value = total samples
+over all ranks / max-over-ranks time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "NU samples/s, tFFR adjoint, 16.7M samples->4096^2 image, rel-L2<=1e-5; HBM %"
+UNIT = "NU samples/s"
+WORKLOAD = "stripmap_4096"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def gpu_id_for_smi(local_rank: int):
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(local_rank).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[local_rank] if vis else str(local_rank)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_time(wl, D, n_pix: int, n_w: int, seed: int = 0):
+    """Time the oracle on n_w weight evaluations and n_pix image pixels; return per-unit seconds.
+
+    D: the oracle's weights for all samples (computed once by the caller, outside the timing).
+    """
+    import numpy as np
+    import oracle
+    g = np.random.default_rng(seed)
+    sel = g.integers(0, wl.N, n_w)
+    t0 = time.perf_counter()
+    oracle.tffr_weights(wl.lam_x[sel], wl.M)
+    t_w = (time.perf_counter() - t0) / n_w
+    jx, jy = g.integers(0, wl.M, n_pix), g.integers(0, wl.M, n_pix)
+    t0 = time.perf_counter()
+    if n_pix:
+        oracle.adjoint_pixels(wl.lam_x, wl.lam_y, wl.values, D, wl.M, wl.M, jx, jy)
+    t_p = (time.perf_counter() - t0) / max(n_pix, 1)
+    return t_w, t_p
+
+
+def cpu_baseline(wl, D, budget_s: float = 15.0):
+    import oracle
+    t_w, t_p1 = oracle_sample_time(wl, D, 2, 200000, seed=1)
+    n_pix = int(max(2, min(4096, budget_s / max(t_p1, 1e-6))))
+    t_w, t_p = oracle_sample_time(wl, D, n_pix, 2000000, seed=2)
+    full = t_w * wl.N + t_p * wl.M * wl.M
+    return {"value": wl.N / full, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "FP64 oracle: tFFR weights on 2,000,000 of the %d samples and the direct sum of "
+                      "Eq. (fstraight) at %d random pixels of the %dx%d image; full-image time "
+                      "extrapolated (weights x N, sum x M^2 pixels) = %.0f s" % (wl.N, n_pix, wl.M, wl.M, full)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    from synth import make_workload
+    wl = make_workload(WORKLOAD)
+    D = oracle.tffr_weights(wl.lam_x, wl.M)
+    n_pix, n_w = 4, 200000
+
+    def step(i):
+        return oracle_sample_time(wl, D, n_pix, n_w, seed=100 + i)
+
+    for i in range(args.warmup):
+        step(i)
+    tw = tp = 0.0
+    for i in range(args.steps):
+        a, b = step(args.warmup + i)
+        tw += a
+        tp += b
+    tw /= args.steps
+    tp /= args.steps
+    full = tw * wl.N + tp * wl.M * wl.M
+    value = wl.N / full
+    sample = ("each step: FP64 oracle weights on %d samples + direct sum at %d pixels; throughput "
+              "extrapolated to the full %d-sample, %dx%d image" % (n_w, n_pix, wl.N, wl.M, wl.M))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": wl.N, "image": "%dx%d" % (wl.M, wl.M)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1910_10908_gb300 import Plan
+    from synth import make_workload
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = make_workload(WORKLOAD)
+    N, M = wl.N, wl.M
+    lx = torch.from_numpy(wl.lam_x).to(dev)
+    ly = torch.from_numpy(wl.lam_y).to(dev)
+    vals = torch.from_numpy(wl.values).to(dev)
+    img = torch.empty((M, M), dtype=torch.complex64, device=dev)
+    plan = Plan(M, values="c64", device=dev)
+    stream = plan.stream
+
+    def step():
+        plan.set_points(lx, ly)
+        plan.weights(count=False)
+        plan.adjoint(vals, out=img)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = plan.info()
+
+    # ---- timed region: K steps, device events on the plan's stream ----
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = plan.info()["kernel_launches"]
+    with ClockSampler(gpu_id_for_smi(local)) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        plan.profile(True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    stages = plan.profile_read()
+    plan.profile(False)
+    launches = plan.info()["kernel_launches"] - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms_max = max_over_ranks(ms, world)
+    value = world * N / (ms_max * 1e-3)
+
+    # ---- per-kernel roofline from the stage timings of the timed region ----
+    hbm, peak_kind = peaks()
+    R = int(info["row_cells"])
+    T_bytes = 8 * M * (2 * M)
+    alg = {
+        "points": N * (16 + 33),
+        "weights": N * (8 + 4),
+        "spread": N * 20 + 8 * R,
+        "row_fft": 8 * R + T_bytes,
+        "col_fft": T_bytes + 8 * M * M,
+    }
+    kern = {}
+    for name, b in alg.items():
+        tot, cnt = stages[name]
+        if cnt:
+            per = tot / cnt
+            kern[name] = {"ms": per, "gbs": b / (per * 1e-3) / 1e9, "alg_bytes": b,
+                          "frac": b / (per * 1e-3) / 1e9 / hbm}
+    hot = max(("spread", "row_fft", "col_fft"), key=lambda k: kern[k]["ms"])
+    roof = {"bound": "hbm", "kernel": hot, "achieved": kern[hot]["gbs"], "peak": hbm, "unit": "GB/s",
+            "frac": kern[hot]["frac"], "peak_source": peak_kind, "traffic": None}
+
+    # ---- forward twin, timed on its own ----
+    yout = torch.empty(N, dtype=torch.complex64, device=dev)
+    for _ in range(2):
+        plan.forward(img, out=yout)
+    kf = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(kf):
+        plan.forward(img, out=yout)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / kf
+
+    # ---- end to end through host buffers ----
+    h_lx = torch.from_numpy(wl.lam_x).pin_memory()
+    h_ly = torch.from_numpy(wl.lam_y).pin_memory()
+    h_v = torch.from_numpy(wl.values).pin_memory()
+    h_img = torch.empty((M, M), dtype=torch.complex64).pin_memory()
+    d_lx, d_ly, d_v = torch.empty_like(lx), torch.empty_like(ly), torch.empty_like(vals)
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            d_lx.copy_(h_lx, non_blocking=True)
+            d_ly.copy_(h_ly, non_blocking=True)
+            d_v.copy_(h_v, non_blocking=True)
+        plan.set_points(d_lx, d_ly)
+        plan.weights(count=False)
+        plan.adjoint(d_v, out=img)
+        with torch.cuda.stream(stream):
+            h_img.copy_(img, non_blocking=True)
+
+    e2e_step()
+    ke = max(3, args.steps // 4)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev0.record(stream)
+    for _ in range(ke):
+        e2e_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(ev0.elapsed_time(ev1) / ke, world)
+    h2d = int(h_lx.numel() * 8 + h_ly.numel() * 8 + h_v.numel() * 8)
+    d2h = int(h_img.numel() * 8)
+
+    line = None
+    if rank == 0:
+        # sampled accuracy of the timed configuration against the FP64 oracle
+        import oracle
+        g = np.random.default_rng(7)
+        jx, jy = g.integers(0, M, 24), g.integers(0, M, 24)
+        D = oracle.tffr_weights(wl.lam_x, M)
+        ref = oracle.adjoint_pixels(wl.lam_x, wl.lam_y, wl.values, D, M, M, jx, jy)
+        got = img.cpu().numpy()[jy, jx].astype(np.complex128)
+        rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        base = cpu_baseline(wl, D) if world == 1 else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "image": "%dx%d" % (M, M), "pulses": wl.n_pulses,
+                       "freqs": wl.n_freq, "sigma": 2, "width": 6, "beta": info["beta"], "values": "c64",
+                       "layout": "rows" if info["layout"] == 2 else "general", "pulse_rows": info["n_rows"],
+                       "step": "set_points+weights+adjoint", "l2": "inputs (402 MB/step) larger than L2",
+                       "parallelism": "independent images per GPU" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "kernels": kern,
+            "pixels_per_s": world * M * M / (ms_max * 1e-3),
+            "adjoint_only_samples_per_s": N / (sum(stages[k][0] / max(stages[k][1], 1)
+                                                   for k in ("spread", "row_fft", "col_fft")) * 1e-3),
+            "forward": {"value": N / (fwd_ms * 1e-3), "unit": UNIT, "ms": fwd_ms},
+            "accuracy": {"rel_l2_vs_fp64_oracle": rel, "pixels": int(jx.shape[0])},
+            "e2e": {"value": world * N / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        if base is not None:
+            line["cpu_baseline"] = base
+    plan.close()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    barrier(world)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="tffr", choices=["tffr", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_gpu(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

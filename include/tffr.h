@@ -1,0 +1,212 @@
+/*
+ * tffr.h -- C ABI of the GB300 tFFR library: the weighted adjoint non-uniform
+ * FFT behind thresholded Fourier-frame reconstruction (tFFR) of stripmap SAR
+ * data, and its forward twin.
+ *
+ * What is computed (McKay, Gelb, Jayasuriya, Monga, arXiv 1910.10908):
+ *
+ *   image   f[jy][jx] = sum_n D_n fhat_n exp(+2 pi i (lam_x[n] x_jx + lam_y[n] y_jy))
+ *           with x_j = (j - M/2) / M on the centred pixel grid, no 1/N factor:
+ *           Eq. (fstraight) of Sec. II.B with alpha_n = D_n, evaluated the NUFFT
+ *           way of Eq. (Anu) (spread with a window, inverse FFT, divide by the
+ *           window transform) and Algorithm 1 (per-slice correction, one 2-D IFFT).
+ *   weights D_n = R_tau(diag(Psi W)^+) on the range axis (Algorithm 1; Eq. (Psi);
+ *           R_tau(x) = x if x >= tau else 0 of Sec. III.B; window
+ *           w(x) = exp(-a |x - 1/2|), a = 0.01, tau = 0.97 of Sec. IV).
+ *   forward y_n = D_n sum_j f_j exp(-2 pi i lam_n . x_j), the adjoint of the image map.
+ *
+ * Coordinates lam are in grid units (cycles per image extent), so the image's
+ * own Fourier grid is the integers in [-M/2, M/2).  lam_x is the range
+ * (non-uniform) axis, lam_y the azimuth (uniform) axis.
+ *
+ * Conventions shared by every call:
+ *  - Every pointer argument marked "device" must point to device memory of
+ *    the current CUDA device; the caller owns it and keeps ownership.  The
+ *    plan owns all of its internal device buffers and frees them in
+ *    tffr_destroy.
+ *  - Every call is ordered on the plan's stream.  tffr_adjoint and
+ *    tffr_forward never synchronise; tffr_set_points synchronises the stream
+ *    before it returns (the caller may free lam_x / lam_y afterwards);
+ *    tffr_weights synchronises only when n_kept is requested.
+ *  - Return value: a tffr_status.  On TFFR_ERR_CUDA the CUDA error text is
+ *    available from tffr_last_error(plan).
+ *  - A plan is not thread-safe: calls on one plan must not overlap.
+ */
+#ifndef TFFR_H
+#define TFFR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tffr_plan_s* tffr_plan_t;
+
+/* A cudaStream_t passed as an opaque pointer; NULL is the default stream. */
+typedef void* tffr_stream_t;
+
+typedef enum {
+    TFFR_OK = 0,
+    TFFR_ERR_INVALID_ARG = 1, /* bad size, option, pointer, or non-finite coordinate */
+    TFFR_ERR_NOT_READY = 2,   /* adjoint/forward before set_points and weights */
+    TFFR_ERR_CUDA = 3,        /* a CUDA call failed; see tffr_last_error */
+    TFFR_ERR_OOM = 4,         /* device allocation failed */
+    TFFR_ERR_TIMEOUT = 5      /* a bounded device wait gave up */
+} tffr_status;
+
+/* Storage type of the sample values read by tffr_adjoint (and written by
+ * tffr_forward).  Arithmetic is FP32 in every case. */
+typedef enum {
+    TFFR_VALUES_C64 = 0,  /* complex64: float re, im (8 bytes per sample) */
+    TFFR_VALUES_C128 = 1, /* complex128: double re, im (16 bytes); forward writes complex128 */
+    TFFR_VALUES_F16 = 2,  /* half re, im (4 bytes); forward writes complex64 */
+    TFFR_VALUES_BF16 = 3  /* bfloat16 re, im (4 bytes); forward writes complex64 */
+} tffr_values;
+
+/* How samples are organised. */
+typedef enum {
+    TFFR_POINTS_AUTO = 0,    /* pulse rows if runs of equal lam_y average >= 8 samples */
+    TFFR_POINTS_GENERAL = 1, /* arbitrary points, bucketed by fine-grid row */
+    TFFR_POINTS_ROWS = 2     /* consecutive samples with bit-equal lam_y form one pulse row */
+} tffr_points_layout;
+
+typedef struct {
+    int sigma;      /* oversampling of the FFT grid; only 2 is supported */
+    int width;      /* spreading-kernel width w in fine cells: 2, 4, 6 or 8 (default 6) */
+    double beta;    /* exponential-of-semicircle shape; <= 0 selects 2.30 * width */
+    int values;     /* tffr_values (default TFFR_VALUES_C64) */
+    int layout;     /* tffr_points_layout (default TFFR_POINTS_AUTO) */
+} tffr_opts;
+
+typedef enum {
+    TFFR_WEIGHTS_TFFR = 0, /* D_n = R_tau(1 / G_n), G_n the diagonal of Psi W */
+    TFFR_WEIGHTS_UNIT = 1, /* D_n = 1: the plain sum of Eq. (fstraight) */
+    TFFR_WEIGHTS_USER = 2  /* D_n given by the caller (device float[N], no threshold) */
+} tffr_weight_mode;
+
+typedef struct {
+    int mode;             /* tffr_weight_mode */
+    int separable;        /* 0: range axis only (Algorithm 1); 1: D = R_tau(1 / (G(lam_x) G(lam_y))) */
+    double a;             /* window decay a of w(x) = exp(-a |x - 1/2|), default 0.01 */
+    double q;             /* band of W: grid points with |lam - l| < q, default 3 */
+    double tau;           /* threshold of R_tau, default 0.97 */
+    const float* user_D;  /* device float[N] for TFFR_WEIGHTS_USER, else ignored */
+} tffr_weight_opts;
+
+typedef struct {
+    int Mx, My;                /* image size */
+    int nx, ny;                /* fine (oversampled) grid size, 2 Mx by 2 My */
+    int width;
+    double beta;
+    int64_t N;                 /* samples of the last tffr_set_points */
+    int layout;                /* TFFR_POINTS_ROWS or TFFR_POINTS_GENERAL in use (0 before points) */
+    int64_t n_rows;            /* pulse rows (rows layout) */
+    int64_t row_cells;         /* cells of all pulse-row buffers (rows layout) */
+    int max_row_cells;         /* longest pulse-row buffer */
+    int64_t n_kept;            /* samples with D_n != 0 after the last tffr_weights (-1 if unknown) */
+    size_t device_bytes;       /* device memory held by the plan */
+    int64_t kernel_launches;   /* kernels this plan has launched since it was created */
+} tffr_plan_info;
+
+/* Stages of the pipeline, for tffr_profile_read. */
+typedef enum {
+    TFFR_STAGE_POINTS = 0,     /* tffr_set_points: coordinate reduction, rows or buckets */
+    TFFR_STAGE_WEIGHTS = 1,    /* tffr_weights */
+    TFFR_STAGE_SPREAD = 2,     /* adjoint: range-axis spread of pulse rows */
+    TFFR_STAGE_ROW_FFT = 3,    /* adjoint: azimuth taps + FFT along x + x deapodisation */
+    TFFR_STAGE_COL_FFT = 4,    /* adjoint: FFT along y + y deapodisation + image store */
+    TFFR_STAGE_FWD_COL_FFT = 5,/* forward: deapodise + FFT along y */
+    TFFR_STAGE_FWD_ROW_FFT = 6,/* forward: FFT along x + transposed azimuth taps */
+    TFFR_STAGE_INTERP = 7,     /* forward: range-axis interpolation to the samples */
+    TFFR_NUM_STAGES = 8
+} tffr_stage;
+
+/* Fill the defaults: sigma 2, width 6, beta 2.30 * width, complex64 values, auto layout. */
+void tffr_default_opts(tffr_opts* opts);
+
+/* Fill the defaults: tFFR mode, range axis, a = 0.01, q = 3, tau = 0.97 (Sec. IV). */
+void tffr_default_weight_opts(tffr_weight_opts* opts);
+
+/*
+ * Create a plan for an My x Mx image (Mx, My powers of two, 16 <= M <= 4096).
+ * Precomputes in FP64 on the host the FFT twiddles and the deapodisation
+ * factors 1 / phi_hat(k / 2M) of the spreading kernel, uploads them, and
+ * allocates the Mx x 2My intermediate of the two FFT passes.
+ * opts may be NULL (defaults).  stream: the stream every later call uses.
+ * Errors: INVALID_ARG for out-of-range sizes or options; OOM; CUDA.
+ */
+int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stream_t stream);
+
+/*
+ * Set the N sample frequencies (device double[N] each, grid units; Sec. II.A:
+ * lam_x range, lam_y azimuth).  Reduces each coordinate in FP64 to a fine-grid
+ * cell and an FP32 offset, finds the pulse rows (runs of bit-equal lam_y) or
+ * buckets the samples by fine-grid row, and sizes the per-row buffers.
+ * N = 0 is allowed (adjoint then returns a zero image).  Invalidates the weights.
+ * Errors: INVALID_ARG for N < 0, N >= 2^31, NULL pointers with N > 0, or any
+ * |lam| >= 2^28 or non-finite coordinate; OOM; CUDA.  Synchronises the stream.
+ */
+int tffr_set_points(tffr_plan_t plan, int64_t N, const double* lam_x, const double* lam_y);
+
+/*
+ * Compute the frame weights D_n (Algorithm 1, lines forming W, Psi and
+ * D = R_tau((W Psi)^+), diagonal only) in FP64 and keep them, as FP32, in the
+ * plan.  opts may be NULL (defaults).  D_out (nullable, device float[N])
+ * receives a copy; n_kept (nullable, host) receives the count of D_n != 0 and
+ * makes the call synchronise.
+ * Errors: NOT_READY before tffr_set_points; INVALID_ARG for bad options
+ * (q <= 0, a < 0, unknown mode, USER mode without user_D); CUDA.
+ */
+int tffr_weights(tffr_plan_t plan, const tffr_weight_opts* opts, float* D_out, int64_t* n_kept);
+
+/*
+ * The tFFR image (the hot path).  values: device, N samples in the plan's
+ * value type, in the order given to tffr_set_points.  image: device complex64
+ * [My][Mx], row-major, x fastest, fully overwritten.
+ * Errors: NOT_READY before tffr_set_points + tffr_weights; INVALID_ARG for
+ * NULL pointers; CUDA.
+ */
+int tffr_adjoint(tffr_plan_t plan, const void* values, void* image);
+
+/*
+ * The forward twin: values[n] = (apply_weights ? D_n : 1) * sum_j image_j
+ * exp(-2 pi i lam_n . x_j).  image: device complex64 [My][Mx].  values:
+ * device, N samples (complex128 for the C128 value type, complex64 otherwise).
+ * Errors: as tffr_adjoint.
+ */
+int tffr_forward(tffr_plan_t plan, const void* image, void* values, int apply_weights);
+
+/*
+ * Per-stage timing with CUDA events recorded on the plan's stream around each
+ * stage's kernels.  enable != 0 starts (and resets) recording, 0 stops it.
+ * Recording costs two event records per stage launch.
+ */
+int tffr_profile(tffr_plan_t plan, int enable);
+
+/*
+ * Synchronise the plan's stream and return, per stage (arrays of length
+ * nstages <= TFFR_NUM_STAGES), the summed event time in milliseconds and the
+ * number of timed executions since the last tffr_profile(plan, 1).
+ * At most 4096 executions per stage are kept; later ones are not timed.
+ */
+int tffr_profile_read(tffr_plan_t plan, double* ms, int64_t* count, int nstages);
+
+/* Query sizes and the state of a plan. */
+int tffr_plan_get_info(tffr_plan_t plan, tffr_plan_info* info);
+
+/* Free the plan and every device buffer it owns (after synchronising its stream). NULL is a no-op. */
+int tffr_destroy(tffr_plan_t plan);
+
+/* Static text for a status code. */
+const char* tffr_error_string(int status);
+
+/* Text of the last error on this plan ("" if none).  Valid until the next call on the plan. */
+const char* tffr_last_error(tffr_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFFR_H */

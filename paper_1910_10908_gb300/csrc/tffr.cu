@@ -1,0 +1,752 @@
+// Host side of the C ABI declared in include/tffr.h: plan set-up (FP64
+// tables), point preparation, weights, and the launch sequences of the
+// adjoint and forward transforms.  All device work is in the .cuh kernels.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tffr.h"
+#include "common.cuh"
+#include "fft_smem.cuh"
+#include "kernels_fft.cuh"
+#include "kernels_points.cuh"
+#include "kernels_spread.cuh"
+
+using namespace tffr;
+
+// Device buffer with a capacity; grown (never shrunk) on demand.
+template <typename T>
+struct DevBuf {
+    T* ptr = nullptr;
+    int64_t cap = 0;
+};
+
+// Event pairs recorded around one stage's kernels.
+struct StageProf {
+    std::vector<cudaEvent_t> ev;
+    int64_t n = 0;
+};
+constexpr int64_t kProfMaxPerStage = 4096;
+
+struct tffr_plan_s {
+    int Mx = 0, My = 0, nx = 0, ny = 0, lognx = 0, logny = 0, w = 6;
+    double beta = 0.0;
+    int values = TFFR_VALUES_C64;
+    int layout_hint = TFFR_POINTS_AUTO;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    size_t device_bytes = 0;
+
+    // plan-time tables and the intermediate of the FFT passes
+    DevBuf<float2> twx, twy, T;
+    DevBuf<float> deap_x, deap_y;
+    DevBuf<int> d_small;                  // [0] error flag, [1] scan sum
+    DevBuf<unsigned long long> d_kept;
+
+    // points
+    int64_t N = 0;
+    bool have_points = false, have_weights = false;
+    int layout = 0;
+    int64_t n_kept = -1;
+    DevBuf<double> keep_x, keep_y;
+    DevBuf<int> lx, ly;
+    DevBuf<float> fx, fy, D;
+    DevBuf<uint8_t> run_start;
+    DevBuf<int> tiles;
+
+    // pulse rows
+    int P = 0;
+    int64_t R_cells = 0;
+    int max_len = 0;
+    DevBuf<int> row_start, row_clo, row_len, row_ly, bucket_rows, bucket_start;
+    DevBuf<float> row_fy;
+    DevBuf<int64_t> row_off;
+    DevBuf<float2> R;
+
+    // general points
+    DevBuf<int> perm, slx, cursor;
+    DevBuf<float> sfx, sfy, sD;
+    DevBuf<float2> acc;
+
+    // launch count and optional per-stage event timing
+    int64_t launches = 0;
+    bool prof_on = false;
+    StageProf prof[TFFR_NUM_STAGES];
+};
+
+namespace {
+
+int fail(tffr_plan_s* p, int status, const std::string& msg) {
+    if (p) p->last_error = msg;
+    return status;
+}
+
+int cuda_fail(tffr_plan_s* p, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + ": " + cudaGetErrorString(e);
+    return fail(p, e == cudaErrorMemoryAllocation ? TFFR_ERR_OOM : TFFR_ERR_CUDA, m);
+}
+
+#define CK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(p, e_, #call); \
+    } while (0)
+
+#define CK_LAUNCH(where)                                  \
+    do {                                                  \
+        ++p->launches;                                    \
+        cudaError_t e_ = cudaGetLastError();              \
+        if (e_ != cudaSuccess) return cuda_fail(p, e_, where); \
+    } while (0)
+
+int stage_mark(tffr_plan_s* p, int stage, bool end) {
+    if (!p->prof_on) return TFFR_OK;
+    StageProf& sp = p->prof[stage];
+    if (sp.n >= kProfMaxPerStage) return TFFR_OK;
+    const size_t idx = (size_t)(2 * sp.n + (end ? 1 : 0));
+    while (sp.ev.size() <= idx) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        sp.ev.push_back(e);
+    }
+    CK(cudaEventRecord(sp.ev[idx], p->stream));
+    if (end) ++sp.n;
+    return TFFR_OK;
+}
+
+#define STAGE_BEGIN(st) do { int s_ = stage_mark(p, (st), false); if (s_ != TFFR_OK) return s_; } while (0)
+#define STAGE_END(st) do { int s_ = stage_mark(p, (st), true); if (s_ != TFFR_OK) return s_; } while (0)
+
+template <typename T>
+cudaError_t grow(tffr_plan_s* p, DevBuf<T>& b, int64_t want) {
+    if (b.ptr && want <= b.cap) return cudaSuccess;
+    if (b.ptr) {
+        cudaFree(b.ptr);
+        p->device_bytes -= (size_t)b.cap * sizeof(T);
+        b.ptr = nullptr;
+        b.cap = 0;
+    }
+    const int64_t n = std::max<int64_t>(want, 1);
+    cudaError_t e = cudaMalloc((void**)&b.ptr, (size_t)n * sizeof(T));
+    if (e == cudaSuccess) {
+        b.cap = n;
+        p->device_bytes += (size_t)n * sizeof(T);
+    }
+    return e;
+}
+
+template <typename T>
+void release(DevBuf<T>& b) {
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.cap = 0;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n).
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wts) {
+    x.assign(n, 0.0);
+    wts.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int k = 1; k <= n; ++k) {
+                const double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            const double dz = p0 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        wts[i] = wts[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// phi_hat(xi) = int_{-w/2}^{w/2} phi(z) exp(2 pi i xi z) dz for the ES kernel (real, even).
+std::vector<double> es_transform(const std::vector<double>& xi, int w, double beta) {
+    std::vector<double> gx, gw;
+    const int nq = 160;
+    gauss_legendre(nq, gx, gw);
+    const double hw = 0.5 * w, two_pi = 6.283185307179586476925286766559;
+    std::vector<double> z(nq), phi(nq), wz(nq);
+    for (int i = 0; i < nq; ++i) {
+        z[i] = 0.5 * hw * (gx[i] + 1.0);      // [0, w/2]
+        wz[i] = 0.5 * hw * gw[i];
+        const double s = z[i] / hw;
+        const double t = 1.0 - s * s;
+        phi[i] = t > 0 ? std::exp(beta * (std::sqrt(t) - 1.0)) : 0.0;
+    }
+    std::vector<double> out(xi.size());
+    for (size_t k = 0; k < xi.size(); ++k) {
+        double acc = 0.0;
+        for (int i = 0; i < nq; ++i) acc += wz[i] * phi[i] * std::cos(two_pi * xi[k] * z[i]);
+        out[k] = 2.0 * acc;
+    }
+    return out;
+}
+
+int upload_tables(tffr_plan_s* p) {
+    auto twiddles = [](int n) {
+        std::vector<float2> t(n);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int m = 0; m < n; ++m) {
+            const double a = two_pi * (double)m / (double)n;
+            t[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        return t;
+    };
+    auto deapod = [&](int M, int n) {
+        std::vector<double> xi(M);
+        for (int j = 0; j < M; ++j) xi[j] = (double)(j - M / 2) / (double)n;
+        std::vector<double> ph = es_transform(xi, p->w, p->beta);
+        std::vector<float> d(M);
+        for (int j = 0; j < M; ++j) d[j] = (float)(1.0 / ph[j]);
+        return d;
+    };
+    std::vector<float2> tx = twiddles(p->nx), ty = twiddles(p->ny);
+    std::vector<float> dx = deapod(p->Mx, p->nx), dy = deapod(p->My, p->ny);
+    CK(grow(p, p->twx, p->nx));
+    CK(grow(p, p->twy, p->ny));
+    CK(grow(p, p->deap_x, p->Mx));
+    CK(grow(p, p->deap_y, p->My));
+    CK(cudaMemcpyAsync(p->twx.ptr, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->twy.ptr, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->deap_x.ptr, dx.data(), dx.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->deap_y.ptr, dy.data(), dy.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaStreamSynchronize(p->stream));   // the host vectors end with this scope
+    return TFFR_OK;
+}
+
+constexpr int kFftSmemMax = (kFftNMax + kFftNMax / 16) * (int)sizeof(float2);
+constexpr int kRowSmemMax = kFftNMax * (int)sizeof(float2);
+
+template <typename K>
+cudaError_t smem_attr(K kernel, int bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+int set_kernel_attributes(tffr_plan_s* p) {
+    static bool done = false;
+    if (done) return TFFR_OK;
+    CK(smem_attr(k_adj_rows<true, float2>, kFftSmemMax));
+    CK(smem_attr(k_adj_rows<true, double2>, kFftSmemMax));
+    CK(smem_attr(k_adj_rows<true, __half2>, kFftSmemMax));
+    CK(smem_attr(k_adj_rows<true, __nv_bfloat162>, kFftSmemMax));
+    CK(smem_attr(k_adj_rows<false, float2>, kFftSmemMax));
+    CK(smem_attr(k_adj_rows<false, double2>, kFftSmemMax));
+    CK(smem_attr(k_adj_rows<false, __half2>, kFftSmemMax));
+    CK(smem_attr(k_adj_rows<false, __nv_bfloat162>, kFftSmemMax));
+    CK(smem_attr(k_adj_cols, kFftSmemMax));
+    CK(smem_attr(k_fwd_cols, kFftSmemMax));
+    CK(smem_attr(k_fwd_rows<true>, kFftSmemMax));
+    CK(smem_attr(k_fwd_rows<false>, kFftSmemMax));
+    CK(smem_attr(k_spread_rows<float2>, kRowSmemMax));
+    CK(smem_attr(k_spread_rows<double2>, kRowSmemMax));
+    CK(smem_attr(k_spread_rows<__half2>, kRowSmemMax));
+    CK(smem_attr(k_spread_rows<__nv_bfloat162>, kRowSmemMax));
+    done = true;
+    return TFFR_OK;
+}
+
+int grid_for(int64_t n, int threads) {
+    const int64_t b = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+}
+
+RowsView rows_view(const tffr_plan_s* p) {
+    RowsView v;
+    v.P = p->P;
+    v.row_start = p->row_start.ptr;
+    v.row_clo = p->row_clo.ptr;
+    v.row_len = p->row_len.ptr;
+    v.row_ly = p->row_ly.ptr;
+    v.row_fy = p->row_fy.ptr;
+    v.row_off = p->row_off.ptr;
+    v.bucket_start = p->bucket_start.ptr;
+    v.bucket_rows = p->bucket_rows.ptr;
+    return v;
+}
+
+GeneralView general_view(const tffr_plan_s* p) {
+    GeneralView v;
+    v.bucket_start = p->bucket_start.ptr;
+    v.perm = p->perm.ptr;
+    v.slx = p->slx.ptr;
+    v.sfx = p->sfx.ptr;
+    v.sfy = p->sfy.ptr;
+    v.sD = p->sD.ptr;
+    return v;
+}
+
+// Number of runs of equal lam_y (pulse rows); with emit, their first samples in order.
+int compact_run_starts(tffr_plan_s* p, int64_t N, int* P_out, bool emit) {
+    const int64_t ntiles = (N + kScanTile - 1) / kScanTile;
+    CK(grow(p, p->tiles, ntiles));
+    k_count_flags<<<(unsigned)ntiles, kScanThreads, 0, p->stream>>>(N, p->run_start.ptr, p->tiles.ptr);
+    CK_LAUNCH("k_count_flags");
+    k_scan_tile_counts<<<1, kScanThreads, 0, p->stream>>>((int)ntiles, p->tiles.ptr, p->d_small.ptr + 1);
+    CK_LAUNCH("k_scan_tile_counts");
+    int P = 0;
+    CK(cudaMemcpyAsync(&P, p->d_small.ptr + 1, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    *P_out = P;
+    if (!emit) return TFFR_OK;
+    CK(grow(p, p->row_start, P));
+    k_emit_run_starts<<<(unsigned)ntiles, kScanThreads, 0, p->stream>>>(N, p->run_start.ptr, p->tiles.ptr,
+                                                                         p->row_start.ptr);
+    CK_LAUNCH("k_emit_run_starts");
+    return TFFR_OK;
+}
+
+int build_rows(tffr_plan_s* p) {
+    const int64_t N = p->N;
+    int P = 0;
+    int s = compact_run_starts(p, N, &P, true);
+    if (s != TFFR_OK) return s;
+    p->P = P;
+    CK(grow(p, p->row_clo, P));
+    CK(grow(p, p->row_len, P));
+    CK(grow(p, p->row_ly, P));
+    CK(grow(p, p->row_fy, P));
+    CK(grow(p, p->row_off, P));
+    CK(grow(p, p->bucket_rows, P));
+    CK(grow(p, p->bucket_start, p->ny + 1));
+    k_row_info<<<std::min(P, 152 * 16), 256, 0, p->stream>>>(P, N, p->nx, p->w, p->row_start.ptr, p->lx.ptr,
+                                                               p->ly.ptr, p->fy.ptr, p->row_clo.ptr,
+                                                               p->row_len.ptr, p->row_ly.ptr, p->row_fy.ptr);
+    CK_LAUNCH("k_row_info");
+    // Per-row bookkeeping (P entries) on the host: buffer offsets and the
+    // grouping of rows by fine y cell.
+    std::vector<int> len(P), rly(P);
+    CK(cudaMemcpyAsync(len.data(), p->row_len.ptr, (size_t)P * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(rly.data(), p->row_ly.ptr, (size_t)P * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    std::vector<int64_t> off(P);
+    int64_t tot = 0;
+    int mx = 0;
+    std::vector<int> bstart(p->ny + 1, 0);
+    for (int i = 0; i < P; ++i) {
+        off[i] = tot;
+        tot += len[i];
+        mx = std::max(mx, len[i]);
+        bstart[(rly[i] & (p->ny - 1)) + 1]++;
+    }
+    for (int b = 0; b < p->ny; ++b) bstart[b + 1] += bstart[b];
+    std::vector<int> brows(P), cur(bstart.begin(), bstart.end() - 1);
+    for (int i = 0; i < P; ++i) brows[cur[rly[i] & (p->ny - 1)]++] = i;
+    p->R_cells = tot;
+    p->max_len = mx;
+    CK(grow(p, p->R, tot));
+    CK(cudaMemcpyAsync(p->row_off.ptr, off.data(), (size_t)P * sizeof(int64_t), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->bucket_start.ptr, bstart.data(), (size_t)(p->ny + 1) * sizeof(int),
+                       cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->bucket_rows.ptr, brows.data(), (size_t)P * sizeof(int), cudaMemcpyHostToDevice,
+                       p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    return TFFR_OK;
+}
+
+int build_general(tffr_plan_s* p) {
+    const int64_t N = p->N;
+    p->P = 0;
+    CK(grow(p, p->bucket_start, p->ny + 1));
+    CK(grow(p, p->cursor, p->ny + 1));
+    CK(grow(p, p->perm, N));
+    CK(grow(p, p->slx, N));
+    CK(grow(p, p->sfx, N));
+    CK(grow(p, p->sfy, N));
+    CK(grow(p, p->sD, N));
+    CK(grow(p, p->acc, N));
+    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(p->ny + 1) * sizeof(int), p->stream));
+    k_bucket_hist<<<grid_for(N, 256), 256, p->ny * sizeof(int), p->stream>>>(N, p->ny, p->ly.ptr, p->cursor.ptr);
+    CK_LAUNCH("k_bucket_hist");
+    std::vector<int> cnt(p->ny);
+    CK(cudaMemcpyAsync(cnt.data(), p->cursor.ptr, (size_t)p->ny * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    std::vector<int> bstart(p->ny + 1, 0);
+    for (int b = 0; b < p->ny; ++b) bstart[b + 1] = bstart[b] + cnt[b];
+    CK(cudaMemcpyAsync(p->bucket_start.ptr, bstart.data(), (size_t)(p->ny + 1) * sizeof(int),
+                       cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(p->ny + 1) * sizeof(int), p->stream));
+    k_bucket_scatter<<<grid_for(N, 256), 256, 0, p->stream>>>(N, p->ny, p->ly.ptr, p->bucket_start.ptr,
+                                                               p->cursor.ptr, p->perm.ptr);
+    CK_LAUNCH("k_bucket_scatter");
+    k_gather_sorted<<<grid_for(N, 256), 256, 0, p->stream>>>(N, p->perm.ptr, p->lx.ptr, p->fx.ptr, p->fy.ptr,
+                                                              p->slx.ptr, p->sfx.ptr, p->sfy.ptr);
+    CK_LAUNCH("k_gather_sorted");
+    CK(cudaStreamSynchronize(p->stream));
+    return TFFR_OK;
+}
+
+size_t fft_smem_bytes(const tffr_plan_s* p) {
+    const int n = std::max(p->nx, p->ny);
+    return (size_t)(n + n / 16) * sizeof(float2);
+}
+
+template <typename VT>
+int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
+    const size_t fsm = fft_smem_bytes(p);
+    const float beta = (float)p->beta;
+    if (p->layout == TFFR_POINTS_ROWS) {
+        const RowsView rv = rows_view(p);
+        STAGE_BEGIN(TFFR_STAGE_SPREAD);
+        k_spread_rows<VT><<<p->P, kSpreadThreads, (size_t)p->max_len * sizeof(float2), p->stream>>>(
+            rv, p->N, p->nx, p->w, beta, values, p->D.ptr, p->lx.ptr, p->fx.ptr, p->R.ptr);
+        CK_LAUNCH("k_spread_rows");
+        STAGE_END(TFFR_STAGE_SPREAD);
+        STAGE_BEGIN(TFFR_STAGE_ROW_FFT);
+        k_adj_rows<true, VT><<<p->ny, kFftThreads, fsm, p->stream>>>(rv, general_view(p), p->R.ptr, values, p->nx,
+                                                                      p->lognx, p->ny, p->Mx, p->w, beta,
+                                                                      p->twx.ptr, p->deap_x.ptr, p->T.ptr);
+        CK_LAUNCH("k_adj_rows");
+        STAGE_END(TFFR_STAGE_ROW_FFT);
+    } else {
+        STAGE_BEGIN(TFFR_STAGE_ROW_FFT);
+        k_adj_rows<false, VT><<<p->ny, kFftThreads, fsm, p->stream>>>(rows_view(p), general_view(p), p->R.ptr,
+                                                                       values, p->nx, p->lognx, p->ny, p->Mx, p->w,
+                                                                       beta, p->twx.ptr, p->deap_x.ptr, p->T.ptr);
+        CK_LAUNCH("k_adj_rows");
+        STAGE_END(TFFR_STAGE_ROW_FFT);
+    }
+    STAGE_BEGIN(TFFR_STAGE_COL_FFT);
+    k_adj_cols<<<p->Mx, kFftThreads, fsm, p->stream>>>(p->T.ptr, p->ny, p->logny, p->My, p->Mx, p->twy.ptr,
+                                                       p->deap_y.ptr, image);
+    CK_LAUNCH("k_adj_cols");
+    STAGE_END(TFFR_STAGE_COL_FFT);
+    return TFFR_OK;
+}
+
+template <typename VT>
+int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_weights) {
+    const size_t fsm = fft_smem_bytes(p);
+    const float beta = (float)p->beta;
+    STAGE_BEGIN(TFFR_STAGE_FWD_COL_FFT);
+    k_fwd_cols<<<p->Mx, kFftThreads, fsm, p->stream>>>(image, p->ny, p->logny, p->My, p->Mx, p->twy.ptr,
+                                                       p->deap_y.ptr, p->deap_x.ptr, p->T.ptr);
+    CK_LAUNCH("k_fwd_cols");
+    STAGE_END(TFFR_STAGE_FWD_COL_FFT);
+    STAGE_BEGIN(TFFR_STAGE_FWD_ROW_FFT);
+    if (p->layout == TFFR_POINTS_ROWS) {
+        CK(cudaMemsetAsync(p->R.ptr, 0, (size_t)p->R_cells * sizeof(float2), p->stream));
+        const RowsView rv = rows_view(p);
+        k_fwd_rows<true><<<p->ny, kFftThreads, fsm, p->stream>>>(rv, general_view(p), p->T.ptr, p->nx, p->lognx,
+                                                                 p->ny, p->Mx, p->w, beta, p->twx.ptr, p->R.ptr,
+                                                                 p->acc.ptr);
+        CK_LAUNCH("k_fwd_rows");
+        STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
+        STAGE_BEGIN(TFFR_STAGE_INTERP);
+        k_interp_rows<VT><<<p->P, kSpreadThreads, 0, p->stream>>>(rv, p->N, p->nx, p->w, beta, p->R.ptr, p->D.ptr,
+                                                                   apply_weights, p->lx.ptr, p->fx.ptr, values);
+        CK_LAUNCH("k_interp_rows");
+        STAGE_END(TFFR_STAGE_INTERP);
+    } else {
+        CK(cudaMemsetAsync(p->acc.ptr, 0, (size_t)p->N * sizeof(float2), p->stream));
+        k_fwd_rows<false><<<p->ny, kFftThreads, fsm, p->stream>>>(rows_view(p), general_view(p), p->T.ptr, p->nx,
+                                                                  p->lognx, p->ny, p->Mx, p->w, beta, p->twx.ptr,
+                                                                  p->R.ptr, p->acc.ptr);
+        CK_LAUNCH("k_fwd_rows");
+        STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
+        STAGE_BEGIN(TFFR_STAGE_INTERP);
+        k_unpermute_output<VT><<<grid_for(p->N, 256), 256, 0, p->stream>>>(p->N, p->perm.ptr, p->acc.ptr, p->sD.ptr,
+                                                                            apply_weights, values);
+        CK_LAUNCH("k_unpermute_output");
+        STAGE_END(TFFR_STAGE_INTERP);
+    }
+    return TFFR_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void tffr_default_opts(tffr_opts* o) {
+    if (!o) return;
+    o->sigma = 2;
+    o->width = 6;
+    o->beta = 0.0;
+    o->values = TFFR_VALUES_C64;
+    o->layout = TFFR_POINTS_AUTO;
+}
+
+void tffr_default_weight_opts(tffr_weight_opts* o) {
+    if (!o) return;
+    o->mode = TFFR_WEIGHTS_TFFR;
+    o->separable = 0;
+    o->a = 0.01;
+    o->q = 3.0;
+    o->tau = 0.97;
+    o->user_D = nullptr;
+}
+
+const char* tffr_error_string(int s) {
+    switch (s) {
+        case TFFR_OK: return "ok";
+        case TFFR_ERR_INVALID_ARG: return "invalid argument";
+        case TFFR_ERR_NOT_READY: return "not ready: set points and weights first";
+        case TFFR_ERR_CUDA: return "CUDA error";
+        case TFFR_ERR_OOM: return "out of device memory";
+        case TFFR_ERR_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+const char* tffr_last_error(tffr_plan_t p) { return p ? p->last_error.c_str() : ""; }
+
+int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stream_t stream) {
+    if (!out) return TFFR_ERR_INVALID_ARG;
+    *out = nullptr;
+    tffr_opts o;
+    tffr_default_opts(&o);
+    if (opts) o = *opts;
+    if (!is_pow2(Mx) || !is_pow2(My) || Mx < 16 || My < 16 || 2 * Mx > kFftNMax || 2 * My > kFftNMax)
+        return TFFR_ERR_INVALID_ARG;
+    if (o.sigma != 2) return TFFR_ERR_INVALID_ARG;
+    if (o.width < 2 || o.width > 8 || (o.width & 1)) return TFFR_ERR_INVALID_ARG;
+    if (o.values < TFFR_VALUES_C64 || o.values > TFFR_VALUES_BF16) return TFFR_ERR_INVALID_ARG;
+    if (o.layout < TFFR_POINTS_AUTO || o.layout > TFFR_POINTS_ROWS) return TFFR_ERR_INVALID_ARG;
+    if (!(o.beta == o.beta) || o.beta > 100.0) return TFFR_ERR_INVALID_ARG;
+    tffr_plan_s* p = new (std::nothrow) tffr_plan_s();
+    if (!p) return TFFR_ERR_OOM;
+    p->Mx = Mx;
+    p->My = My;
+    p->nx = 2 * Mx;
+    p->ny = 2 * My;
+    p->lognx = ilog2(p->nx);
+    p->logny = ilog2(p->ny);
+    p->w = o.width;
+    p->beta = o.beta > 0 ? o.beta : 2.30 * o.width;
+    p->values = o.values;
+    p->layout_hint = o.layout;
+    p->stream = (cudaStream_t)stream;
+    int s = set_kernel_attributes(p);
+    if (s == TFFR_OK) s = upload_tables(p);
+    if (s == TFFR_OK) {
+        cudaError_t e = grow(p, p->T, (int64_t)Mx * p->ny);
+        if (e == cudaSuccess) e = grow(p, p->d_small, 4);
+        if (e == cudaSuccess) e = grow(p, p->d_kept, 1);
+        if (e != cudaSuccess) s = cuda_fail(p, e, "tffr_plan: allocation");
+    }
+    if (s != TFFR_OK) {
+        tffr_destroy(p);
+        return s;
+    }
+    *out = p;
+    return TFFR_OK;
+}
+
+int tffr_destroy(tffr_plan_t p) {
+    if (!p) return TFFR_OK;
+    cudaStreamSynchronize(p->stream);
+    release(p->twx); release(p->twy); release(p->T); release(p->deap_x); release(p->deap_y);
+    release(p->d_small); release(p->d_kept);
+    release(p->keep_x); release(p->keep_y); release(p->lx); release(p->ly); release(p->fx); release(p->fy);
+    release(p->D); release(p->run_start); release(p->tiles);
+    release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly); release(p->bucket_rows);
+    release(p->bucket_start); release(p->row_fy); release(p->row_off); release(p->R);
+    release(p->perm); release(p->slx); release(p->cursor); release(p->sfx); release(p->sfy); release(p->sD);
+    release(p->acc);
+    for (auto& sp : p->prof)
+        for (cudaEvent_t e : sp.ev) cudaEventDestroy(e);
+    delete p;
+    return TFFR_OK;
+}
+
+int tffr_plan_get_info(tffr_plan_t p, tffr_plan_info* info) {
+    if (!p || !info) return TFFR_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->Mx = p->Mx;
+    info->My = p->My;
+    info->nx = p->nx;
+    info->ny = p->ny;
+    info->width = p->w;
+    info->beta = p->beta;
+    info->N = p->have_points ? p->N : 0;
+    info->layout = p->have_points ? p->layout : 0;
+    const bool rows = p->have_points && p->layout == TFFR_POINTS_ROWS;
+    info->n_rows = rows ? p->P : 0;
+    info->row_cells = rows ? p->R_cells : 0;
+    info->max_row_cells = rows ? p->max_len : 0;
+    info->n_kept = p->have_weights ? p->n_kept : -1;
+    info->device_bytes = p->device_bytes;
+    info->kernel_launches = p->launches;
+    return TFFR_OK;
+}
+
+int tffr_profile(tffr_plan_t p, int enable) {
+    if (!p) return TFFR_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(p->stream));
+    for (auto& sp : p->prof) sp.n = 0;
+    p->prof_on = enable != 0;
+    return TFFR_OK;
+}
+
+int tffr_profile_read(tffr_plan_t p, double* ms, int64_t* count, int nstages) {
+    if (!p || nstages < 0 || nstages > TFFR_NUM_STAGES) return TFFR_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(p->stream));
+    for (int st = 0; st < nstages; ++st) {
+        const StageProf& sp = p->prof[st];
+        double tot = 0.0;
+        for (int64_t i = 0; i < sp.n; ++i) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, sp.ev[2 * i], sp.ev[2 * i + 1]));
+            tot += t;
+        }
+        if (ms) ms[st] = tot;
+        if (count) count[st] = sp.n;
+    }
+    return TFFR_OK;
+}
+
+int tffr_set_points(tffr_plan_t p, int64_t N, const double* lam_x, const double* lam_y) {
+    if (!p) return TFFR_ERR_INVALID_ARG;
+    p->last_error.clear();
+    if (N < 0 || N >= (int64_t)0x7fffffff) return fail(p, TFFR_ERR_INVALID_ARG, "N out of range");
+    if (N > 0 && (!lam_x || !lam_y)) return fail(p, TFFR_ERR_INVALID_ARG, "NULL coordinates");
+    p->have_points = false;
+    p->have_weights = false;
+    p->n_kept = -1;
+    p->N = N;
+    if (N == 0) {
+        p->layout = TFFR_POINTS_GENERAL;
+        p->P = 0;
+        p->have_points = true;
+        return TFFR_OK;
+    }
+    CK(grow(p, p->keep_x, N));
+    CK(grow(p, p->keep_y, N));
+    CK(grow(p, p->lx, N));
+    CK(grow(p, p->ly, N));
+    CK(grow(p, p->fx, N));
+    CK(grow(p, p->fy, N));
+    CK(grow(p, p->run_start, N));
+    CK(grow(p, p->D, N));
+    STAGE_BEGIN(TFFR_STAGE_POINTS);
+    CK(cudaMemsetAsync(p->d_small.ptr, 0, 4 * sizeof(int), p->stream));
+    k_prep_points<<<grid_for(N, 256), 256, 0, p->stream>>>(N, lam_x, lam_y, p->keep_x.ptr, p->keep_y.ptr,
+                                                          p->lx.ptr, p->fx.ptr, p->ly.ptr, p->fy.ptr,
+                                                          p->run_start.ptr, p->d_small.ptr);
+    CK_LAUNCH("k_prep_points");
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, p->d_small.ptr, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+    if (err) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite coordinate or |lam| >= 2^28");
+
+    int layout = p->layout_hint;
+    if (layout == TFFR_POINTS_AUTO) {
+        int P = 0;
+        int s = compact_run_starts(p, N, &P, false);
+        if (s != TFFR_OK) return s;
+        layout = (N >= 8 * (int64_t)P) ? TFFR_POINTS_ROWS : TFFR_POINTS_GENERAL;
+    }
+    p->layout = layout;
+    const int s = (layout == TFFR_POINTS_ROWS) ? build_rows(p) : build_general(p);
+    if (s != TFFR_OK) return s;
+    STAGE_END(TFFR_STAGE_POINTS);
+    p->have_points = true;
+    return TFFR_OK;
+}
+
+int tffr_weights(tffr_plan_t p, const tffr_weight_opts* opts, float* D_out, int64_t* n_kept) {
+    if (!p) return TFFR_ERR_INVALID_ARG;
+    p->last_error.clear();
+    if (!p->have_points) return fail(p, TFFR_ERR_NOT_READY, "tffr_weights before tffr_set_points");
+    tffr_weight_opts o;
+    tffr_default_weight_opts(&o);
+    if (opts) o = *opts;
+    if (o.mode < TFFR_WEIGHTS_TFFR || o.mode > TFFR_WEIGHTS_USER) return fail(p, TFFR_ERR_INVALID_ARG, "mode");
+    if (!(o.q > 0) || !(o.q < 1e6) || !(o.a >= 0) || !(o.a < 1e3) || !(o.tau == o.tau))
+        return fail(p, TFFR_ERR_INVALID_ARG, "a, q or tau out of range");
+    if (o.mode == TFFR_WEIGHTS_USER && !o.user_D && p->N > 0) return fail(p, TFFR_ERR_INVALID_ARG, "user_D");
+    const int64_t N = p->N;
+    p->n_kept = -1;
+    if (N > 0) {
+        WeightParams wp;
+        wp.mode = o.mode;
+        wp.separable = o.separable ? 1 : 0;
+        wp.a = o.a;
+        wp.q = o.q;
+        wp.tau = o.tau;
+        wp.e_minus = std::exp(-o.a / 2.0);
+        wp.e_plus = std::exp(o.a / 2.0);
+        wp.user_D = o.user_D;
+        STAGE_BEGIN(TFFR_STAGE_WEIGHTS);
+        CK(cudaMemsetAsync(p->d_kept.ptr, 0, sizeof(unsigned long long), p->stream));
+        k_weights<<<grid_for(N, 256), 256, 0, p->stream>>>(N, p->keep_x.ptr, p->keep_y.ptr, p->Mx, p->My, wp,
+                                                          p->D.ptr, p->d_kept.ptr);
+        CK_LAUNCH("k_weights");
+        if (p->layout == TFFR_POINTS_GENERAL) {
+            k_gather_weights<<<grid_for(N, 256), 256, 0, p->stream>>>(N, p->perm.ptr, p->D.ptr, p->sD.ptr);
+            CK_LAUNCH("k_gather_weights");
+        }
+        STAGE_END(TFFR_STAGE_WEIGHTS);
+        if (D_out)
+            CK(cudaMemcpyAsync(D_out, p->D.ptr, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+    }
+    if (n_kept) {
+        unsigned long long k = 0;
+        if (N > 0) {
+            CK(cudaMemcpyAsync(&k, p->d_kept.ptr, sizeof(k), cudaMemcpyDeviceToHost, p->stream));
+            CK(cudaStreamSynchronize(p->stream));
+        }
+        *n_kept = (int64_t)k;
+        p->n_kept = (int64_t)k;
+    }
+    p->have_weights = true;
+    return TFFR_OK;
+}
+
+int tffr_adjoint(tffr_plan_t p, const void* values, void* image) {
+    if (!p) return TFFR_ERR_INVALID_ARG;
+    p->last_error.clear();
+    if (!p->have_points || !p->have_weights) return fail(p, TFFR_ERR_NOT_READY, "adjoint before points/weights");
+    if (!image || (p->N > 0 && !values)) return fail(p, TFFR_ERR_INVALID_ARG, "NULL pointer");
+    float2* img = reinterpret_cast<float2*>(image);
+    if (p->N == 0) {
+        CK(cudaMemsetAsync(img, 0, (size_t)p->Mx * p->My * sizeof(float2), p->stream));
+        return TFFR_OK;
+    }
+    switch (p->values) {
+        case TFFR_VALUES_C64: return adjoint_impl<float2>(p, values, img);
+        case TFFR_VALUES_C128: return adjoint_impl<double2>(p, values, img);
+        case TFFR_VALUES_F16: return adjoint_impl<__half2>(p, values, img);
+        default: return adjoint_impl<__nv_bfloat162>(p, values, img);
+    }
+}
+
+int tffr_forward(tffr_plan_t p, const void* image, void* values, int apply_weights) {
+    if (!p) return TFFR_ERR_INVALID_ARG;
+    p->last_error.clear();
+    if (!p->have_points || !p->have_weights) return fail(p, TFFR_ERR_NOT_READY, "forward before points/weights");
+    if (!image || (p->N > 0 && !values)) return fail(p, TFFR_ERR_INVALID_ARG, "NULL pointer");
+    if (p->N == 0) return TFFR_OK;
+    const float2* img = reinterpret_cast<const float2*>(image);
+    switch (p->values) {
+        case TFFR_VALUES_C128: return forward_impl<double2>(p, img, values, apply_weights);
+        default: return forward_impl<float2>(p, img, values, apply_weights);
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,272 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerance: relative L2 error <= 1e-5 for the FP32 path (complex64 or complex128
+sample storage), measured against the direct FP64 sum.  The spreading kernel
+alone contributes ~5e-6 at width 6 on stripmap geometry (~1e-5 on uniform
+random points, which the tests therefore run at width 8, ~1e-7).
+Reduced-precision sample storage has its own bound from its rounding unit.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import make_workload, random_points, scene_samples, stolt_points
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__ as g
+    g.build()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel_l2(got, ref):
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def gpu_adjoint(lx, ly, vals, Mx, My=None, values="c64", layout="auto", width=6, wkw=None):
+    from paper_1910_10908_gb300 import Plan
+    My = Mx if My is None else My
+    with Plan(Mx, My, values=values, layout=layout, width=width) as plan:
+        plan.set_points(dev(lx), dev(ly))
+        D = torch.empty(lx.shape[0], dtype=torch.float32, device="cuda")
+        kept = plan.weights(D_out=D, **(wkw or {}))
+        img = plan.adjoint(vals if isinstance(vals, torch.Tensor) else dev(vals))
+        torch.cuda.synchronize()
+        info = plan.info()
+        return img.cpu().numpy().astype(np.complex128), D.cpu().numpy().astype(np.float64), kept, info
+
+
+def stolt_scene(P, F, M, seed=11, noise=True):
+    lx, ly, rp = stolt_points(P, F, M)
+    v, _ = scene_samples(lx, ly, rp, n_targets=50, speckle_sigma=0.1, snr_db=20.0 if noise else None, seed=seed)
+    return lx, ly, rp, v
+
+
+def test_tiny_config_complex128_full_image():
+    wl = make_workload("tiny_64")
+    img, D, kept, info = gpu_adjoint(wl.lam_x, wl.lam_y, wl.values, wl.M, values="c128")
+    Dref = oracle.tffr_weights(wl.lam_x, wl.M)
+    assert info["layout"] == 2 and info["n_rows"] == 64
+    assert np.max(np.abs(D - Dref)) < 2e-7
+    assert kept == np.count_nonzero(Dref)
+    ref = oracle.adjoint_image(wl.lam_x, wl.lam_y, wl.values, Dref, wl.M, wl.M)
+    assert rel_l2(img, ref) <= TOL
+
+
+@pytest.mark.parametrize("layout", ["auto", "general"])
+def test_stolt_128_ragged_rows_full_image(layout):
+    lx, ly, rp, v = stolt_scene(128, 256, 128)
+    lens = np.diff(rp)
+    assert lens.min() < lens.max()             # evanescent pairs make the outer rows shorter
+    img, D, kept, info = gpu_adjoint(lx, ly, v.astype(np.complex64), 128, layout=layout)
+    assert info["layout"] == (2 if layout == "auto" else 1)
+    Dref = oracle.tffr_weights(lx, 128)
+    ref = oracle.adjoint_image(lx, ly, v.astype(np.complex64), Dref, 128, 128)
+    assert rel_l2(img, ref) <= TOL
+
+
+def test_non_square_image():
+    lx, ly, rp = stolt_points(64, 200, 128)
+    ly = ly * (32 / 128)                       # azimuth band of a 32-row image
+    g = np.random.default_rng(4)
+    v = (g.standard_normal(lx.shape[0]) + 1j * g.standard_normal(lx.shape[0])).astype(np.complex64)
+    # white sample values put energy at the image edge, where width 6 sits at ~1.1e-5: use width 8
+    img, _, _, info = gpu_adjoint(lx, ly, v, 128, 32, width=8)
+    assert img.shape == (32, 128) and info["layout"] == 2
+    ref = oracle.adjoint_image(lx, ly, v, oracle.tffr_weights(lx, 128), 128, 32)
+    assert rel_l2(img, ref) <= TOL
+
+
+@pytest.mark.parametrize("M,N,extent", [(64, 3000, 0.45), (128, 20000, 0.5), (16, 100, 0.5)])
+def test_general_random_points_width8(M, N, extent):
+    lx, ly, v = random_points(N, M, seed=M + N, extent=extent)
+    img, D, _, info = gpu_adjoint(lx, ly, v, M, width=8)
+    assert info["layout"] == 1
+    ref = oracle.adjoint_image(lx, ly, v, oracle.tffr_weights(lx, M), M, M)
+    assert rel_l2(img, ref) <= TOL
+
+
+def test_points_on_cell_edges_and_grid_boundary():
+    M = 32
+    g = np.random.default_rng(9)
+    lx = np.concatenate([np.arange(-16, 16, 0.5), [-16.0, 15.999999999, 0.0, -0.25]])
+    ly = np.concatenate([np.full(64, 3.5), [-16.0, -16.0, 15.75, 0.0]])
+    v = (g.standard_normal(lx.shape[0]) + 1j * g.standard_normal(lx.shape[0])).astype(np.complex64)
+    img, _, _, _ = gpu_adjoint(lx, ly, v, M, width=8, layout="general")
+    ref = oracle.adjoint_image(lx, ly, v, oracle.tffr_weights(lx, M), M, M)
+    assert rel_l2(img, ref) <= TOL
+
+
+def test_rows_layout_forced_on_short_rows():
+    lx, ly, rp = stolt_points(48, 6, 64)       # 6 samples per pulse row
+    g = np.random.default_rng(1)
+    v = (g.standard_normal(lx.shape[0]) + 1j * g.standard_normal(lx.shape[0])).astype(np.complex64)
+    img, _, _, info = gpu_adjoint(lx, ly, v, 64, layout="rows", width=8)
+    assert info["layout"] == 2 and info["n_rows"] == 48
+    ref = oracle.adjoint_image(lx, ly, v, oracle.tffr_weights(lx, 64), 64, 64)
+    assert rel_l2(img, ref) <= TOL
+
+
+def test_stripmap_1024_sampled_pixels():
+    wl = make_workload("stripmap_1024")
+    img, D, kept, info = gpu_adjoint(wl.lam_x, wl.lam_y, wl.values, wl.M)
+    assert info["n_rows"] == 512 and kept == wl.N
+    Dref = oracle.tffr_weights(wl.lam_x, wl.M)
+    assert np.max(np.abs(D - Dref)) < 2e-7
+    g = np.random.default_rng(21)
+    jx = np.concatenate([g.integers(0, wl.M, 160), np.repeat(np.arange(504, 520), 16)])
+    jy = np.concatenate([g.integers(0, wl.M, 160), np.tile(np.arange(504, 520), 16)])
+    ref = oracle.adjoint_pixels(wl.lam_x, wl.lam_y, wl.values, Dref, wl.M, wl.M, jx, jy)
+    assert rel_l2(img[jy, jx], ref) <= TOL
+
+
+def test_stripmap_4096_sampled_pixels_bench_configuration():
+    wl = make_workload("stripmap_4096")
+    img, D, kept, info = gpu_adjoint(wl.lam_x, wl.lam_y, wl.values, wl.M)
+    assert info["layout"] == 2 and info["n_rows"] == 4096 and kept == wl.N
+    g = np.random.default_rng(22)
+    n = 48
+    jx, jy = g.integers(0, wl.M, n), g.integers(0, wl.M, n)
+    # the targets sit at pixel-scale positions: include the brightest pixels too
+    flat = np.argsort(np.abs(img).ravel())[-16:]
+    jy = np.concatenate([jy, flat // wl.M])
+    jx = np.concatenate([jx, flat % wl.M])
+    idx = g.integers(0, wl.N, 200000)
+    assert np.max(np.abs(D[idx] - oracle.tffr_weights(wl.lam_x[idx], wl.M))) < 2e-7
+    Dref = oracle.tffr_weights(wl.lam_x, wl.M)
+    ref = oracle.adjoint_pixels(wl.lam_x, wl.lam_y, wl.values, Dref, wl.M, wl.M, jx, jy)
+    assert rel_l2(img[jy, jx], ref) <= TOL
+
+
+@pytest.mark.parametrize("apply_weights", [True, False])
+def test_forward_twin_vs_oracle(apply_weights):
+    from paper_1910_10908_gb300 import Plan
+    lx, ly, rp, _ = stolt_scene(128, 256, 128)
+    g = np.random.default_rng(3)
+    f = (g.standard_normal((128, 128)) + 1j * g.standard_normal((128, 128))).astype(np.complex64)
+    with Plan(128) as plan:
+        plan.set_points(dev(lx), dev(ly))
+        plan.weights(tau=1.02)
+        y = plan.forward(dev(f), apply_weights=apply_weights).cpu().numpy()
+    idx = g.integers(0, lx.shape[0], 400)
+    Dref = oracle.tffr_weights(lx, 128, tau=1.02)
+    ref = oracle.forward_samples(lx, ly, f, Dref if apply_weights else None, idx=idx)
+    assert rel_l2(y[idx], ref) <= TOL
+
+
+@pytest.mark.parametrize("layout", ["auto", "general"])
+def test_adjointness_on_the_gpu(layout):
+    from paper_1910_10908_gb300 import Plan
+    lx, ly, _, _ = stolt_scene(96, 160, 64)
+    g = np.random.default_rng(8)
+    y = (g.standard_normal(lx.shape[0]) + 1j * g.standard_normal(lx.shape[0])).astype(np.complex64)
+    f = (g.standard_normal((64, 64)) + 1j * g.standard_normal((64, 64))).astype(np.complex64)
+    with Plan(64, layout=layout) as plan:
+        plan.set_points(dev(lx), dev(ly))
+        plan.weights(tau=1.02)
+        Ay = plan.adjoint(dev(y)).cpu().numpy().astype(np.complex128)
+        Af = plan.forward(dev(f)).cpu().numpy().astype(np.complex128)
+    lhs = np.vdot(f.astype(np.complex128), Ay)
+    rhs = np.vdot(Af, y.astype(np.complex128))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_empty_and_fully_thresholded():
+    from paper_1910_10908_gb300 import Plan
+    with Plan(32) as plan:
+        e = torch.empty(0, dtype=torch.float64, device="cuda")
+        plan.set_points(e, e)
+        assert plan.weights() == 0
+        img = plan.adjoint(torch.empty(0, dtype=torch.complex64, device="cuda"))
+        assert torch.count_nonzero(img).item() == 0
+    lx, ly, _, v = stolt_scene(32, 32, 32)
+    with Plan(32) as plan:
+        plan.set_points(dev(lx), dev(ly))
+        assert plan.weights(tau=2.0) == 0
+        img = plan.adjoint(dev(v.astype(np.complex64)))
+        assert torch.count_nonzero(img).item() == 0
+
+
+def test_errors_are_reported():
+    from paper_1910_10908_gb300 import Plan, TffrError
+    lx, ly, _, v = stolt_scene(32, 32, 32)
+    with Plan(32) as plan:
+        with pytest.raises(TffrError) as e:
+            plan.adjoint(dev(v.astype(np.complex64)))
+        assert e.value.status == 2
+        bad = lx.copy()
+        bad[7] = np.nan
+        with pytest.raises(TffrError) as e:
+            plan.set_points(dev(bad), dev(ly))
+        assert e.value.status == 1
+        bad[7] = 3e8
+        with pytest.raises(TffrError) as e:
+            plan.set_points(dev(bad), dev(ly))
+        assert e.value.status == 1
+        with pytest.raises(TffrError) as e:
+            plan.weights()
+        assert e.value.status == 2
+        plan.set_points(dev(lx), dev(ly))        # the plan recovers
+        plan.weights()
+        plan.adjoint(dev(v.astype(np.complex64)))
+        with pytest.raises(TffrError) as e:
+            plan.weights(q=-1.0)
+        assert e.value.status == 1
+
+
+@pytest.mark.parametrize("kw", [dict(mode="unit"), dict(tau=1.02), dict(tau=1.05), dict(separable=True, tau=1.0),
+                                dict(a=0.5, q=2.5, tau=0.97)])
+def test_weight_modes_vs_oracle(kw):
+    lx, ly, _, v = stolt_scene(64, 96, 64)
+    img, D, kept, _ = gpu_adjoint(lx, ly, v.astype(np.complex64), 64, wkw=kw)
+    if kw.get("mode") == "unit":
+        Dref = np.ones_like(lx)
+    else:
+        okw = {k: kw[k] for k in ("tau", "a", "q") if k in kw}
+        Dref = oracle.tffr_weights(lx, 64, lam_y=ly, My=64, separable=kw.get("separable", False), **okw)
+    assert kept == np.count_nonzero(Dref)
+    assert np.max(np.abs(D - Dref)) < 2e-7
+    if kept:
+        ref = oracle.adjoint_image(lx, ly, v.astype(np.complex64), Dref, 64, 64)
+        assert rel_l2(img, ref) <= TOL
+
+
+def test_user_weights():
+    lx, ly, _, v = stolt_scene(64, 96, 64)
+    g = np.random.default_rng(5)
+    Du = g.uniform(0.5, 1.5, lx.shape[0]).astype(np.float32)
+    Du[::7] = 0.0
+    img, D, kept, _ = gpu_adjoint(lx, ly, v.astype(np.complex64), 64,
+                                  wkw=dict(mode="user", user_D=dev(Du)))
+    assert np.array_equal(D.astype(np.float32), Du) and kept == np.count_nonzero(Du)
+    ref = oracle.adjoint_image(lx, ly, v.astype(np.complex64), Du.astype(np.float64), 64, 64)
+    assert rel_l2(img, ref) <= TOL
+
+
+@pytest.mark.parametrize("values,bound", [("f16", 1e-3), ("bf16", 8e-3)])
+def test_reduced_precision_sample_storage(values, bound):
+    lx, ly, _, v = stolt_scene(128, 256, 128)
+    if values == "f16":
+        t = dev(v.astype(np.complex64)).to(torch.complex32)
+        stored = t.to(torch.complex64).cpu().numpy()
+    else:
+        t = torch.view_as_real(dev(v.astype(np.complex64))).to(torch.bfloat16).contiguous()
+        stored = torch.view_as_complex(t.float().contiguous()).cpu().numpy()
+    img, _, _, _ = gpu_adjoint(lx, ly, t, 128, values=values)
+    Dref = oracle.tffr_weights(lx, 128)
+    ref = oracle.adjoint_image(lx, ly, v, Dref, 128, 128)
+    err = rel_l2(img, ref)
+    assert err <= bound
+    # against the rounded samples themselves the FP32 path is as exact as ever
+    ref_stored = oracle.adjoint_image(lx, ly, stored, Dref, 128, 128)
+    assert rel_l2(img, ref_stored) <= TOL
