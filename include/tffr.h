@@ -26,8 +26,11 @@
  *    tffr_destroy.
  *  - Every call is ordered on the plan's stream.  tffr_adjoint and
  *    tffr_forward never synchronise; tffr_set_points synchronises the stream
- *    before it returns (the caller may free lam_x / lam_y afterwards);
- *    tffr_weights synchronises only when n_kept is requested.
+ *    before it returns; tffr_weights synchronises only when n_kept is
+ *    requested.
+ *  - The coordinate arrays given to tffr_set_points are used in place (no
+ *    copy): they must stay valid and unchanged until the next
+ *    tffr_set_points or tffr_destroy on that plan.
  *  - Return value: a tffr_status.  On TFFR_ERR_CUDA the CUDA error text is
  *    available from tffr_last_error(plan).
  *  - A plan is not thread-safe: calls on one plan must not overlap.
@@ -141,9 +144,12 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
 
 /*
  * Set the N sample frequencies (device double[N] each, grid units; Sec. II.A:
- * lam_x range, lam_y azimuth).  Reduces each coordinate in FP64 to a fine-grid
- * cell and an FP32 offset, finds the pulse rows (runs of bit-equal lam_y) or
- * buckets the samples by fine-grid row, and sizes the per-row buffers.
+ * lam_x range, lam_y azimuth).  The arrays are kept by pointer (see above).
+ * Finds the pulse rows (runs of bit-equal lam_y; layout ROWS) or buckets the
+ * samples by fine-grid row (layout GENERAL) and sizes the per-row buffers.
+ * Every later call reduces a coordinate exactly from its FP64 bits to a fine
+ * cell floor(2 lam) and an FP32 offset (at 8192 cells an FP32 coordinate
+ * would keep only ~1e-3 cell).
  * N = 0 is allowed (adjoint then returns a zero image).  Invalidates the weights.
  * Errors: INVALID_ARG for N < 0, N >= 2^31, NULL pointers with N > 0, or any
  * |lam| >= 2^28 or non-finite coordinate; OOM; CUDA.  Synchronises the stream.
@@ -151,11 +157,15 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
 int tffr_set_points(tffr_plan_t plan, int64_t N, const double* lam_x, const double* lam_y);
 
 /*
- * Compute the frame weights D_n (Algorithm 1, lines forming W, Psi and
- * D = R_tau((W Psi)^+), diagonal only) in FP64 and keep them, as FP32, in the
- * plan.  opts may be NULL (defaults).  D_out (nullable, device float[N])
- * receives a copy; n_kept (nullable, host) receives the count of D_n != 0 and
- * makes the call synchronise.
+ * Set the frame weights D_n (Algorithm 1: W, Psi and D = R_tau((W Psi)^+),
+ * diagonal only).  The plan fits the diagonal G(delta) of the fractional
+ * offset once in FP64 and the kernels evaluate D_n inline (FP32 polynomial,
+ * with the closed form in FP64 deciding every sample near tau, near the grid
+ * edge or on a truncation breakpoint), so the threshold decision is an FP64
+ * one.  opts may be NULL (defaults).  USER weights are copied.  D_out
+ * (nullable, device float[N]) receives D; n_kept (nullable, host) receives the
+ * count of D_n != 0; either makes the call evaluate D for every sample, and
+ * n_kept makes it synchronise.
  * Errors: NOT_READY before tffr_set_points; INVALID_ARG for bad options
  * (q <= 0, a < 0, unknown mode, USER mode without user_D); CUDA.
  */

@@ -80,6 +80,7 @@ def tffr_plan(Mx: int, My: int, *, width: int = 6, beta: float = 0.0, values: st
 
 
 def tffr_set_points(plan, lam_x: torch.Tensor, lam_y: torch.Tensor):
+    """The library keeps the coordinate pointers: the tensors must outlive their use by the plan."""
     if lam_x.shape != lam_y.shape or lam_x.dim() != 1:
         raise ValueError("lam_x and lam_y must be 1-D of equal length")
     N = lam_x.shape[0]
@@ -164,7 +165,9 @@ class Plan:
         return self._h
 
     def set_points(self, lam_x: torch.Tensor, lam_y: torch.Tensor) -> "Plan":
+        """The plan reads the coordinate tensors in place: keep references to them."""
         tffr_set_points(self._handle(), lam_x, lam_y)
+        self._coords = (lam_x, lam_y)
         self.N = int(lam_x.shape[0])
         return self
 

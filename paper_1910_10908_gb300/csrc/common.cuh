@@ -21,6 +21,70 @@ __device__ __forceinline__ int wrapmod(int c, int n) {  // n is a power of two
     return c & (n - 1);
 }
 
+// floor(2v) and 2v - floor(2v) from the FP64 bit pattern, with integer
+// operations only (FP64 arithmetic runs at a small fraction of the FP32 rate
+// on this GPU).  The fraction is rounded to FP32 (it may round up to 1.0f,
+// which places the sample on the next cell edge: the taps stay consistent).
+// Returns false for |v| >= 2^28, infinities and NaN.
+__device__ __forceinline__ bool fine_coord(double v, int& cell, float& frac) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    cell = 0;
+    frac = 0.0f;
+    if (e > 1050) return false;                 // |v| >= 2^28 (also inf, NaN)
+    if (e == 0) return true;                    // zero or subnormal
+    const bool neg = (b >> 63) != 0ull;
+    const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int sh = 1074 - e;                    // |2v| = m * 2^-sh, sh >= 24
+    const unsigned long long I = (sh >= 64) ? 0ull : (m >> sh);
+    const unsigned long long F = (sh >= 64) ? m : (m & ((1ull << sh) - 1ull));
+    const float scale = (sh <= 126) ? __int_as_float((127 - sh) << 23) : 0.0f;
+    if (!neg) {
+        cell = (int)I;
+        frac = __ull2float_rn(F) * scale;
+    } else if (F == 0ull) {
+        cell = -(int)I;
+    } else {
+        cell = -(int)I - 1;
+        frac = (sh >= 64) ? 1.0f - __ull2float_rn(F) * scale : __ull2float_rn((1ull << sh) - F) * scale;
+    }
+    return true;
+}
+
+// Spreading-kernel taps as polynomials in t = 2f - 1 (f the fine-cell offset
+// in [0, 1]): tap s (fine cell floor(u) - (w/2 - 1) + s) has weight
+// P_s(t) = sum_k c[s][k] t^k, fitted at plan time in FP64 to the ES kernel
+// phi(s - (w/2 - 1) - f).  phi is even, so P_{w-1-s}(t) = P_s(-t).
+constexpr int kTapCoefs = 11;                   // degree 10
+struct TapPoly {
+    float c[8][kTapCoefs];
+};
+
+__device__ __forceinline__ float tap_eval(const TapPoly& P, int s, float t) {
+    float a = P.c[s][kTapCoefs - 1];
+#pragma unroll
+    for (int k = kTapCoefs - 2; k >= 0; --k) a = fmaf(a, t, P.c[s][k]);
+    return a;
+}
+
+// All W taps; mirrored pairs share the even and odd parts in t^2.
+template <int W>
+__device__ __forceinline__ void taps_all(const TapPoly& P, float f, float (&wt)[W]) {
+    const float t = 2.0f * f - 1.0f;
+    const float t2 = t * t;
+#pragma unroll
+    for (int s = 0; s < W / 2; ++s) {
+        float e = P.c[s][kTapCoefs - 1];        // degree 10: even part has c0, c2, ..., c10
+#pragma unroll
+        for (int k = kTapCoefs - 3; k >= 0; k -= 2) e = fmaf(e, t2, P.c[s][k]);
+        float o = P.c[s][kTapCoefs - 2];        // odd part: c1, c3, ..., c9
+#pragma unroll
+        for (int k = kTapCoefs - 4; k >= 1; k -= 2) o = fmaf(o, t2, P.c[s][k]);
+        wt[s] = fmaf(t, o, e);
+        wt[W - 1 - s] = fmaf(-t, o, e);
+    }
+}
+
 // Exponential-of-semicircle spreading kernel of width w (fine-grid cells):
 //   phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)) for |z| < w/2, 0 otherwise.
 __device__ __forceinline__ float es_kernel(float z, float beta, float two_over_w) {

@@ -57,16 +57,28 @@ __device__ __forceinline__ bool row_has_taps(const int* bucket_start, int r, int
     return false;
 }
 
-template <bool ROWS, typename VT>
+// Shared tail of the adjoint row pass: FFT along x, keep the Mx wanted modes,
+// deapodise, store row r of T.
+__device__ __forceinline__ void adj_row_finish(float2* sm, int r, int nx, int lognx, int ny, int Mx,
+                                               const float2* __restrict__ twx, const float* __restrict__ deap_x,
+                                               float2* __restrict__ T) {
+    fft_smem(sm, nx, lognx, twx, +1.0f);
+    const int half = Mx >> 1;
+    for (int jx = threadIdx.x; jx < Mx; jx += kFftThreads) {
+        const float2 v = sm[pad16(wrapmod(jx - half, nx))];
+        T[t_index(jx, r, ny)] = cscale(v, deap_x[jx]);
+    }
+}
+
+// Pass 1 of the adjoint, pulse rows: fine row r = sum over the pulse rows p
+// whose azimuth taps reach r of phi_y(r - v_p) R_p (shifted to its x cells).
 __global__ void __launch_bounds__(kFftThreads)
-k_adj_rows(RowsView rv, GeneralView gv, const float2* __restrict__ R, const void* __restrict__ values, int nx,
-           int lognx, int ny, int Mx, int w, float beta, const float2* __restrict__ twx,
-           const float* __restrict__ deap_x, float2* __restrict__ T) {
+k_adj_rows(RowsView rv, const float2* __restrict__ R, int nx, int lognx, int ny, int Mx, int w, TapPoly tp,
+           const float2* __restrict__ twx, const float* __restrict__ deap_x, float2* __restrict__ T) {
     extern __shared__ float2 sm[];
     const int r = blockIdx.x;
     const int tid = threadIdx.x;
-    const int* bstart = ROWS ? rv.bucket_start : gv.bucket_start;
-    if (!row_has_taps(bstart, r, ny, w)) {
+    if (!row_has_taps(rv.bucket_start, r, ny, w)) {
         for (int jx = tid; jx < Mx; jx += kFftThreads) T[t_index(jx, r, ny)] = make_float2(0.f, 0.f);
         return;
     }
@@ -74,44 +86,54 @@ k_adj_rows(RowsView rv, GeneralView gv, const float2* __restrict__ R, const void
     for (int i = tid; i < nsm; i += kFftThreads) sm[i] = make_float2(0.f, 0.f);
     __syncthreads();
     const int h = w / 2;
-    const float two_over_w = 2.0f / (float)w;
     for (int t = 0; t < w; ++t) {
         const int b = wrapmod(r + h - 1 - t, ny);
-        const int q0 = bstart[b], q1 = bstart[b + 1];
-        if (ROWS) {
-            for (int q = q0; q < q1; ++q) {
-                const int p = rv.bucket_rows[q];
-                const float wy = es_kernel((float)(t - (h - 1)) - rv.row_fy[p], beta, two_over_w);
-                if (wy == 0.0f) continue;
-                const int clo = rv.row_clo[p], len = rv.row_len[p];
-                const float2* Rp = R + rv.row_off[p];
-                for (int i = tid; i < len; i += kFftThreads) {
-                    const int c = wrapmod(clo + i, nx);
-                    atomic_add_f2_shared(&sm[pad16(c)], cscale(Rp[i], wy));
-                }
-            }
-        } else {
-            for (int q = q0 + tid; q < q1; q += kFftThreads) {
-                const float d = gv.sD[q];
-                if (d == 0.0f) continue;
-                const float wy = es_kernel((float)(t - (h - 1)) - gv.sfy[q], beta, two_over_w);
-                if (wy == 0.0f) continue;
-                const float2 v = cscale(ValueIO<VT>::load(values, gv.perm[q]), d * wy);
-                const int c0 = gv.slx[q] - (h - 1);
-                const float f = gv.sfx[q];
-                for (int s = 0; s < w; ++s) {
-                    const float wt = es_kernel((float)(s - (h - 1)) - f, beta, two_over_w);
-                    atomic_add_f2_shared(&sm[pad16(wrapmod(c0 + s, nx))], cscale(v, wt));
-                }
+        for (int q = rv.bucket_start[b]; q < rv.bucket_start[b + 1]; ++q) {
+            const int p = rv.bucket_rows[q];
+            const float wy = tap_eval(tp, t, 2.0f * rv.row_fy[p] - 1.0f);
+            const int clo = rv.row_clo[p], len = rv.row_len[p];
+            const float2* Rp = R + rv.row_off[p];
+            for (int i = tid; i < len; i += kFftThreads) {
+                const int c = wrapmod(clo + i, nx);
+                atomic_add_f2_shared(&sm[pad16(c)], cscale(Rp[i], wy));
             }
         }
     }
-    fft_smem(sm, nx, lognx, twx, +1.0f);
-    const int half = Mx >> 1;
-    for (int jx = tid; jx < Mx; jx += kFftThreads) {
-        const float2 v = sm[pad16(wrapmod(jx - half, nx))];
-        T[t_index(jx, r, ny)] = cscale(v, deap_x[jx]);
+    adj_row_finish(sm, r, nx, lognx, ny, Mx, twx, deap_x, T);
+}
+
+// Pass 1 of the adjoint, general points: the samples of the w buckets whose
+// taps reach fine row r are spread straight into the shared row.
+template <typename VT>
+__global__ void __launch_bounds__(kFftThreads)
+k_adj_rows_general(GeneralView gv, const void* __restrict__ values, int nx, int lognx, int ny, int Mx, int w,
+                   TapPoly tp, const float2* __restrict__ twx, const float* __restrict__ deap_x,
+                   float2* __restrict__ T) {
+    extern __shared__ float2 sm[];
+    const int r = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (!row_has_taps(gv.bucket_start, r, ny, w)) {
+        for (int jx = tid; jx < Mx; jx += kFftThreads) T[t_index(jx, r, ny)] = make_float2(0.f, 0.f);
+        return;
     }
+    const int nsm = nx + (nx >> 4);
+    for (int i = tid; i < nsm; i += kFftThreads) sm[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int h = w / 2;
+    for (int t = 0; t < w; ++t) {
+        const int b = wrapmod(r + h - 1 - t, ny);
+        for (int q = gv.bucket_start[b] + tid; q < gv.bucket_start[b + 1]; q += kFftThreads) {
+            const float d = gv.sD[q];
+            if (d == 0.0f) continue;
+            const float wy = tap_eval(tp, t, 2.0f * gv.sfy[q] - 1.0f);
+            const float2 v = cscale(ValueIO<VT>::load(values, gv.perm[q]), d * wy);
+            const int c0 = gv.slx[q] - (h - 1);
+            const float tx = 2.0f * gv.sfx[q] - 1.0f;
+            for (int s = 0; s < w; ++s)
+                atomic_add_f2_shared(&sm[pad16(wrapmod(c0 + s, nx))], cscale(v, tap_eval(tp, s, tx)));
+        }
+    }
+    adj_row_finish(sm, r, nx, lognx, ny, Mx, twx, deap_x, T);
 }
 
 __global__ void __launch_bounds__(kFftThreads)
@@ -151,7 +173,7 @@ k_fwd_cols(const float2* __restrict__ img, int ny, int logny, int My, int Mx, co
 template <bool ROWS>
 __global__ void __launch_bounds__(kFftThreads)
 k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int nx, int lognx, int ny, int Mx, int w,
-           float beta, const float2* __restrict__ twx, float2* __restrict__ R, float2* __restrict__ acc) {
+           TapPoly tp, const float2* __restrict__ twx, float2* __restrict__ R, float2* __restrict__ acc) {
     extern __shared__ float2 sm[];
     const int r = blockIdx.x;
     const int tid = threadIdx.x;
@@ -164,15 +186,13 @@ k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int nx, in
     for (int jx = tid; jx < Mx; jx += kFftThreads) sm[pad16(wrapmod(jx - half, nx))] = T[t_index(jx, r, ny)];
     fft_smem(sm, nx, lognx, twx, -1.0f);
     const int h = w / 2;
-    const float two_over_w = 2.0f / (float)w;
     for (int t = 0; t < w; ++t) {
         const int b = wrapmod(r + h - 1 - t, ny);
         const int q0 = bstart[b], q1 = bstart[b + 1];
         if (ROWS) {
             for (int q = q0; q < q1; ++q) {
                 const int p = rv.bucket_rows[q];
-                const float wy = es_kernel((float)(t - (h - 1)) - rv.row_fy[p], beta, two_over_w);
-                if (wy == 0.0f) continue;
+                const float wy = tap_eval(tp, t, 2.0f * rv.row_fy[p] - 1.0f);
                 const int clo = rv.row_clo[p], len = rv.row_len[p];
                 float2* Rp = R + rv.row_off[p];
                 for (int i = tid; i < len; i += kFftThreads) {
@@ -182,16 +202,15 @@ k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int nx, in
             }
         } else {
             for (int q = q0 + tid; q < q1; q += kFftThreads) {
-                const float wy = es_kernel((float)(t - (h - 1)) - gv.sfy[q], beta, two_over_w);
-                if (wy == 0.0f) continue;
+                const float wy = tap_eval(tp, t, 2.0f * gv.sfy[q] - 1.0f);
                 const int c0 = gv.slx[q] - (h - 1);
-                const float f = gv.sfx[q];
+                const float tx = 2.0f * gv.sfx[q] - 1.0f;
                 float2 a = make_float2(0.f, 0.f);
                 for (int s = 0; s < w; ++s) {
-                    const float wt = es_kernel((float)(s - (h - 1)) - f, beta, two_over_w);
+                    const float wt = tap_eval(tp, s, tx);
                     const float2 g = sm[pad16(wrapmod(c0 + s, nx))];
-                    a.x += wt * g.x;
-                    a.y += wt * g.y;
+                    a.x = fmaf(wt, g.x, a.x);
+                    a.y = fmaf(wt, g.y, a.y);
                 }
                 atomic_add_f2_global(&acc[q], cscale(a, wy));
             }

@@ -1,5 +1,5 @@
-// Point preparation (coordinate -> fine-grid cell + offset, pulse-row
-// detection, bucketing by grid row) and the tFFR frame weights.
+// Point preparation (pulse-row detection, bucketing by fine row) and the tFFR
+// frame weights.
 #pragma once
 
 #include "common.cuh"
@@ -7,45 +7,127 @@
 namespace tffr {
 
 // ---------------------------------------------------------------------------
-// Coordinates.  u = sigma * lam (sigma = 2) in fine-grid cells, unwrapped;
-// cell = floor(u) (int32), offset = u - cell in [0, 1] (FP32).  The reduction
-// runs in FP64: at 8192 cells an FP32 coordinate keeps only ~1e-3 of a cell.
-// A run start marks a sample whose lam_y differs (bitwise) from the previous
-// sample's: runs of equal lam_y are pulse rows (azimuth is uniform, Sec. II.A).
+// tFFR weights (Algorithm 1, Sec. III.B-C).  For a sample at frequency lam
+// (grid units) on an axis with an M-point Fourier grid l in [-M/2, M/2):
+//   w_hat(xi) = 2 [a + e^{-a/2}(-a cos(pi xi) + 2 pi xi sin(pi xi))] / (a^2 + 4 pi^2 xi^2)
+//   psi(eta)  = 2 [-a + e^{a/2}(a cos(pi eta) + 2 pi eta sin(pi eta))] / (a^2 + 4 pi^2 eta^2)
+//   G(lam)    = sum_{l on the grid, |lam - l| < q} psi(lam - l) w_hat(l - lam)
+//   D         = R_tau(1 / G)      (0 when G = 0; kept when 1/G >= tau)
+// These are the transforms of the window w(t) = exp(-a|t|) and of 1/w on the
+// centred domain t in [-1/2, 1/2] (Eq. (Psi); the window of Sec. IV).
+//
+// Away from the grid edges G depends only on the offset delta = lam - floor(lam)
+// and is symmetric about delta = 1/2, so the plan fits it once (FP64, on the
+// host) as polynomials in v = |delta - 1/2| and evaluates those in FP32 here.
+// Samples near the grid edges, on a breakpoint of the truncation, or with
+// 1/G within a guard band of tau take the closed form in FP64, so the
+// threshold decision is always made in FP64.
 // ---------------------------------------------------------------------------
-__global__ void k_prep_points(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y,
-                              double* __restrict__ keep_x, double* __restrict__ keep_y,
-                              int* __restrict__ lx, float* __restrict__ fx, int* __restrict__ ly,
-                              float* __restrict__ fy, uint8_t* __restrict__ run_start, int* __restrict__ err) {
-    const double lim = 268435456.0;   // |lam| < 2^28 keeps 2 lam in int32
-    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-        const double a = lam_x[n], b = lam_y[n];
-        keep_x[n] = a;
-        keep_y[n] = b;
-        int cx = 0, cy = 0;
-        float ox = 0.f, oy = 0.f;
-        if (!(fabs(a) < lim) || !(fabs(b) < lim)) {   // also catches NaN
-            atomicOr(err, 1);
-        } else {
-            const double u = 2.0 * a, v = 2.0 * b;
-            const double fu = floor(u), fv = floor(v);
-            cx = (int)fu;
-            cy = (int)fv;
-            ox = (float)(u - fu);
-            oy = (float)(v - fv);
-        }
-        lx[n] = cx;
-        fx[n] = ox;
-        ly[n] = cy;
-        fy[n] = oy;
-        uint8_t s = 1;
-        if (n > 0) s = (__double_as_longlong(b) != __double_as_longlong(lam_y[n - 1])) ? 1 : 0;
-        run_start[n] = s;
+constexpr int kGCoefs = 16;
+
+struct WeightArgs {
+    int mode;              // 0 tFFR, 1 unit, 2 user (per-sample array)
+    int separable;         // 0 range only, 1 product of range and azimuth factors
+    float tau, guard;      // threshold and relative guard band for the FP64 re-check
+    double tau_d;
+    // fitted G: piece 0 on v in [0, vb] as a polynomial in s = 2 (v/vb)^2 - 1;
+    // piece 1 on v in [vb, 1/2] as a polynomial in s = (2v - vb - 1/2)/(1/2 - vb)
+    float vb;
+    int n0, n1;
+    float c0[kGCoefs], c1[kGCoefs];
+    // closed-form parameters
+    double a, q, e_minus, e_plus;
+    int reach;             // ceil(q) + 1
+    const float* user_D;
+};
+
+__host__ __device__ inline double wt_sinpi(double x);
+__host__ __device__ inline double wt_cospi(double x);
+
+#ifdef __CUDA_ARCH__
+__device__ inline double wt_sinpi(double x) { return sinpi(x); }
+__device__ inline double wt_cospi(double x) { return cospi(x); }
+#else
+inline double wt_sinpi(double x) {
+    const double r = x - 2.0 * std::floor(0.5 * x);       // [0, 2)
+    return std::sin(3.14159265358979323846 * r);
+}
+inline double wt_cospi(double x) {
+    const double r = x - 2.0 * std::floor(0.5 * x);
+    return std::cos(3.14159265358979323846 * r);
+}
+#endif
+
+__host__ __device__ inline double window_hat(double xi, double a, double e_minus) {
+    const double two_pi = 6.283185307179586476925286766559;
+    const double num = a + e_minus * (-a * wt_cospi(xi) + two_pi * xi * wt_sinpi(xi));
+    return 2.0 * num / (a * a + two_pi * two_pi * xi * xi);
+}
+
+__host__ __device__ inline double inv_window_hat(double eta, double a, double e_plus) {
+    const double two_pi = 6.283185307179586476925286766559;
+    const double num = -a + e_plus * (a * wt_cospi(eta) + two_pi * eta * wt_sinpi(eta));
+    return 2.0 * num / (a * a + two_pi * two_pi * eta * eta);
+}
+
+// G(lam) with the grid truncation; M <= 0 means an unbounded grid.
+__host__ __device__ inline double diag_psi_w(double lam, int M, double a, double q, double e_minus,
+                                             double e_plus, int reach) {
+    const double base = floor(lam);
+    double G = 0.0;
+    for (int off = -reach; off <= reach; ++off) {
+        const double l = base + off;
+        if (M > 0 && (l < -(double)(M / 2) || l >= (double)(M - M / 2))) continue;
+        const double eta = lam - l;
+        if (!(fabs(eta) < q)) continue;
+        G += inv_window_hat(eta, a, e_plus) * window_hat(-eta, a, e_minus);
     }
+    return G;
+}
+
+__device__ __forceinline__ float horner(const float* c, int n, float s) {
+    float a = c[n - 1];
+    for (int k = n - 2; k >= 0; --k) a = fmaf(a, s, c[k]);
+    return a;
+}
+
+// FP32 G from the fine cell (floor(2 lam)) and offset; sets exact = true when the
+// closed form must decide instead (grid edge or truncation breakpoint).
+__device__ __forceinline__ float g_fitted(int cell, float f, int M, const WeightArgs& A, bool& exact) {
+    const int j0 = cell >> 1;                                    // floor(lam)
+    if (j0 - A.reach < -(M / 2) || j0 + A.reach >= M - M / 2) exact = true;
+    const float delta = 0.5f * ((float)(cell & 1) + f);          // lam - floor(lam), exact in FP32
+    const float v = fabsf(delta - 0.5f);
+    if (v == A.vb || v == 0.5f) exact = true;                    // on a breakpoint of the truncation
+    if (v < A.vb) {
+        const float r = v / A.vb;
+        return horner(A.c0, A.n0, 2.0f * r * r - 1.0f);
+    }
+    return horner(A.c1, A.n1, (2.0f * v - A.vb - 0.5f) / (0.5f - A.vb));
+}
+
+__device__ __noinline__ float weight_exact(double lam_x, double lam_y, int Mx, int My, const WeightArgs& A) {
+    double G = diag_psi_w(lam_x, Mx, A.a, A.q, A.e_minus, A.e_plus, A.reach);
+    if (A.separable) G *= diag_psi_w(lam_y, My, A.a, A.q, A.e_minus, A.e_plus, A.reach);
+    double d = (G != 0.0) ? 1.0 / G : 0.0;
+    if (!(d >= A.tau_d)) d = 0.0;
+    return (float)d;
+}
+
+// D_n in tFFR mode from the x cell/offset (and the y ones in separable mode).
+__device__ __forceinline__ float weight_tffr(double lam_x, int cx, float fx, double lam_y, int cy, float fy, int Mx,
+                                             int My, const WeightArgs& A) {
+    bool exact = false;
+    float G = g_fitted(cx, fx, Mx, A, exact);
+    if (A.separable) G *= g_fitted(cy, fy, My, A, exact);
+    const float d = (G != 0.0f) ? 1.0f / G : 0.0f;
+    if (!exact && fabsf(d - A.tau) > A.guard * fabsf(A.tau)) return (d >= A.tau) ? d : 0.0f;
+    return weight_exact(lam_x, lam_y, Mx, My, A);
 }
 
 // ---------------------------------------------------------------------------
-// Order-preserving compaction of run starts (three-pass block scan).
+// Pulse rows: runs of samples with bit-equal lam_y (azimuth is uniform,
+// Sec. II.A).  Order-preserving compaction of the run starts in three passes.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
@@ -77,15 +159,29 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int* tot
     return before;
 }
 
-__global__ void k_count_flags(int64_t N, const uint8_t* __restrict__ flag, int* __restrict__ tile_count) {
+__device__ __forceinline__ int run_start_flag(const double* __restrict__ lam_y, int64_t n) {
+    if (n == 0) return 1;
+    return __double_as_longlong(lam_y[n]) != __double_as_longlong(lam_y[n - 1]) ? 1 : 0;
+}
+
+// Per tile: number of run starts; also checks every lam_y (err bit 1).
+__global__ void k_count_runs(int64_t N, const double* __restrict__ lam_y, int* __restrict__ tile_count,
+                             int* __restrict__ err) {
     __shared__ int s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int c = 0;
+    bool bad = false;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const int64_t n = base + (int64_t)threadIdx.x * kScanItems + i;
-        if (n < N) c += flag[n];
+        if (n < N) {
+            c += run_start_flag(lam_y, n);
+            int cell;
+            float f;
+            bad |= !fine_coord(lam_y[n], cell, f);
+        }
     }
+    if (bad) atomicOr(err, 1);
     int total;
     block_exclusive_scan(c, s_warp, &total);
     if (threadIdx.x == 0) tile_count[blockIdx.x] = total;
@@ -106,46 +202,47 @@ __global__ void k_scan_tile_counts(int ntiles, int* __restrict__ counts, int* __
     if (threadIdx.x == 0) *sum = carry;
 }
 
-__global__ void k_emit_run_starts(int64_t N, const uint8_t* __restrict__ flag, const int* __restrict__ tile_off,
+__global__ void k_emit_run_starts(int64_t N, const double* __restrict__ lam_y, const int* __restrict__ tile_off,
                                   int* __restrict__ row_start) {
     __shared__ int s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int c = 0;
-    uint8_t f[kScanItems];
+    int f[kScanItems];
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const int64_t n = base + (int64_t)threadIdx.x * kScanItems + i;
-        f[i] = (n < N) ? flag[n] : 0;
+        f[i] = (n < N) ? run_start_flag(lam_y, n) : 0;
         c += f[i];
     }
     int total;
     int pos = tile_off[blockIdx.x] + block_exclusive_scan(c, s_warp, &total);
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
+    for (int i = 0; i < kScanItems; ++i)
         if (f[i]) row_start[pos++] = (int)(base + (int64_t)threadIdx.x * kScanItems + i);
-    }
 }
 
-// ---------------------------------------------------------------------------
-// Per pulse row: extent of its x footprint and its y cell/offset.
-// row_clo: first fine cell of the 1-D row buffer; row_len: cells in it.
-// A row whose footprint spans >= nx cells uses the whole periodic row
-// (row_clo = 0, row_len = nx, indices reduced modulo nx).
-// ---------------------------------------------------------------------------
+// Per pulse row: extent of its x footprint (checking every lam_x, err bit 1),
+// and its y cell/offset.  row_clo is the first fine x cell of the row buffer,
+// row_len its cells; a row whose footprint spans >= nx cells uses the whole
+// periodic row (row_clo = 0, row_len = nx, cells reduced modulo nx).
 __global__ void k_row_info(int P, int64_t N, int nx, int w, const int* __restrict__ row_start,
-                           const int* __restrict__ lx, const int* __restrict__ ly, const float* __restrict__ fy,
+                           const double* __restrict__ lam_x, const double* __restrict__ lam_y,
                            int* __restrict__ row_clo, int* __restrict__ row_len, int* __restrict__ row_ly,
-                           float* __restrict__ row_fy) {
+                           float* __restrict__ row_fy, double* __restrict__ row_lam_y, int* __restrict__ err) {
     __shared__ int s_min[32], s_max[32];
     for (int p = blockIdx.x; p < P; p += gridDim.x) {
         const int64_t s = row_start[p];
         const int64_t e = (p + 1 < P) ? row_start[p + 1] : N;
         int mn = 0x7fffffff, mx = -0x7fffffff;
+        bool bad = false;
         for (int64_t n = s + threadIdx.x; n < e; n += blockDim.x) {
-            const int c = lx[n];
+            int c;
+            float f;
+            bad |= !fine_coord(lam_x[n], c, f);
             mn = min(mn, c);
             mx = max(mx, c);
         }
+        if (bad) atomicOr(err, 1);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -171,16 +268,39 @@ __global__ void k_row_info(int P, int64_t N, int nx, int w, const int* __restric
                 row_clo[p] = mn - (h - 1);
                 row_len[p] = (int)span;
             }
-            row_ly[p] = ly[s];
-            row_fy[p] = fy[s];
+            const double ly = lam_y[s];
+            int cy;
+            float fy;
+            fine_coord(ly, cy, fy);
+            row_ly[p] = cy;
+            row_fy[p] = fy;
+            row_lam_y[p] = ly;
         }
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
-// Bucketing by fine-grid row (general points): histogram, then scatter.
+// General points: fine cells of both axes (err bit 1 on a bad coordinate),
+// then bucketing by fine row (histogram, scatter) and a sorted copy.
 // ---------------------------------------------------------------------------
+__global__ void k_prep_general(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y,
+                               int* __restrict__ lx, float* __restrict__ fx, int* __restrict__ ly,
+                               float* __restrict__ fy, int* __restrict__ err) {
+    bool bad = false;
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        int cx, cy;
+        float ox, oy;
+        bad |= !fine_coord(lam_x[n], cx, ox);
+        bad |= !fine_coord(lam_y[n], cy, oy);
+        lx[n] = cx;
+        fx[n] = ox;
+        ly[n] = cy;
+        fy[n] = oy;
+    }
+    if (bad) atomicOr(err, 1);
+}
+
 __global__ void k_bucket_hist(int64_t N, int ny, const int* __restrict__ ly, int* __restrict__ hist) {
     extern __shared__ int s_hist[];
     for (int i = threadIdx.x; i < ny; i += blockDim.x) s_hist[i] = 0;
@@ -213,70 +333,28 @@ __global__ void k_gather_sorted(int64_t N, const int* __restrict__ perm, const i
 }
 
 // ---------------------------------------------------------------------------
-// tFFR weights (Algorithm 1, Sec. III.B-C), FP64:
-//   w_hat(xi)  = 2 [a + e^{-a/2}(-a cos(pi xi) + 2 pi xi sin(pi xi))] / (a^2 + 4 pi^2 xi^2)
-//   psi(eta)   = 2 [-a + e^{a/2}(a cos(pi eta) + 2 pi eta sin(pi eta))] / (a^2 + 4 pi^2 eta^2)
-//   G(lam)     = sum over grid points l in [-M/2, M/2) with |lam - l| < q of psi(lam - l) w_hat(l - lam)
-//   D          = R_tau(1/G)  (0 when G = 0; kept when 1/G >= tau)
-// These are the transforms of the window w(t) = exp(-a|t|) and of 1/w on the
-// centred domain t in [-1/2, 1/2] (Eq. (Psi); the window of Sec. IV).
+// D_n for every sample in the caller's order (D_out, n_kept, general points).
 // ---------------------------------------------------------------------------
-struct WeightParams {
-    int mode;          // 0 tFFR, 1 unit, 2 user
-    int separable;     // 0 range only, 1 product of range and azimuth factors
-    double a, q, tau;
-    double e_minus, e_plus;   // exp(-a/2), exp(+a/2)
-    const float* user_D;
-};
-
-__device__ __forceinline__ double window_hat(double xi, const WeightParams& p) {
-    double s, c;
-    sincospi(xi, &s, &c);
-    const double two_pi = 6.283185307179586476925286766559;
-    const double num = p.a + p.e_minus * (-p.a * c + two_pi * xi * s);
-    return 2.0 * num / (p.a * p.a + two_pi * two_pi * xi * xi);
-}
-
-__device__ __forceinline__ double inv_window_hat(double eta, const WeightParams& p) {
-    double s, c;
-    sincospi(eta, &s, &c);
-    const double two_pi = 6.283185307179586476925286766559;
-    const double num = -p.a + p.e_plus * (p.a * c + two_pi * eta * s);
-    return 2.0 * num / (p.a * p.a + two_pi * two_pi * eta * eta);
-}
-
-__device__ double diag_psi_w(double lam, int M, const WeightParams& p) {
-    const double base = floor(lam);
-    const int reach = (int)ceil(p.q) + 1;
-    const double lo = -(double)(M / 2), hi = (double)(M - M / 2);
-    double G = 0.0;
-    for (int off = -reach; off <= reach; ++off) {
-        const double l = base + off;
-        if (l < lo || l >= hi) continue;
-        const double eta = lam - l;
-        if (!(fabs(eta) < p.q)) continue;
-        G += inv_window_hat(eta, p) * window_hat(-eta, p);
-    }
-    return G;
-}
-
 __global__ void k_weights(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y, int Mx,
-                          int My, WeightParams p, float* __restrict__ D, unsigned long long* __restrict__ kept) {
+                          int My, WeightArgs A, float* __restrict__ D, unsigned long long* __restrict__ kept) {
     int c = 0;
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
-        double d;
-        if (p.mode == 1) {
-            d = 1.0;
-        } else if (p.mode == 2) {
-            d = (double)p.user_D[n];
+        float d;
+        if (A.mode == 1) {
+            d = 1.0f;
+        } else if (A.mode == 2) {
+            d = A.user_D[n];
         } else {
-            double G = diag_psi_w(lam_x[n], Mx, p);
-            if (p.separable) G *= diag_psi_w(lam_y[n], My, p);
-            d = (G != 0.0) ? 1.0 / G : 0.0;
-            if (!(d >= p.tau)) d = 0.0;
+            const double x = lam_x[n];
+            const double y = A.separable ? lam_y[n] : 0.0;
+            int cx = 0, cy = 0;
+            float ox = 0.f, oy = 0.f;
+            fine_coord(x, cx, ox);
+            if (A.separable) fine_coord(y, cy, oy);
+            d = weight_tffr(x, cx, ox, y, cy, oy, Mx, My, A);
         }
-        D[n] = (float)d;
-        c += (d != 0.0);
+        D[n] = d;
+        c += (d != 0.0f);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);

@@ -5,7 +5,10 @@
 // applied later, inside the first FFT pass.
 #pragma once
 
+#include <climits>
+
 #include "common.cuh"
+#include "kernels_points.cuh"
 
 namespace tffr {
 
@@ -16,62 +19,142 @@ struct RowsView {
     const int* row_len;             // [P] cells in the row buffer (nx: periodic row)
     const int* row_ly;              // [P] fine y cell floor(2 lam_y)
     const float* row_fy;            // [P] fine y offset in [0, 1]
+    const double* row_lam_y;        // [P] lam_y of the row
     const int64_t* row_off;         // [P] offset of the row buffer in R (cells)
     const int* bucket_start;        // [ny + 1] rows grouped by row_ly mod ny
     const int* bucket_rows;         // [P]
 };
 
 constexpr int kSpreadThreads = 256;
+constexpr int kSpreadPerThread = 8;                      // samples per thread per staged tile
+constexpr int kSpreadTile = kSpreadThreads * kSpreadPerThread;
+// staged lam_x and values of one tile, one pad slot per 64 samples
+constexpr int kSpreadStageElems = kSpreadTile + kSpreadTile / 64 + 1;
+constexpr int kSpreadStageBytes = kSpreadStageElems * (int)(sizeof(double) + sizeof(float2));
 
-// Adjoint, step 1: R_p[c] = sum_{n in row p} D_n v_n phi(c - u_n) over the w
-// taps of each sample, accumulated in shared memory, then stored contiguously.
-template <typename VT>
-__global__ void __launch_bounds__(kSpreadThreads)
-k_spread_rows(RowsView rv, int64_t N, int nx, int w, float beta, const void* __restrict__ values,
-              const float* __restrict__ D, const int* __restrict__ lx, const float* __restrict__ fx,
-              float2* __restrict__ R) {
-    extern __shared__ float2 s_row[];
+// Adjoint, step 1: R_p[c] = sum_{n in row p} D_n v_n phi(c - u_n) over the W
+// taps of each sample.  Samples are staged tile by tile with coalesced loads;
+// each thread then walks a contiguous run of samples (which move slowly along
+// x) and keeps the W cells under its current footprint in registers, flushing
+// a cell into the shared row (atomic add) only when the footprint moves past
+// it.  D_n is evaluated inline from lam_x (tFFR mode) or read (user mode).
+template <typename VT, int W>
+__global__ void __launch_bounds__(kSpreadThreads, 3)
+k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __restrict__ lam_x,
+              const void* __restrict__ values, WeightArgs wa, TapPoly tp, float2* __restrict__ R) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* s_lam = reinterpret_cast<double*>(smem_raw);
+    float2* s_val = reinterpret_cast<float2*>(s_lam + kSpreadStageElems);
+    float2* s_row = s_val + kSpreadStageElems;
+    constexpr int H = W / 2;
     const int p = blockIdx.x;
     const int len = rv.row_len[p];
     const int clo = rv.row_clo[p];
     const bool periodic = (len == nx) && (clo == 0);
     const int64_t s0 = rv.row_start[p];
     const int64_t s1 = (p + 1 < rv.P) ? rv.row_start[p + 1] : N;
-    for (int i = threadIdx.x; i < len; i += blockDim.x) s_row[i] = make_float2(0.f, 0.f);
-    __syncthreads();
     const int L = (int)(s1 - s0);
-    const int chunk = (L + blockDim.x - 1) / blockDim.x;
-    const int h = w / 2;
-    const float two_over_w = 2.0f / (float)w;
-    // Thread t walks samples [t*chunk, (t+1)*chunk): lanes of a warp sit far
-    // apart along the row, so their shared-memory adds rarely collide.
-    for (int k = 0; k < chunk; ++k) {
-        const int i = threadIdx.x * chunk + k;
-        if (i >= L) break;
-        const int64_t n = s0 + i;
-        const float d = D[n];
-        if (d == 0.0f) continue;
-        const float2 v = cscale(ValueIO<VT>::load(values, n), d);
-        const int c0 = lx[n] - (h - 1);
-        const float f = fx[n];
-        for (int s = 0; s < w; ++s) {
-            const float wt = es_kernel((float)(s - (h - 1)) - f, beta, two_over_w);
-            const int c = c0 + s;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < len; i += kSpreadThreads) s_row[i] = make_float2(0.f, 0.f);
+
+    // azimuth factor of the separable weight variant: one value per row
+    float gy = 1.0f;
+    bool gy_exact = false;
+    const double lam_y_row = rv.row_lam_y[p];
+    if (wa.mode == 0 && wa.separable) gy = g_fitted(rv.row_ly[p], rv.row_fy[p], My, wa, gy_exact);
+
+    // Thread (warp wid, lane) walks run number wid + 8 * lane of the tile: the
+    // lanes of a warp are 8 runs apart, so their footprints (and the shared
+    // adds of their flushes) rarely overlap.
+    const int run = (tid >> 5) + (kSpreadThreads / 32) * (tid & 31);
+    for (int t0 = 0; t0 < L; t0 += kSpreadTile) {
+        const int cnt = min(kSpreadTile, L - t0);
+        const int chunk = (cnt + kSpreadThreads - 1) / kSpreadThreads;
+        __syncthreads();                                   // previous tile fully consumed
+        for (int i = tid; i < cnt; i += kSpreadThreads) {
+            const int k = i + (i >> 6);                    // pad: strided reads below stay off one bank
+            s_lam[k] = lam_x[s0 + t0 + i];
+            s_val[k] = ValueIO<VT>::load(values, s0 + t0 + i);
+        }
+        __syncthreads();
+        const int i0 = run * chunk;
+        const int i1 = min(cnt, i0 + chunk);
+        float2 acc[W];
+#pragma unroll
+        for (int s = 0; s < W; ++s) acc[s] = make_float2(0.f, 0.f);
+        int wbase = INT_MIN;                               // first fine cell held in acc
+        auto flush = [&](int s) {
+            const int c = wbase + s;
             const int idx = periodic ? wrapmod(c, nx) : (c - clo);
-            atomic_add_f2_shared(&s_row[idx], cscale(v, wt));
+            atomic_add_f2_shared(&s_row[idx], acc[s]);
+        };
+        for (int i = i0; i < i1; ++i) {
+            const int k = i + (i >> 6);
+            const double lam = s_lam[k];
+            int cell;
+            float f;
+            fine_coord(lam, cell, f);
+            float d;
+            if (wa.mode == 1) {
+                d = 1.0f;
+            } else if (wa.mode == 2) {
+                d = wa.user_D[s0 + t0 + i];
+            } else {
+                bool exact = gy_exact;
+                float G = g_fitted(cell, f, Mx, wa, exact) * gy;
+                d = (G != 0.0f) ? 1.0f / G : 0.0f;
+                if (exact || !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau)))
+                    d = weight_exact(lam, lam_y_row, Mx, My, wa);
+                else if (d < wa.tau)
+                    d = 0.0f;
+            }
+            if (d == 0.0f) continue;
+            const float2 v = cscale(s_val[k], d);
+            float wt[W];
+            taps_all<W>(tp, f, wt);
+            const int c0 = cell - (H - 1);
+            if (c0 != wbase) {
+                if (wbase != INT_MIN && c0 > wbase && c0 - wbase < W) {
+                    // slide the footprint right, flushing the cells it leaves
+                    while (wbase < c0) {
+                        flush(0);
+#pragma unroll
+                        for (int s = 0; s < W - 1; ++s) acc[s] = acc[s + 1];
+                        acc[W - 1] = make_float2(0.f, 0.f);
+                        ++wbase;
+                    }
+                } else {
+                    if (wbase != INT_MIN) {
+#pragma unroll
+                        for (int s = 0; s < W; ++s) flush(s);
+                    }
+#pragma unroll
+                    for (int s = 0; s < W; ++s) acc[s] = make_float2(0.f, 0.f);
+                    wbase = c0;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < W; ++s) {
+                acc[s].x = fmaf(wt[s], v.x, acc[s].x);
+                acc[s].y = fmaf(wt[s], v.y, acc[s].y);
+            }
+        }
+        if (wbase != INT_MIN) {
+#pragma unroll
+            for (int s = 0; s < W; ++s) flush(s);
         }
     }
     __syncthreads();
     float2* out = R + rv.row_off[p];
-    for (int i = threadIdx.x; i < len; i += blockDim.x) out[i] = s_row[i];
+    for (int i = tid; i < len; i += kSpreadThreads) out[i] = s_row[i];
 }
 
 // Forward, last step: y_n = D_n sum_s phi(c_s - u_n) R_p[c_s] (or without D_n).
-template <typename VT>
+template <typename VT, int W>
 __global__ void __launch_bounds__(kSpreadThreads)
-k_interp_rows(RowsView rv, int64_t N, int nx, int w, float beta, const float2* __restrict__ R,
-              const float* __restrict__ D, int apply_weights, const int* __restrict__ lx,
-              const float* __restrict__ fx, void* __restrict__ out) {
+k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __restrict__ lam_x,
+              const float2* __restrict__ R, WeightArgs wa, TapPoly tp, int apply_weights, void* __restrict__ out) {
+    constexpr int H = W / 2;
     const int p = blockIdx.x;
     const int len = rv.row_len[p];
     const int clo = rv.row_clo[p];
@@ -79,21 +162,40 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int w, float beta, const float2* _
     const int64_t s0 = rv.row_start[p];
     const int64_t s1 = (p + 1 < rv.P) ? rv.row_start[p + 1] : N;
     const float2* Rp = R + rv.row_off[p];
-    const int h = w / 2;
-    const float two_over_w = 2.0f / (float)w;
+    float gy = 1.0f;
+    bool gy_exact = false;
+    const double lam_y_row = rv.row_lam_y[p];
+    if (apply_weights && wa.mode == 0 && wa.separable) gy = g_fitted(rv.row_ly[p], rv.row_fy[p], My, wa, gy_exact);
     for (int64_t n = s0 + threadIdx.x; n < s1; n += blockDim.x) {
-        const int c0 = lx[n] - (h - 1);
-        const float f = fx[n];
+        const double lam = lam_x[n];
+        int cell;
+        float f;
+        fine_coord(lam, cell, f);
+        float wt[W];
+        taps_all<W>(tp, f, wt);
+        const int c0 = cell - (H - 1);
         float2 acc = make_float2(0.f, 0.f);
-        for (int s = 0; s < w; ++s) {
-            const float wt = es_kernel((float)(s - (h - 1)) - f, beta, two_over_w);
+#pragma unroll
+        for (int s = 0; s < W; ++s) {
             const int c = c0 + s;
-            const int idx = periodic ? wrapmod(c, nx) : (c - clo);
-            const float2 r = Rp[idx];
-            acc.x += wt * r.x;
-            acc.y += wt * r.y;
+            const float2 r = Rp[periodic ? wrapmod(c, nx) : (c - clo)];
+            acc.x = fmaf(wt[s], r.x, acc.x);
+            acc.y = fmaf(wt[s], r.y, acc.y);
         }
-        const float d = apply_weights ? D[n] : 1.0f;
+        float d = 1.0f;
+        if (apply_weights) {
+            if (wa.mode == 2) {
+                d = wa.user_D[n];
+            } else if (wa.mode == 0) {
+                bool exact = gy_exact;
+                float G = g_fitted(cell, f, Mx, wa, exact) * gy;
+                d = (G != 0.0f) ? 1.0f / G : 0.0f;
+                if (exact || !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau)))
+                    d = weight_exact(lam, lam_y_row, Mx, My, wa);
+                else if (d < wa.tau)
+                    d = 0.0f;
+            }
+        }
         ValueIO<VT>::store(out, n, cscale(acc, d));
     }
 }

@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/tffr.h: plan set-up (FP64
-// tables), point preparation, weights, and the launch sequences of the
-// adjoint and forward transforms.  All device work is in the .cuh kernels.
+// tables and polynomial fits), point preparation, weights, and the launch
+// sequences of the adjoint and forward transforms.  All device work is in
+// the .cuh kernels.
 
 #include <cuda_runtime.h>
 
@@ -43,22 +44,25 @@ struct tffr_plan_s {
     cudaStream_t stream = nullptr;
     std::string last_error;
     size_t device_bytes = 0;
+    TapPoly taps;                          // spreading-kernel taps, fitted at plan time
+    WeightArgs wargs;                      // weight evaluation, set by tffr_weights
+    WeightArgs fit_cache;                  // last fitted G pieces, reused while (a, q) stay the same
+    bool fit_valid = false;
 
     // plan-time tables and the intermediate of the FFT passes
     DevBuf<float2> twx, twy, T;
     DevBuf<float> deap_x, deap_y;
-    DevBuf<int> d_small;                  // [0] error flag, [1] scan sum
+    DevBuf<int> d_small;                   // [0] error flag, [1] scan sum
     DevBuf<unsigned long long> d_kept;
 
-    // points
+    // points (the caller's coordinate arrays are used in place)
     int64_t N = 0;
+    const double* lam_x = nullptr;
+    const double* lam_y = nullptr;
     bool have_points = false, have_weights = false;
     int layout = 0;
     int64_t n_kept = -1;
-    DevBuf<double> keep_x, keep_y;
-    DevBuf<int> lx, ly;
-    DevBuf<float> fx, fy, D;
-    DevBuf<uint8_t> run_start;
+    DevBuf<float> D;                       // per-sample weights when materialised
     DevBuf<int> tiles;
 
     // pulse rows
@@ -67,12 +71,13 @@ struct tffr_plan_s {
     int max_len = 0;
     DevBuf<int> row_start, row_clo, row_len, row_ly, bucket_rows, bucket_start;
     DevBuf<float> row_fy;
+    DevBuf<double> row_lam_y;
     DevBuf<int64_t> row_off;
     DevBuf<float2> R;
 
     // general points
-    DevBuf<int> perm, slx, cursor;
-    DevBuf<float> sfx, sfy, sD;
+    DevBuf<int> lx, ly, perm, slx, cursor;
+    DevBuf<float> fx, fy, sfx, sfy, sD;
     DevBuf<float2> acc;
 
     // launch count and optional per-stage event timing
@@ -93,16 +98,16 @@ int cuda_fail(tffr_plan_s* p, cudaError_t e, const char* where) {
     return fail(p, e == cudaErrorMemoryAllocation ? TFFR_ERR_OOM : TFFR_ERR_CUDA, m);
 }
 
-#define CK(call)                                          \
-    do {                                                  \
-        cudaError_t e_ = (call);                          \
+#define CK(call)                                               \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
         if (e_ != cudaSuccess) return cuda_fail(p, e_, #call); \
     } while (0)
 
-#define CK_LAUNCH(where)                                  \
-    do {                                                  \
-        ++p->launches;                                    \
-        cudaError_t e_ = cudaGetLastError();              \
+#define CK_LAUNCH(where)                                       \
+    do {                                                       \
+        ++p->launches;                                         \
+        cudaError_t e_ = cudaGetLastError();                   \
         if (e_ != cudaSuccess) return cuda_fail(p, e_, where); \
     } while (0)
 
@@ -121,8 +126,16 @@ int stage_mark(tffr_plan_s* p, int stage, bool end) {
     return TFFR_OK;
 }
 
-#define STAGE_BEGIN(st) do { int s_ = stage_mark(p, (st), false); if (s_ != TFFR_OK) return s_; } while (0)
-#define STAGE_END(st) do { int s_ = stage_mark(p, (st), true); if (s_ != TFFR_OK) return s_; } while (0)
+#define STAGE_BEGIN(st)                          \
+    do {                                         \
+        int s_ = stage_mark(p, (st), false);     \
+        if (s_ != TFFR_OK) return s_;            \
+    } while (0)
+#define STAGE_END(st)                            \
+    do {                                         \
+        int s_ = stage_mark(p, (st), true);      \
+        if (s_ != TFFR_OK) return s_;            \
+    } while (0)
 
 template <typename T>
 cudaError_t grow(tffr_plan_s* p, DevBuf<T>& b, int64_t want) {
@@ -156,6 +169,10 @@ int ilog2(int v) {
     return l;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 host numerics: quadrature, Chebyshev fits
+// ---------------------------------------------------------------------------
+
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on P_n).
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wts) {
     x.assign(n, 0.0);
@@ -182,6 +199,12 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& wts) {
     }
 }
 
+double es_phi(double z, int w, double beta) {
+    const double x = 2.0 * z / w;
+    const double t = 1.0 - x * x;
+    return t > 0 ? std::exp(beta * (std::sqrt(t) - 1.0)) : 0.0;
+}
+
 // phi_hat(xi) = int_{-w/2}^{w/2} phi(z) exp(2 pi i xi z) dz for the ES kernel (real, even).
 std::vector<double> es_transform(const std::vector<double>& xi, int w, double beta) {
     std::vector<double> gx, gw;
@@ -190,11 +213,9 @@ std::vector<double> es_transform(const std::vector<double>& xi, int w, double be
     const double hw = 0.5 * w, two_pi = 6.283185307179586476925286766559;
     std::vector<double> z(nq), phi(nq), wz(nq);
     for (int i = 0; i < nq; ++i) {
-        z[i] = 0.5 * hw * (gx[i] + 1.0);      // [0, w/2]
+        z[i] = 0.5 * hw * (gx[i] + 1.0);       // [0, w/2]
         wz[i] = 0.5 * hw * gw[i];
-        const double s = z[i] / hw;
-        const double t = 1.0 - s * s;
-        phi[i] = t > 0 ? std::exp(beta * (std::sqrt(t) - 1.0)) : 0.0;
+        phi[i] = es_phi(z[i], w, beta);
     }
     std::vector<double> out(xi.size());
     for (size_t k = 0; k < xi.size(); ++k) {
@@ -203,6 +224,88 @@ std::vector<double> es_transform(const std::vector<double>& xi, int w, double be
         out[k] = 2.0 * acc;
     }
     return out;
+}
+
+// Chebyshev interpolant of f on [-1, 1] at n nodes, returned as power-basis
+// coefficients a_0..a_{n-1} of the variable s in [-1, 1].
+template <typename F>
+std::vector<double> cheb_fit_power(F f, int n) {
+    const double pi = 3.14159265358979323846;
+    std::vector<double> fv(n), c(n, 0.0);
+    for (int k = 0; k < n; ++k) fv[k] = f(std::cos(pi * (k + 0.5) / n));
+    for (int j = 0; j < n; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += fv[k] * std::cos(pi * j * (k + 0.5) / n);
+        c[j] = (j == 0 ? 1.0 : 2.0) * s / n;
+    }
+    // T_j in the power basis, by T_{j+1} = 2 s T_j - T_{j-1}
+    std::vector<double> a(n, 0.0), tprev(n, 0.0), tcur(n, 0.0), tnext(n, 0.0);
+    tprev[0] = 1.0;
+    if (n > 1) tcur[1] = 1.0;
+    for (int i = 0; i < n; ++i) a[i] += c[0] * tprev[i];
+    if (n > 1)
+        for (int i = 0; i < n; ++i) a[i] += c[1] * tcur[i];
+    for (int j = 2; j < n; ++j) {
+        for (int i = 0; i < n; ++i) tnext[i] = (i > 0 ? 2.0 * tcur[i - 1] : 0.0) - tprev[i];
+        for (int i = 0; i < n; ++i) a[i] += c[j] * tnext[i];
+        tprev.swap(tcur);
+        tcur.swap(tnext);
+    }
+    return a;
+}
+
+template <typename F>
+double power_fit_error(const std::vector<double>& a, F f) {
+    double err = 0.0;
+    for (int i = 0; i <= 2000; ++i) {
+        const double s = -1.0 + 2.0 * i / 2000.0;
+        double v = 0.0;
+        for (int k = (int)a.size() - 1; k >= 0; --k) v = v * s + a[k];
+        err = std::max(err, std::fabs(v - f(s)));
+    }
+    return err;
+}
+
+// Taps P_s(t), t = 2f - 1, for s < w/2; the mirrored taps are P_s(-t).
+void fit_taps(tffr_plan_s* p) {
+    std::memset(&p->taps, 0, sizeof(p->taps));
+    const int w = p->w, h = w / 2;
+    for (int s = 0; s < h; ++s) {
+        auto f = [&](double t) { return es_phi((double)(s - (h - 1)) - 0.5 * (t + 1.0), w, p->beta); };
+        const std::vector<double> a = cheb_fit_power(f, kTapCoefs);
+        for (int k = 0; k < kTapCoefs; ++k) {
+            p->taps.c[s][k] = (float)a[k];
+            p->taps.c[w - 1 - s][k] = (float)((k & 1) ? -a[k] : a[k]);
+        }
+    }
+}
+
+// Polynomial pieces of G(delta) (unbounded grid) in v = |delta - 1/2|; see WeightArgs.
+void fit_weights(WeightArgs& A) {
+    const double fq = A.q - std::floor(A.q);
+    A.vb = (float)std::fabs(fq - 0.5);
+    const double vb = A.vb;
+    auto G = [&](double v) { return diag_psi_w(0.5 + v, 0, A.a, A.q, A.e_minus, A.e_plus, A.reach); };
+    A.n0 = A.n1 = 1;
+    A.c0[0] = A.c1[0] = 0.0f;
+    if (vb > 0.0) {
+        auto f0 = [&](double s) { return G(vb * std::sqrt(std::max(0.0, 0.5 * (s + 1.0)))); };
+        for (int n = 8; n <= kGCoefs; ++n) {
+            std::vector<double> a = cheb_fit_power(f0, n);
+            A.n0 = n;
+            for (int k = 0; k < n; ++k) A.c0[k] = (float)a[k];
+            if (power_fit_error(a, f0) < 1e-10) break;
+        }
+    }
+    if (vb < 0.5) {
+        auto f1 = [&](double s) { return G(vb + (0.5 - vb) * 0.5 * (s + 1.0)); };
+        for (int n = 8; n <= kGCoefs; ++n) {
+            std::vector<double> a = cheb_fit_power(f1, n);
+            A.n1 = n;
+            for (int k = 0; k < n; ++k) A.c1[k] = (float)a[k];
+            if (power_fit_error(a, f1) < 1e-10) break;
+        }
+    }
 }
 
 int upload_tables(tffr_plan_s* p) {
@@ -238,33 +341,38 @@ int upload_tables(tffr_plan_s* p) {
 }
 
 constexpr int kFftSmemMax = (kFftNMax + kFftNMax / 16) * (int)sizeof(float2);
-constexpr int kRowSmemMax = kFftNMax * (int)sizeof(float2);
+constexpr int kSpreadSmemMax = kSpreadStageBytes + kFftNMax * (int)sizeof(float2);
 
 template <typename K>
 cudaError_t smem_attr(K kernel, int bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+template <typename VT>
+cudaError_t spread_attrs() {
+    cudaError_t e = smem_attr(k_spread_rows<VT, 2>, kSpreadSmemMax);
+    if (e == cudaSuccess) e = smem_attr(k_spread_rows<VT, 4>, kSpreadSmemMax);
+    if (e == cudaSuccess) e = smem_attr(k_spread_rows<VT, 6>, kSpreadSmemMax);
+    if (e == cudaSuccess) e = smem_attr(k_spread_rows<VT, 8>, kSpreadSmemMax);
+    if (e == cudaSuccess) e = smem_attr(k_adj_rows_general<VT>, kFftSmemMax);
+    return e;
+}
+
 int set_kernel_attributes(tffr_plan_s* p) {
-    static bool done = false;
-    if (done) return TFFR_OK;
-    CK(smem_attr(k_adj_rows<true, float2>, kFftSmemMax));
-    CK(smem_attr(k_adj_rows<true, double2>, kFftSmemMax));
-    CK(smem_attr(k_adj_rows<true, __half2>, kFftSmemMax));
-    CK(smem_attr(k_adj_rows<true, __nv_bfloat162>, kFftSmemMax));
-    CK(smem_attr(k_adj_rows<false, float2>, kFftSmemMax));
-    CK(smem_attr(k_adj_rows<false, double2>, kFftSmemMax));
-    CK(smem_attr(k_adj_rows<false, __half2>, kFftSmemMax));
-    CK(smem_attr(k_adj_rows<false, __nv_bfloat162>, kFftSmemMax));
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    static bool done[64] = {false};
+    if (dev < 64 && done[dev]) return TFFR_OK;
+    CK(smem_attr(k_adj_rows, kFftSmemMax));
     CK(smem_attr(k_adj_cols, kFftSmemMax));
     CK(smem_attr(k_fwd_cols, kFftSmemMax));
     CK(smem_attr(k_fwd_rows<true>, kFftSmemMax));
     CK(smem_attr(k_fwd_rows<false>, kFftSmemMax));
-    CK(smem_attr(k_spread_rows<float2>, kRowSmemMax));
-    CK(smem_attr(k_spread_rows<double2>, kRowSmemMax));
-    CK(smem_attr(k_spread_rows<__half2>, kRowSmemMax));
-    CK(smem_attr(k_spread_rows<__nv_bfloat162>, kRowSmemMax));
-    done = true;
+    CK(spread_attrs<float2>());
+    CK(spread_attrs<double2>());
+    CK(spread_attrs<__half2>());
+    CK(spread_attrs<__nv_bfloat162>());
+    if (dev < 64) done[dev] = true;
     return TFFR_OK;
 }
 
@@ -281,6 +389,7 @@ RowsView rows_view(const tffr_plan_s* p) {
     v.row_len = p->row_len.ptr;
     v.row_ly = p->row_ly.ptr;
     v.row_fy = p->row_fy.ptr;
+    v.row_lam_y = p->row_lam_y.ptr;
     v.row_off = p->row_off.ptr;
     v.bucket_start = p->bucket_start.ptr;
     v.bucket_rows = p->bucket_rows.ptr;
@@ -298,49 +407,53 @@ GeneralView general_view(const tffr_plan_s* p) {
     return v;
 }
 
-// Number of runs of equal lam_y (pulse rows); with emit, their first samples in order.
-int compact_run_starts(tffr_plan_s* p, int64_t N, int* P_out, bool emit) {
+// Number of runs of bit-equal lam_y (pulse rows); checks lam_y.
+int count_runs(tffr_plan_s* p, int* P_out) {
+    const int64_t N = p->N;
     const int64_t ntiles = (N + kScanTile - 1) / kScanTile;
     CK(grow(p, p->tiles, ntiles));
-    k_count_flags<<<(unsigned)ntiles, kScanThreads, 0, p->stream>>>(N, p->run_start.ptr, p->tiles.ptr);
-    CK_LAUNCH("k_count_flags");
+    k_count_runs<<<(unsigned)ntiles, kScanThreads, 0, p->stream>>>(N, p->lam_y, p->tiles.ptr, p->d_small.ptr);
+    CK_LAUNCH("k_count_runs");
     k_scan_tile_counts<<<1, kScanThreads, 0, p->stream>>>((int)ntiles, p->tiles.ptr, p->d_small.ptr + 1);
     CK_LAUNCH("k_scan_tile_counts");
-    int P = 0;
-    CK(cudaMemcpyAsync(&P, p->d_small.ptr + 1, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    int h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, p->d_small.ptr, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
-    *P_out = P;
-    if (!emit) return TFFR_OK;
-    CK(grow(p, p->row_start, P));
-    k_emit_run_starts<<<(unsigned)ntiles, kScanThreads, 0, p->stream>>>(N, p->run_start.ptr, p->tiles.ptr,
-                                                                         p->row_start.ptr);
-    CK_LAUNCH("k_emit_run_starts");
+    if (h[0]) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_y or |lam_y| >= 2^28");
+    *P_out = h[1];
     return TFFR_OK;
 }
 
-int build_rows(tffr_plan_s* p) {
+int build_rows(tffr_plan_s* p, int P) {
     const int64_t N = p->N;
-    int P = 0;
-    int s = compact_run_starts(p, N, &P, true);
-    if (s != TFFR_OK) return s;
+    const int64_t ntiles = (N + kScanTile - 1) / kScanTile;
     p->P = P;
+    CK(grow(p, p->row_start, P));
     CK(grow(p, p->row_clo, P));
     CK(grow(p, p->row_len, P));
     CK(grow(p, p->row_ly, P));
     CK(grow(p, p->row_fy, P));
+    CK(grow(p, p->row_lam_y, P));
     CK(grow(p, p->row_off, P));
     CK(grow(p, p->bucket_rows, P));
     CK(grow(p, p->bucket_start, p->ny + 1));
-    k_row_info<<<std::min(P, 152 * 16), 256, 0, p->stream>>>(P, N, p->nx, p->w, p->row_start.ptr, p->lx.ptr,
-                                                               p->ly.ptr, p->fy.ptr, p->row_clo.ptr,
-                                                               p->row_len.ptr, p->row_ly.ptr, p->row_fy.ptr);
+    k_emit_run_starts<<<(unsigned)ntiles, kScanThreads, 0, p->stream>>>(N, p->lam_y, p->tiles.ptr,
+                                                                         p->row_start.ptr);
+    CK_LAUNCH("k_emit_run_starts");
+    k_row_info<<<std::min(P, 152 * 16), 256, 0, p->stream>>>(P, N, p->nx, p->w, p->row_start.ptr, p->lam_x,
+                                                               p->lam_y, p->row_clo.ptr, p->row_len.ptr,
+                                                               p->row_ly.ptr, p->row_fy.ptr, p->row_lam_y.ptr,
+                                                               p->d_small.ptr);
     CK_LAUNCH("k_row_info");
     // Per-row bookkeeping (P entries) on the host: buffer offsets and the
     // grouping of rows by fine y cell.
     std::vector<int> len(P), rly(P);
+    int err = 0;
     CK(cudaMemcpyAsync(len.data(), p->row_len.ptr, (size_t)P * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaMemcpyAsync(rly.data(), p->row_ly.ptr, (size_t)P * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(&err, p->d_small.ptr, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
+    if (err) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_x or |lam_x| >= 2^28");
     std::vector<int64_t> off(P);
     int64_t tot = 0;
     int mx = 0;
@@ -371,18 +484,29 @@ int build_general(tffr_plan_s* p) {
     p->P = 0;
     CK(grow(p, p->bucket_start, p->ny + 1));
     CK(grow(p, p->cursor, p->ny + 1));
+    CK(grow(p, p->lx, N));
+    CK(grow(p, p->ly, N));
+    CK(grow(p, p->fx, N));
+    CK(grow(p, p->fy, N));
     CK(grow(p, p->perm, N));
     CK(grow(p, p->slx, N));
     CK(grow(p, p->sfx, N));
     CK(grow(p, p->sfy, N));
     CK(grow(p, p->sD, N));
     CK(grow(p, p->acc, N));
+    CK(cudaMemsetAsync(p->d_small.ptr, 0, sizeof(int), p->stream));
+    k_prep_general<<<grid_for(N, 256), 256, 0, p->stream>>>(N, p->lam_x, p->lam_y, p->lx.ptr, p->fx.ptr, p->ly.ptr,
+                                                           p->fy.ptr, p->d_small.ptr);
+    CK_LAUNCH("k_prep_general");
     CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(p->ny + 1) * sizeof(int), p->stream));
     k_bucket_hist<<<grid_for(N, 256), 256, p->ny * sizeof(int), p->stream>>>(N, p->ny, p->ly.ptr, p->cursor.ptr);
     CK_LAUNCH("k_bucket_hist");
     std::vector<int> cnt(p->ny);
+    int err = 0;
     CK(cudaMemcpyAsync(cnt.data(), p->cursor.ptr, (size_t)p->ny * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(&err, p->d_small.ptr, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
+    if (err) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite coordinate or |lam| >= 2^28");
     std::vector<int> bstart(p->ny + 1, 0);
     for (int b = 0; b < p->ny; ++b) bstart[b + 1] = bstart[b] + cnt[b];
     CK(cudaMemcpyAsync(p->bucket_start.ptr, bstart.data(), (size_t)(p->ny + 1) * sizeof(int),
@@ -403,29 +527,38 @@ size_t fft_smem_bytes(const tffr_plan_s* p) {
     return (size_t)(n + n / 16) * sizeof(float2);
 }
 
+template <typename VT, int W>
+void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values) {
+    const size_t smem = (size_t)kSpreadStageBytes + (size_t)p->max_len * sizeof(float2);
+    k_spread_rows<VT, W><<<p->P, kSpreadThreads, smem, p->stream>>>(rv, p->N, p->nx, p->Mx, p->My, p->lam_x, values,
+                                                                     p->wargs, p->taps, p->R.ptr);
+}
+
 template <typename VT>
 int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
     const size_t fsm = fft_smem_bytes(p);
-    const float beta = (float)p->beta;
     if (p->layout == TFFR_POINTS_ROWS) {
         const RowsView rv = rows_view(p);
         STAGE_BEGIN(TFFR_STAGE_SPREAD);
-        k_spread_rows<VT><<<p->P, kSpreadThreads, (size_t)p->max_len * sizeof(float2), p->stream>>>(
-            rv, p->N, p->nx, p->w, beta, values, p->D.ptr, p->lx.ptr, p->fx.ptr, p->R.ptr);
+        switch (p->w) {
+            case 2: launch_spread<VT, 2>(p, rv, values); break;
+            case 4: launch_spread<VT, 4>(p, rv, values); break;
+            case 6: launch_spread<VT, 6>(p, rv, values); break;
+            default: launch_spread<VT, 8>(p, rv, values); break;
+        }
         CK_LAUNCH("k_spread_rows");
         STAGE_END(TFFR_STAGE_SPREAD);
         STAGE_BEGIN(TFFR_STAGE_ROW_FFT);
-        k_adj_rows<true, VT><<<p->ny, kFftThreads, fsm, p->stream>>>(rv, general_view(p), p->R.ptr, values, p->nx,
-                                                                      p->lognx, p->ny, p->Mx, p->w, beta,
-                                                                      p->twx.ptr, p->deap_x.ptr, p->T.ptr);
+        k_adj_rows<<<p->ny, kFftThreads, fsm, p->stream>>>(rv, p->R.ptr, p->nx, p->lognx, p->ny, p->Mx, p->w,
+                                                           p->taps, p->twx.ptr, p->deap_x.ptr, p->T.ptr);
         CK_LAUNCH("k_adj_rows");
         STAGE_END(TFFR_STAGE_ROW_FFT);
     } else {
         STAGE_BEGIN(TFFR_STAGE_ROW_FFT);
-        k_adj_rows<false, VT><<<p->ny, kFftThreads, fsm, p->stream>>>(rows_view(p), general_view(p), p->R.ptr,
-                                                                       values, p->nx, p->lognx, p->ny, p->Mx, p->w,
-                                                                       beta, p->twx.ptr, p->deap_x.ptr, p->T.ptr);
-        CK_LAUNCH("k_adj_rows");
+        k_adj_rows_general<VT><<<p->ny, kFftThreads, fsm, p->stream>>>(general_view(p), values, p->nx, p->lognx,
+                                                                        p->ny, p->Mx, p->w, p->taps, p->twx.ptr,
+                                                                        p->deap_x.ptr, p->T.ptr);
+        CK_LAUNCH("k_adj_rows_general");
         STAGE_END(TFFR_STAGE_ROW_FFT);
     }
     STAGE_BEGIN(TFFR_STAGE_COL_FFT);
@@ -436,10 +569,15 @@ int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
     return TFFR_OK;
 }
 
+template <typename VT, int W>
+void launch_interp(tffr_plan_s* p, const RowsView& rv, void* values, int apply_weights) {
+    k_interp_rows<VT, W><<<p->P, kSpreadThreads, 0, p->stream>>>(rv, p->N, p->nx, p->Mx, p->My, p->lam_x, p->R.ptr,
+                                                                  p->wargs, p->taps, apply_weights, values);
+}
+
 template <typename VT>
 int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_weights) {
     const size_t fsm = fft_smem_bytes(p);
-    const float beta = (float)p->beta;
     STAGE_BEGIN(TFFR_STAGE_FWD_COL_FFT);
     k_fwd_cols<<<p->Mx, kFftThreads, fsm, p->stream>>>(image, p->ny, p->logny, p->My, p->Mx, p->twy.ptr,
                                                        p->deap_y.ptr, p->deap_x.ptr, p->T.ptr);
@@ -450,19 +588,23 @@ int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_we
         CK(cudaMemsetAsync(p->R.ptr, 0, (size_t)p->R_cells * sizeof(float2), p->stream));
         const RowsView rv = rows_view(p);
         k_fwd_rows<true><<<p->ny, kFftThreads, fsm, p->stream>>>(rv, general_view(p), p->T.ptr, p->nx, p->lognx,
-                                                                 p->ny, p->Mx, p->w, beta, p->twx.ptr, p->R.ptr,
+                                                                 p->ny, p->Mx, p->w, p->taps, p->twx.ptr, p->R.ptr,
                                                                  p->acc.ptr);
         CK_LAUNCH("k_fwd_rows");
         STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
         STAGE_BEGIN(TFFR_STAGE_INTERP);
-        k_interp_rows<VT><<<p->P, kSpreadThreads, 0, p->stream>>>(rv, p->N, p->nx, p->w, beta, p->R.ptr, p->D.ptr,
-                                                                   apply_weights, p->lx.ptr, p->fx.ptr, values);
+        switch (p->w) {
+            case 2: launch_interp<VT, 2>(p, rv, values, apply_weights); break;
+            case 4: launch_interp<VT, 4>(p, rv, values, apply_weights); break;
+            case 6: launch_interp<VT, 6>(p, rv, values, apply_weights); break;
+            default: launch_interp<VT, 8>(p, rv, values, apply_weights); break;
+        }
         CK_LAUNCH("k_interp_rows");
         STAGE_END(TFFR_STAGE_INTERP);
     } else {
         CK(cudaMemsetAsync(p->acc.ptr, 0, (size_t)p->N * sizeof(float2), p->stream));
         k_fwd_rows<false><<<p->ny, kFftThreads, fsm, p->stream>>>(rows_view(p), general_view(p), p->T.ptr, p->nx,
-                                                                  p->lognx, p->ny, p->Mx, p->w, beta, p->twx.ptr,
+                                                                  p->lognx, p->ny, p->Mx, p->w, p->taps, p->twx.ptr,
                                                                   p->R.ptr, p->acc.ptr);
         CK_LAUNCH("k_fwd_rows");
         STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
@@ -541,6 +683,8 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
     p->values = o.values;
     p->layout_hint = o.layout;
     p->stream = (cudaStream_t)stream;
+    fit_taps(p);
+    std::memset(&p->wargs, 0, sizeof(p->wargs));
     int s = set_kernel_attributes(p);
     if (s == TFFR_OK) s = upload_tables(p);
     if (s == TFFR_OK) {
@@ -561,13 +705,11 @@ int tffr_destroy(tffr_plan_t p) {
     if (!p) return TFFR_OK;
     cudaStreamSynchronize(p->stream);
     release(p->twx); release(p->twy); release(p->T); release(p->deap_x); release(p->deap_y);
-    release(p->d_small); release(p->d_kept);
-    release(p->keep_x); release(p->keep_y); release(p->lx); release(p->ly); release(p->fx); release(p->fy);
-    release(p->D); release(p->run_start); release(p->tiles);
+    release(p->d_small); release(p->d_kept); release(p->D); release(p->tiles);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly); release(p->bucket_rows);
-    release(p->bucket_start); release(p->row_fy); release(p->row_off); release(p->R);
-    release(p->perm); release(p->slx); release(p->cursor); release(p->sfx); release(p->sfy); release(p->sD);
-    release(p->acc);
+    release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);
+    release(p->lx); release(p->ly); release(p->perm); release(p->slx); release(p->cursor);
+    release(p->fx); release(p->fy); release(p->sfx); release(p->sfy); release(p->sD); release(p->acc);
     for (auto& sp : p->prof)
         for (cudaEvent_t e : sp.ev) cudaEventDestroy(e);
     delete p;
@@ -629,40 +771,26 @@ int tffr_set_points(tffr_plan_t p, int64_t N, const double* lam_x, const double*
     p->have_weights = false;
     p->n_kept = -1;
     p->N = N;
+    p->lam_x = lam_x;
+    p->lam_y = lam_y;
     if (N == 0) {
         p->layout = TFFR_POINTS_GENERAL;
         p->P = 0;
         p->have_points = true;
         return TFFR_OK;
     }
-    CK(grow(p, p->keep_x, N));
-    CK(grow(p, p->keep_y, N));
-    CK(grow(p, p->lx, N));
-    CK(grow(p, p->ly, N));
-    CK(grow(p, p->fx, N));
-    CK(grow(p, p->fy, N));
-    CK(grow(p, p->run_start, N));
-    CK(grow(p, p->D, N));
     STAGE_BEGIN(TFFR_STAGE_POINTS);
     CK(cudaMemsetAsync(p->d_small.ptr, 0, 4 * sizeof(int), p->stream));
-    k_prep_points<<<grid_for(N, 256), 256, 0, p->stream>>>(N, lam_x, lam_y, p->keep_x.ptr, p->keep_y.ptr,
-                                                          p->lx.ptr, p->fx.ptr, p->ly.ptr, p->fy.ptr,
-                                                          p->run_start.ptr, p->d_small.ptr);
-    CK_LAUNCH("k_prep_points");
-    int err = 0;
-    CK(cudaMemcpyAsync(&err, p->d_small.ptr, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
-    if (err) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite coordinate or |lam| >= 2^28");
-
     int layout = p->layout_hint;
-    if (layout == TFFR_POINTS_AUTO) {
-        int P = 0;
-        int s = compact_run_starts(p, N, &P, false);
+    int P = 0;
+    int s = TFFR_OK;
+    if (layout != TFFR_POINTS_GENERAL) {
+        s = count_runs(p, &P);
         if (s != TFFR_OK) return s;
-        layout = (N >= 8 * (int64_t)P) ? TFFR_POINTS_ROWS : TFFR_POINTS_GENERAL;
+        if (layout == TFFR_POINTS_AUTO) layout = (N >= 8 * (int64_t)P) ? TFFR_POINTS_ROWS : TFFR_POINTS_GENERAL;
     }
     p->layout = layout;
-    const int s = (layout == TFFR_POINTS_ROWS) ? build_rows(p) : build_general(p);
+    s = (layout == TFFR_POINTS_ROWS) ? build_rows(p, P) : build_general(p);
     if (s != TFFR_OK) return s;
     STAGE_END(TFFR_STAGE_POINTS);
     p->have_points = true;
@@ -677,34 +805,58 @@ int tffr_weights(tffr_plan_t p, const tffr_weight_opts* opts, float* D_out, int6
     tffr_default_weight_opts(&o);
     if (opts) o = *opts;
     if (o.mode < TFFR_WEIGHTS_TFFR || o.mode > TFFR_WEIGHTS_USER) return fail(p, TFFR_ERR_INVALID_ARG, "mode");
-    if (!(o.q > 0) || !(o.q < 1e6) || !(o.a >= 0) || !(o.a < 1e3) || !(o.tau == o.tau))
+    if (!(o.q > 0) || !(o.q < 1e6) || !(o.a >= 0) || !(o.a < 1e3) || !(o.tau == o.tau) || !(std::fabs(o.tau) < 1e30))
         return fail(p, TFFR_ERR_INVALID_ARG, "a, q or tau out of range");
     if (o.mode == TFFR_WEIGHTS_USER && !o.user_D && p->N > 0) return fail(p, TFFR_ERR_INVALID_ARG, "user_D");
     const int64_t N = p->N;
+    p->have_weights = false;
     p->n_kept = -1;
-    if (N > 0) {
-        WeightParams wp;
-        wp.mode = o.mode;
-        wp.separable = o.separable ? 1 : 0;
-        wp.a = o.a;
-        wp.q = o.q;
-        wp.tau = o.tau;
-        wp.e_minus = std::exp(-o.a / 2.0);
-        wp.e_plus = std::exp(o.a / 2.0);
-        wp.user_D = o.user_D;
-        STAGE_BEGIN(TFFR_STAGE_WEIGHTS);
+    WeightArgs& A = p->wargs;
+    std::memset(&A, 0, sizeof(A));
+    A.mode = o.mode;
+    A.separable = o.separable ? 1 : 0;
+    A.tau = (float)o.tau;
+    A.tau_d = o.tau;
+    A.guard = 1e-5f;
+    A.a = o.a;
+    A.q = o.q;
+    A.e_minus = std::exp(-o.a / 2.0);
+    A.e_plus = std::exp(o.a / 2.0);
+    A.reach = (int)std::ceil(o.q) + 1;
+    if (p->fit_valid && p->fit_cache.a == A.a && p->fit_cache.q == A.q) {
+        A.vb = p->fit_cache.vb;
+        A.n0 = p->fit_cache.n0;
+        A.n1 = p->fit_cache.n1;
+        std::memcpy(A.c0, p->fit_cache.c0, sizeof(A.c0));
+        std::memcpy(A.c1, p->fit_cache.c1, sizeof(A.c1));
+    } else {
+        fit_weights(A);
+        p->fit_cache = A;
+        p->fit_valid = true;
+    }
+    STAGE_BEGIN(TFFR_STAGE_WEIGHTS);
+    if (N > 0 && o.mode == TFFR_WEIGHTS_USER) {
+        CK(grow(p, p->D, N));
+        CK(cudaMemcpyAsync(p->D.ptr, o.user_D, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+        A.user_D = p->D.ptr;
+    }
+    // Materialise D in the caller's order only when asked for, or for general
+    // points (whose kernels read it); the pulse-row kernels evaluate it inline.
+    const bool need_D = N > 0 && (D_out || n_kept || p->layout == TFFR_POINTS_GENERAL);
+    if (need_D) {
+        CK(grow(p, p->D, N));
         CK(cudaMemsetAsync(p->d_kept.ptr, 0, sizeof(unsigned long long), p->stream));
-        k_weights<<<grid_for(N, 256), 256, 0, p->stream>>>(N, p->keep_x.ptr, p->keep_y.ptr, p->Mx, p->My, wp,
-                                                          p->D.ptr, p->d_kept.ptr);
+        k_weights<<<grid_for(N, 256), 256, 0, p->stream>>>(N, p->lam_x, p->lam_y, p->Mx, p->My, A, p->D.ptr,
+                                                          p->d_kept.ptr);
         CK_LAUNCH("k_weights");
         if (p->layout == TFFR_POINTS_GENERAL) {
             k_gather_weights<<<grid_for(N, 256), 256, 0, p->stream>>>(N, p->perm.ptr, p->D.ptr, p->sD.ptr);
             CK_LAUNCH("k_gather_weights");
         }
-        STAGE_END(TFFR_STAGE_WEIGHTS);
         if (D_out)
             CK(cudaMemcpyAsync(D_out, p->D.ptr, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
     }
+    STAGE_END(TFFR_STAGE_WEIGHTS);
     if (n_kept) {
         unsigned long long k = 0;
         if (N > 0) {
