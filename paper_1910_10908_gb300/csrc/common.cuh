@@ -9,13 +9,7 @@
 
 namespace tffr {
 
-constexpr int kFftThreads = 512;        // threads of every FFT-pass CTA
 constexpr int kFftNMax = 8192;          // largest oversampled side (M <= 4096)
-constexpr int kColGroup = 16;           // x-modes per 128-byte line of the intermediate
-
-// Padded shared-memory index: one spare float2 every 16 keeps the strided
-// butterfly stores of the early Stockham stages off the same banks.
-__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 
 __device__ __forceinline__ int wrapmod(int c, int n) {  // n is a power of two
     return c & (n - 1);

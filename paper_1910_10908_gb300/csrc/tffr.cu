@@ -15,7 +15,7 @@
 
 #include "../../include/tffr.h"
 #include "common.cuh"
-#include "fft_smem.cuh"
+#include "fft_reg.cuh"
 #include "kernels_fft.cuh"
 #include "kernels_points.cuh"
 #include "kernels_spread.cuh"
@@ -50,7 +50,7 @@ struct tffr_plan_s {
     bool fit_valid = false;
 
     // plan-time tables and the intermediate of the FFT passes
-    DevBuf<float2> twx, twy, T;
+    DevBuf<float2> twh_x, twl_x, twh_y, twl_y, T;
     DevBuf<float> deap_x, deap_y;
     DevBuf<int> d_small;                   // [0] error flag, [1] scan sum
     DevBuf<unsigned long long> d_kept;
@@ -309,11 +309,12 @@ void fit_weights(WeightArgs& A) {
 }
 
 int upload_tables(tffr_plan_s* p) {
-    auto twiddles = [](int n) {
-        std::vector<float2> t(n);
+    // two-level twiddles of an n-point line: exp(2 pi i 64 h / n) and exp(2 pi i l / n)
+    auto level = [](int n, int count, int step) {
+        std::vector<float2> t(count);
         const double two_pi = 6.283185307179586476925286766559;
-        for (int m = 0; m < n; ++m) {
-            const double a = two_pi * (double)m / (double)n;
+        for (int m = 0; m < count; ++m) {
+            const double a = two_pi * (double)((int64_t)m * step % n) / (double)n;
             t[m] = make_float2((float)std::cos(a), (float)std::sin(a));
         }
         return t;
@@ -326,26 +327,32 @@ int upload_tables(tffr_plan_s* p) {
         for (int j = 0; j < M; ++j) d[j] = (float)(1.0 / ph[j]);
         return d;
     };
-    std::vector<float2> tx = twiddles(p->nx), ty = twiddles(p->ny);
+    const int nhx = std::max(1, p->nx / 64), nlx = std::min(64, p->nx);
+    const int nhy = std::max(1, p->ny / 64), nly = std::min(64, p->ny);
+    std::vector<float2> hx = level(p->nx, nhx, 64), lx = level(p->nx, nlx, 1);
+    std::vector<float2> hy = level(p->ny, nhy, 64), ly = level(p->ny, nly, 1);
     std::vector<float> dx = deapod(p->Mx, p->nx), dy = deapod(p->My, p->ny);
-    CK(grow(p, p->twx, p->nx));
-    CK(grow(p, p->twy, p->ny));
+    CK(grow(p, p->twh_x, nhx));
+    CK(grow(p, p->twl_x, nlx));
+    CK(grow(p, p->twh_y, nhy));
+    CK(grow(p, p->twl_y, nly));
     CK(grow(p, p->deap_x, p->Mx));
     CK(grow(p, p->deap_y, p->My));
-    CK(cudaMemcpyAsync(p->twx.ptr, tx.data(), tx.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
-    CK(cudaMemcpyAsync(p->twy.ptr, ty.data(), ty.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->twh_x.ptr, hx.data(), hx.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->twl_x.ptr, lx.data(), lx.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->twh_y.ptr, hy.data(), hy.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->twl_y.ptr, ly.data(), ly.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
     CK(cudaMemcpyAsync(p->deap_x.ptr, dx.data(), dx.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     CK(cudaMemcpyAsync(p->deap_y.ptr, dy.data(), dy.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
     CK(cudaStreamSynchronize(p->stream));   // the host vectors end with this scope
     return TFFR_OK;
 }
 
-constexpr int kFftSmemMax = (kFftNMax + kFftNMax / 16) * (int)sizeof(float2);
 constexpr int kSpreadSmemMax = kSpreadStageBytes + kFftNMax * (int)sizeof(float2);
 
 template <typename K>
-cudaError_t smem_attr(K kernel, int bytes) {
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+cudaError_t smem_attr(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename VT>
@@ -354,7 +361,18 @@ cudaError_t spread_attrs() {
     if (e == cudaSuccess) e = smem_attr(k_spread_rows<VT, 4>, kSpreadSmemMax);
     if (e == cudaSuccess) e = smem_attr(k_spread_rows<VT, 6>, kSpreadSmemMax);
     if (e == cudaSuccess) e = smem_attr(k_spread_rows<VT, 8>, kSpreadSmemMax);
-    if (e == cudaSuccess) e = smem_attr(k_adj_rows_general<VT>, kFftSmemMax);
+    return e;
+}
+
+template <int V>
+cudaError_t line_attrs() {
+    const size_t b = line_smem_bytes<V>(kFftNMax);
+    cudaError_t e = smem_attr(k_adj_rows<V>, b);
+    if (e == cudaSuccess) e = smem_attr(k_adj_rows_general<V>, b);
+    if (e == cudaSuccess) e = smem_attr(k_adj_cols<V>, b);
+    if (e == cudaSuccess) e = smem_attr(k_fwd_cols<V>, b);
+    if (e == cudaSuccess) e = smem_attr(k_fwd_rows<V, true>, b);
+    if (e == cudaSuccess) e = smem_attr(k_fwd_rows<V, false>, b);
     return e;
 }
 
@@ -363,11 +381,11 @@ int set_kernel_attributes(tffr_plan_s* p) {
     CK(cudaGetDevice(&dev));
     static bool done[64] = {false};
     if (dev < 64 && done[dev]) return TFFR_OK;
-    CK(smem_attr(k_adj_rows, kFftSmemMax));
-    CK(smem_attr(k_adj_cols, kFftSmemMax));
-    CK(smem_attr(k_fwd_cols, kFftSmemMax));
-    CK(smem_attr(k_fwd_rows<true>, kFftSmemMax));
-    CK(smem_attr(k_fwd_rows<false>, kFftSmemMax));
+    CK(line_attrs<2>());
+    CK(line_attrs<4>());
+    CK(line_attrs<8>());
+    CK(line_attrs<16>());
+    CK(line_attrs<32>());
     CK(spread_attrs<float2>());
     CK(spread_attrs<double2>());
     CK(spread_attrs<__half2>());
@@ -522,10 +540,18 @@ int build_general(tffr_plan_s* p) {
     return TFFR_OK;
 }
 
-size_t fft_smem_bytes(const tffr_plan_s* p) {
-    const int n = std::max(p->nx, p->ny);
-    return (size_t)(n + n / 16) * sizeof(float2);
-}
+FftTables tables_x(const tffr_plan_s* p) { return FftTables{p->twh_x.ptr, p->twl_x.ptr}; }
+FftTables tables_y(const tffr_plan_s* p) { return FftTables{p->twh_y.ptr, p->twl_y.ptr}; }
+
+// Launch one line kernel family member for the values-per-thread of an n-point line.
+#define LINE_DISPATCH(n, LAUNCH)                \
+    switch (line_v(n)) {                        \
+        case 32: LAUNCH(32); break;             \
+        case 16: LAUNCH(16); break;             \
+        case 8: LAUNCH(8); break;               \
+        case 4: LAUNCH(4); break;               \
+        default: LAUNCH(2); break;              \
+    }
 
 template <typename VT, int W>
 void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values) {
@@ -536,7 +562,7 @@ void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values) {
 
 template <typename VT>
 int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
-    const size_t fsm = fft_smem_bytes(p);
+    const int nx = p->nx, ny = p->ny;
     if (p->layout == TFFR_POINTS_ROWS) {
         const RowsView rv = rows_view(p);
         STAGE_BEGIN(TFFR_STAGE_SPREAD);
@@ -549,21 +575,37 @@ int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
         CK_LAUNCH("k_spread_rows");
         STAGE_END(TFFR_STAGE_SPREAD);
         STAGE_BEGIN(TFFR_STAGE_ROW_FFT);
-        k_adj_rows<<<p->ny, kFftThreads, fsm, p->stream>>>(rv, p->R.ptr, p->nx, p->lognx, p->ny, p->Mx, p->w,
-                                                           p->taps, p->twx.ptr, p->deap_x.ptr, p->T.ptr);
+#define ADJ_ROWS(V)                                                                                          \
+    k_adj_rows<V><<<ny, nx / V, line_smem_bytes<V>(nx), p->stream>>>(rv, p->R.ptr, nx, p->lognx, ny, p->Mx, \
+                                                                     p->w, p->taps, tables_x(p),            \
+                                                                     p->deap_x.ptr, p->T.ptr)
+        LINE_DISPATCH(nx, ADJ_ROWS)
+#undef ADJ_ROWS
         CK_LAUNCH("k_adj_rows");
         STAGE_END(TFFR_STAGE_ROW_FFT);
     } else {
         STAGE_BEGIN(TFFR_STAGE_ROW_FFT);
-        k_adj_rows_general<VT><<<p->ny, kFftThreads, fsm, p->stream>>>(general_view(p), values, p->nx, p->lognx,
-                                                                        p->ny, p->Mx, p->w, p->taps, p->twx.ptr,
-                                                                        p->deap_x.ptr, p->T.ptr);
+        k_gather_values<VT><<<grid_for(p->N, 256), 256, 0, p->stream>>>(p->N, p->perm.ptr, values, p->sD.ptr,
+                                                                         p->acc.ptr);
+        CK_LAUNCH("k_gather_values");
+        const GeneralView gv = general_view(p);
+#define ADJ_ROWS_G(V)                                                                                        \
+    k_adj_rows_general<V><<<ny, nx / V, line_smem_bytes<V>(nx), p->stream>>>(gv, p->acc.ptr, nx, p->lognx, \
+                                                                             ny, p->Mx, p->w, p->taps,     \
+                                                                             tables_x(p), p->deap_x.ptr,   \
+                                                                             p->T.ptr)
+        LINE_DISPATCH(nx, ADJ_ROWS_G)
+#undef ADJ_ROWS_G
         CK_LAUNCH("k_adj_rows_general");
         STAGE_END(TFFR_STAGE_ROW_FFT);
     }
     STAGE_BEGIN(TFFR_STAGE_COL_FFT);
-    k_adj_cols<<<p->Mx, kFftThreads, fsm, p->stream>>>(p->T.ptr, p->ny, p->logny, p->My, p->Mx, p->twy.ptr,
-                                                       p->deap_y.ptr, image);
+#define ADJ_COLS(V)                                                                                          \
+    k_adj_cols<V><<<p->Mx, ny / V, line_smem_bytes<V>(ny), p->stream>>>(p->T.ptr, ny, p->logny, p->My,    \
+                                                                        p->Mx, tables_y(p), p->deap_y.ptr, \
+                                                                        image)
+    LINE_DISPATCH(ny, ADJ_COLS)
+#undef ADJ_COLS
     CK_LAUNCH("k_adj_cols");
     STAGE_END(TFFR_STAGE_COL_FFT);
     return TFFR_OK;
@@ -577,19 +619,27 @@ void launch_interp(tffr_plan_s* p, const RowsView& rv, void* values, int apply_w
 
 template <typename VT>
 int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_weights) {
-    const size_t fsm = fft_smem_bytes(p);
+    const int nx = p->nx, ny = p->ny;
     STAGE_BEGIN(TFFR_STAGE_FWD_COL_FFT);
-    k_fwd_cols<<<p->Mx, kFftThreads, fsm, p->stream>>>(image, p->ny, p->logny, p->My, p->Mx, p->twy.ptr,
-                                                       p->deap_y.ptr, p->deap_x.ptr, p->T.ptr);
+#define FWD_COLS(V)                                                                                          \
+    k_fwd_cols<V><<<p->Mx, ny / V, line_smem_bytes<V>(ny), p->stream>>>(image, ny, p->logny, p->My, p->Mx, \
+                                                                        tables_y(p), p->deap_y.ptr,        \
+                                                                        p->deap_x.ptr, p->T.ptr)
+    LINE_DISPATCH(ny, FWD_COLS)
+#undef FWD_COLS
     CK_LAUNCH("k_fwd_cols");
     STAGE_END(TFFR_STAGE_FWD_COL_FFT);
     STAGE_BEGIN(TFFR_STAGE_FWD_ROW_FFT);
+    const RowsView rv = rows_view(p);
+    const GeneralView gv = general_view(p);
     if (p->layout == TFFR_POINTS_ROWS) {
         CK(cudaMemsetAsync(p->R.ptr, 0, (size_t)p->R_cells * sizeof(float2), p->stream));
-        const RowsView rv = rows_view(p);
-        k_fwd_rows<true><<<p->ny, kFftThreads, fsm, p->stream>>>(rv, general_view(p), p->T.ptr, p->nx, p->lognx,
-                                                                 p->ny, p->Mx, p->w, p->taps, p->twx.ptr, p->R.ptr,
-                                                                 p->acc.ptr);
+#define FWD_ROWS_R(V)                                                                                        \
+    k_fwd_rows<V, true><<<ny, nx / V, line_smem_bytes<V>(nx), p->stream>>>(rv, gv, p->T.ptr, nx, p->lognx, \
+                                                                           ny, p->Mx, p->w, p->taps,       \
+                                                                           tables_x(p), p->R.ptr, p->acc.ptr)
+        LINE_DISPATCH(nx, FWD_ROWS_R)
+#undef FWD_ROWS_R
         CK_LAUNCH("k_fwd_rows");
         STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
         STAGE_BEGIN(TFFR_STAGE_INTERP);
@@ -603,9 +653,12 @@ int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_we
         STAGE_END(TFFR_STAGE_INTERP);
     } else {
         CK(cudaMemsetAsync(p->acc.ptr, 0, (size_t)p->N * sizeof(float2), p->stream));
-        k_fwd_rows<false><<<p->ny, kFftThreads, fsm, p->stream>>>(rows_view(p), general_view(p), p->T.ptr, p->nx,
-                                                                  p->lognx, p->ny, p->Mx, p->w, p->taps, p->twx.ptr,
-                                                                  p->R.ptr, p->acc.ptr);
+#define FWD_ROWS_G(V)                                                                                         \
+    k_fwd_rows<V, false><<<ny, nx / V, line_smem_bytes<V>(nx), p->stream>>>(rv, gv, p->T.ptr, nx, p->lognx, \
+                                                                            ny, p->Mx, p->w, p->taps,       \
+                                                                            tables_x(p), p->R.ptr, p->acc.ptr)
+        LINE_DISPATCH(nx, FWD_ROWS_G)
+#undef FWD_ROWS_G
         CK_LAUNCH("k_fwd_rows");
         STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
         STAGE_BEGIN(TFFR_STAGE_INTERP);
@@ -704,7 +757,7 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
 int tffr_destroy(tffr_plan_t p) {
     if (!p) return TFFR_OK;
     cudaStreamSynchronize(p->stream);
-    release(p->twx); release(p->twy); release(p->T); release(p->deap_x); release(p->deap_y);
+    release(p->twh_x); release(p->twl_x); release(p->twh_y); release(p->twl_y); release(p->T); release(p->deap_x); release(p->deap_y);
     release(p->d_small); release(p->d_kept); release(p->D); release(p->tiles);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly); release(p->bucket_rows);
     release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);
