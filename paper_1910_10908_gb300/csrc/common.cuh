@@ -20,7 +20,38 @@ __device__ __forceinline__ int wrapmod(int c, int n) {  // n is a power of two
 // on this GPU).  The fraction is rounded to FP32 (it may round up to 1.0f,
 // which places the sample on the next cell edge: the taps stay consistent).
 // Returns false for |v| >= 2^28, infinities and NaN.
+static __device__ __noinline__ bool fine_coord_general(double v, int& cell, float& frac);
+
 __device__ __forceinline__ bool fine_coord(double v, int& cell, float& frac) {
+    // Fast path for 1 <= |2v| < 2^21 with 32-bit integer operations: the
+    // significand is mh * 2^32 + lo (mh has 21 bits) and |2v| = m 2^-sh.
+    const int hi = __double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const int sh = 1074 - ((hi >> 20) & 0x7ff);
+    if (sh >= 32 && sh <= 52) {
+        const unsigned mh = ((unsigned)hi & 0xFFFFFu) | 0x100000u;
+        const int s = sh - 32;                                   // 0..20
+        const unsigned I = mh >> s;
+        const unsigned fh = mh & ((1u << s) - 1u);
+        const float f = fmaf(__uint2float_rn(lo), __int_as_float((127 - sh) << 23),
+                             __uint2float_rn(fh) * __int_as_float((127 - s) << 23));
+        if (hi >= 0) {
+            cell = (int)I;
+            frac = f;
+        } else if (f == 0.0f) {
+            cell = -(int)I;
+            frac = 0.0f;
+        } else {
+            cell = -(int)I - 1;
+            frac = 1.0f - f;
+        }
+        return true;
+    }
+    return fine_coord_general(v, cell, frac);
+}
+
+// Any magnitude (see fine_coord): 64-bit integer operations.
+static __device__ __noinline__ bool fine_coord_general(double v, int& cell, float& frac) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int e = (int)((b >> 52) & 0x7ffu);
     cell = 0;

@@ -1,15 +1,17 @@
-// Block-wide complex FFT of one line of n = 2^logn points (32 <= n <= 8192),
+// Block-wide complex FFT of one line of N = 2^LOGN points (32 <= N <= 8192),
 //
-//     X[k] = sum_{j<n} x[j] exp(sgn * 2 pi i j k / n),   sgn = +1 or -1,
+//     X[k] = sum_{j<N} x[j] exp(sgn * 2 pi i j k / N),   sgn = +1 or -1,
 //
-// computed by T = n / V threads that each hold V points in registers
-// (Stockham autosort; stages of radix V, then one smaller radix for the rest).
-// Between stages the line goes through padded shared memory (one spare slot
-// per V points, which keeps the strided stores of the first stage on distinct
-// banks).  Inner DFTs of radix 2..32 are unrolled with constant roots of
-// unity; the inter-stage twiddles exp(2 pi i m / n) come from a two-level
-// table (exp(2 pi i 64 h / n) * exp(2 pi i l / n), m = 64 h + l) staged in
-// shared memory, both levels built in FP64 on the host.
+// computed by T = N / V threads that each hold V points in registers
+// (Stockham autosort: stages of radix V, then one smaller radix for the
+// rest).  Between stages the line goes through padded shared memory (one
+// spare slot per V points keeps the strided stores of the first stage on
+// distinct banks).  The line length is a template parameter, so every index,
+// stride and twiddle shift is a compile-time constant.  Inner DFTs of radix
+// 2..32 are unrolled with constant roots of unity; the inter-stage twiddles
+// exp(2 pi i m / N) come from a two-level table (exp(2 pi i 64 h / N) *
+// exp(2 pi i l / N), m = 64 h + l) staged in shared memory, both levels built
+// in FP64 on the host.
 #pragma once
 
 #include "common.cuh"
@@ -43,10 +45,6 @@ __device__ __forceinline__ float2 rot32(float2 z, float sgn) {
 
 template <int R> struct Dft;
 
-template <> struct Dft<1> {
-    static __device__ __forceinline__ void run(float2*, float) {}
-};
-
 template <> struct Dft<2> {
     static __device__ __forceinline__ void run(float2* v, float) {
         const float2 a = v[0], b = v[1];
@@ -67,6 +65,26 @@ template <> struct Dft<4> {
     }
 };
 
+// w^k O[k] for radix R, w = exp(sgn 2 pi i / R)
+template <int R, int K>
+__device__ __forceinline__ float2 rotR(float2 z, float sgn) {
+    return rot32<(32 / R) * K>(z, sgn);
+}
+
+template <int R, int K>
+struct Combine {
+    static __device__ __forceinline__ void run(float2* v, const float2* e, const float2* o, float sgn) {
+        const float2 t = rotR<R, K>(o[K], sgn);
+        v[K] = cadd(e[K], t);
+        v[K + R / 2] = csub(e[K], t);
+        Combine<R, K + 1>::run(v, e, o, sgn);
+    }
+};
+template <int R>
+struct Combine<R, R / 2> {
+    static __device__ __forceinline__ void run(float2*, const float2*, const float2*, float) {}
+};
+
 // radix 2 x radix R/2 split: X[k] = E[k] + w^k O[k], X[k + R/2] = E[k] - w^k O[k]
 template <int R>
 __device__ __forceinline__ void dft_split2(float2* v, float sgn) {
@@ -79,45 +97,7 @@ __device__ __forceinline__ void dft_split2(float2* v, float sgn) {
     }
     Dft<H>::run(e, sgn);
     Dft<H>::run(o, sgn);
-#pragma unroll
-    for (int k = 0; k < H; ++k) {
-        float2 t;
-        if (R == 8) {
-            t = (k == 0) ? o[k] : (k == 1) ? rot32<4>(o[k], sgn) : (k == 2) ? rot32<8>(o[k], sgn) : rot32<12>(o[k], sgn);
-        } else if (R == 16) {
-            switch (k) {
-                case 0: t = o[0]; break;
-                case 1: t = rot32<2>(o[1], sgn); break;
-                case 2: t = rot32<4>(o[2], sgn); break;
-                case 3: t = rot32<6>(o[3], sgn); break;
-                case 4: t = rot32<8>(o[4], sgn); break;
-                case 5: t = rot32<10>(o[5], sgn); break;
-                case 6: t = rot32<12>(o[6], sgn); break;
-                default: t = rot32<14>(o[7], sgn); break;
-            }
-        } else {
-            switch (k) {
-                case 0: t = o[0]; break;
-                case 1: t = rot32<1>(o[1], sgn); break;
-                case 2: t = rot32<2>(o[2], sgn); break;
-                case 3: t = rot32<3>(o[3], sgn); break;
-                case 4: t = rot32<4>(o[4], sgn); break;
-                case 5: t = rot32<5>(o[5], sgn); break;
-                case 6: t = rot32<6>(o[6], sgn); break;
-                case 7: t = rot32<7>(o[7], sgn); break;
-                case 8: t = rot32<8>(o[8], sgn); break;
-                case 9: t = rot32<9>(o[9], sgn); break;
-                case 10: t = rot32<10>(o[10], sgn); break;
-                case 11: t = rot32<11>(o[11], sgn); break;
-                case 12: t = rot32<12>(o[12], sgn); break;
-                case 13: t = rot32<13>(o[13], sgn); break;
-                case 14: t = rot32<14>(o[14], sgn); break;
-                default: t = rot32<15>(o[15], sgn); break;
-            }
-        }
-        v[k] = cadd(e[k], t);
-        v[k + H] = csub(e[k], t);
-    }
+    Combine<R, 0>::run(v, e, o, sgn);
 }
 
 template <> struct Dft<8> {
@@ -130,131 +110,148 @@ template <> struct Dft<32> {
     static __device__ __forceinline__ void run(float2* v, float sgn) { dft_split2<32>(v, sgn); }
 };
 
-// Stage plan: radix V stages first, then one stage of radix 2^(logn mod log2 V).
-struct LineFft {
-    int n, logn;
-    const float2* twh;      // shared: exp(2 pi i 64 h / n), h < max(1, n/64)
-    const float2* twl;      // shared: exp(2 pi i l / n), l < min(64, n)
-    float sgn;
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
+// Values per thread for an N-point line.
+__host__ __device__ constexpr int line_v(int n) {
+    return n >= 8192 ? 32 : n >= 512 ? 16 : n >= 256 ? 8 : n >= 128 ? 4 : 2;
+}
+
+template <int LOGN>
+struct Line {
+    static constexpr int N = 1 << LOGN;
+    static constexpr int V = line_v(N);
+    static constexpr int LV = ilog2c(V);
+    static constexpr int T = N / V;                       // threads
+    static constexpr int NFULL = LOGN / LV;               // radix-V stages
+    static constexpr int REM = LOGN - NFULL * LV;         // log2 of the last radix (0: none)
+    static constexpr int PADLEN = N + N / V + 1;          // padded shared line
+    static constexpr int NH = N >= 64 ? N / 64 : 1;       // twiddle table levels
+    static constexpr int NL = N >= 64 ? 64 : N;
+    static constexpr int SMEM_ELEMS = PADLEN + 128 + 64;
+    __device__ __forceinline__ static int pad(int i) { return i + (i >> LV); }
 };
 
-__device__ __forceinline__ float2 twiddle(const LineFft& L, int m) {
-    return cmul(L.twh[m >> 6], L.twl[m & 63]);
-}
+struct Twiddles {
+    const float2* h;        // shared: exp(2 pi i 64 h / N)
+    const float2* l;        // shared: exp(2 pi i l / N)
+    __device__ __forceinline__ float2 operator()(int m) const { return cmul(h[m >> 6], l[m & 63]); }
+};
 
-template <int V>
-__device__ __forceinline__ int fft_pad(int i) {
-    constexpr int S = (V >= 32) ? 5 : (V >= 16) ? 4 : (V >= 8) ? 3 : (V >= 4) ? 2 : 1;
-    return i + (i >> S);
-}
-
-template <int V>
-__host__ __device__ constexpr int fft_pad_len(int n) {
-    return n + n / (V >= 32 ? 32 : V >= 16 ? 16 : V >= 8 ? 8 : V >= 4 ? 4 : 2) + 1;
-}
-
-// Registers v hold the stage input in the pattern v[b*R + r] = x[j_b + r n/R],
-// j_b = tid + b T (T = n / V threads, B = V / R butterflies each).  Apply the
-// stage's twiddles and DFTs in place.
-template <int V, int R, int LOGR>
-__device__ __forceinline__ void stage_compute(float2 (&v)[V], const LineFft& L, int logNs) {
-    constexpr int B = V / R;
-    const int T = L.n / V;
-    const int Ns = 1 << logNs;
-    const int tshift = L.logn - logNs - LOGR;
+// Registers v hold the stage input as v[b*R + r] = x[j_b + r N/R], j_b = tid + b T
+// (B = V / R butterflies per thread).  Apply twiddles and DFTs in place.
+template <int LOGN, int R, int LOGNS>
+__device__ __forceinline__ void stage_compute(float2 (&v)[Line<LOGN>::V], const Twiddles& tw, float sgn) {
+    using L = Line<LOGN>;
+    constexpr int B = L::V / R;
+    constexpr int NS = 1 << LOGNS;
+    constexpr int TSHIFT = LOGN - LOGNS - ilog2c(R);
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        const int j = threadIdx.x + b * T;
-        const int k = j & (Ns - 1);
-        if (k != 0) {
+        if (NS > 1) {
+            const int k = (threadIdx.x + b * L::T) & (NS - 1);
+            if (k != 0) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                float2 t = twiddle(L, (r * k) << tshift);
-                t.y *= L.sgn;
-                v[b * R + r] = cmul(v[b * R + r], t);
+                for (int r = 1; r < R; ++r) {
+                    float2 t = tw((r * k) << TSHIFT);
+                    t.y *= sgn;
+                    v[b * R + r] = cmul(v[b * R + r], t);
+                }
             }
         }
-        Dft<R>::run(&v[b * R], L.sgn);
+        Dft<R>::run(&v[b * R], sgn);
     }
 }
 
-template <int V, int R>
-__device__ __forceinline__ void stage_load(float2 (&v)[V], const float2* buf, int n) {
-    constexpr int B = V / R;
-    const int T = n / V;
-    const int stride = n / R;
+template <int LOGN, int R>
+__device__ __forceinline__ void stage_load(float2 (&v)[Line<LOGN>::V], const float2* buf) {
+    using L = Line<LOGN>;
+    constexpr int B = L::V / R;
 #pragma unroll
     for (int b = 0; b < B; ++b)
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[b * R + r] = buf[fft_pad<V>(threadIdx.x + b * T + r * stride)];
+        for (int r = 0; r < R; ++r) v[b * R + r] = buf[L::pad(threadIdx.x + b * L::T + r * (L::N / R))];
 }
 
-template <int V, int R, int LOGR>
-__device__ __forceinline__ void stage_store(const float2 (&v)[V], float2* buf, int n, int logNs) {
-    constexpr int B = V / R;
-    const int T = n / V;
-    const int Ns = 1 << logNs;
+template <int LOGN, int R, int LOGNS>
+__device__ __forceinline__ void stage_store(const float2 (&v)[Line<LOGN>::V], float2* buf) {
+    using L = Line<LOGN>;
+    constexpr int B = L::V / R;
+    constexpr int NS = 1 << LOGNS;
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        const int j = threadIdx.x + b * T;
-        const int k = j & (Ns - 1);
-        const int base = ((j - k) << LOGR) + k;
+        const int j = threadIdx.x + b * L::T;
+        const int k = j & (NS - 1);
+        const int base = ((j - k) * R) + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[fft_pad<V>(base + r * Ns)] = v[b * R + r];
+        for (int r = 0; r < R; ++r) buf[L::pad(base + r * NS)] = v[b * R + r];
     }
 }
 
-// One full radix-R stage in shared memory: load, sync, compute, store, sync.
-template <int V, int R, int LOGR>
-__device__ __forceinline__ void stage_smem(float2* buf, const LineFft& L, int logNs) {
-    float2 v[V];
-    stage_load<V, R>(v, buf, L.n);
+// One full stage in shared memory: load, sync, compute, store, sync.
+template <int LOGN, int R, int LOGNS>
+__device__ __forceinline__ void stage_smem(float2* buf, const Twiddles& tw, float sgn) {
+    float2 v[Line<LOGN>::V];
+    stage_load<LOGN, R>(v, buf);
     __syncthreads();
-    stage_compute<V, R, LOGR>(v, L, logNs);
-    stage_store<V, R, LOGR>(v, buf, L.n, logNs);
+    stage_compute<LOGN, R, LOGNS>(v, tw, sgn);
+    stage_store<LOGN, R, LOGNS>(v, buf);
     __syncthreads();
 }
 
-template <int V> struct LogOf;
-template <> struct LogOf<2> { static constexpr int v = 1; };
-template <> struct LogOf<4> { static constexpr int v = 2; };
-template <> struct LogOf<8> { static constexpr int v = 3; };
-template <> struct LogOf<16> { static constexpr int v = 4; };
-template <> struct LogOf<32> { static constexpr int v = 5; };
-
-// Remainder stage of radix 2^rem < V, dispatched at run time.
-template <int V>
-__device__ __forceinline__ void stage_rem_smem(float2* buf, const LineFft& L, int logNs, int rem) {
-    switch (rem) {
-        case 1: stage_smem<V, 2, 1>(buf, L, logNs); break;
-        case 2: if constexpr (V >= 4) stage_smem<V, 4, 2>(buf, L, logNs); break;
-        case 3: if constexpr (V >= 8) stage_smem<V, 8, 3>(buf, L, logNs); break;
-        case 4: if constexpr (V >= 16) stage_smem<V, 16, 4>(buf, L, logNs); break;
-        default: break;
+// Stages S..NFULL-1 of radix V (S counts from 0), as a compile-time recursion.
+template <int LOGN, int S, int STOP>
+struct FullStages {
+    static __device__ __forceinline__ void run(float2* buf, const Twiddles& tw, float sgn) {
+        using L = Line<LOGN>;
+        stage_smem<LOGN, L::V, S * L::LV>(buf, tw, sgn);
+        FullStages<LOGN, S + 1, STOP>::run(buf, tw, sgn);
     }
-}
+};
+template <int LOGN, int STOP>
+struct FullStages<LOGN, STOP, STOP> {
+    static __device__ __forceinline__ void run(float2*, const Twiddles&, float) {}
+};
 
-// Whole FFT in shared memory (buf indexed with fft_pad<V>); the caller has
-// synchronised after filling buf, and buf holds the result, in natural order,
+// Whole FFT in shared memory (indexed with Line<LOGN>::pad); the caller has
+// synchronised after filling buf; the result is in buf, in natural order,
 // after the call (which ends with a barrier).
-template <int V>
-__device__ __forceinline__ void fft_line_smem(float2* buf, const LineFft& L) {
-    constexpr int LV = LogOf<V>::v;
-    int logNs = 0;
-    while (logNs + LV <= L.logn) {
-        stage_smem<V, V, LV>(buf, L, logNs);
-        logNs += LV;
-    }
-    if (logNs < L.logn) stage_rem_smem<V>(buf, L, logNs, L.logn - logNs);
+template <int LOGN>
+__device__ __forceinline__ void fft_line_smem(float2* buf, const Twiddles& tw, float sgn) {
+    using L = Line<LOGN>;
+    FullStages<LOGN, 0, L::NFULL>::run(buf, tw, sgn);
+    if constexpr (L::REM > 0) stage_smem<LOGN, (1 << L::REM), L::NFULL * L::LV>(buf, tw, sgn);
 }
 
-// Load the two-level twiddle table of an n-point line into shared memory.
-__device__ __forceinline__ void load_twiddles(float2* s_twh, float2* s_twl, const float2* __restrict__ twh,
-                                              const float2* __restrict__ twl, int n) {
-    const int nh = n >= 64 ? n / 64 : 1;
-    const int nl = n >= 64 ? 64 : n;
-    for (int i = threadIdx.x; i < nh; i += blockDim.x) s_twh[i] = twh[i];
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) s_twl[i] = twl[i];
+// As fft_line_smem, but the last stage hands each output to epi(index, value)
+// from registers instead of storing it (no barrier after; the stage's loads
+// are complete, so the epilogue may write buf).
+template <int LOGN, typename Epi>
+__device__ __forceinline__ void fft_line_epilogue(float2* buf, const Twiddles& tw, float sgn, Epi& epi) {
+    using L = Line<LOGN>;
+    constexpr int NSMEM = L::REM ? L::NFULL : L::NFULL - 1;
+    constexpr int R = L::REM ? (1 << L::REM) : L::V;
+    constexpr int LOGNS = NSMEM * L::LV;
+    FullStages<LOGN, 0, NSMEM>::run(buf, tw, sgn);
+    float2 v[L::V];
+    stage_load<LOGN, R>(v, buf);
+    __syncthreads();
+    stage_compute<LOGN, R, LOGNS>(v, tw, sgn);
+    constexpr int B = L::V / R;
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+        for (int r = 0; r < R; ++r) epi(threadIdx.x + b * L::T + r * (L::N / R), v[b * R + r]);
+}
+
+// Load the two-level twiddle table of an N-point line into shared memory.
+template <int LOGN>
+__device__ __forceinline__ Twiddles load_twiddles(float2* s_twh, float2* s_twl, const float2* __restrict__ twh,
+                                                  const float2* __restrict__ twl) {
+    using L = Line<LOGN>;
+    for (int i = threadIdx.x; i < L::NH; i += L::T) s_twh[i] = twh[i];
+    for (int i = threadIdx.x; i < L::NL; i += L::T) s_twl[i] = twl[i];
+    return Twiddles{s_twh, s_twl};
 }
 
 }  // namespace tffr

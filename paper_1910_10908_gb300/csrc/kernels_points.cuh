@@ -24,6 +24,7 @@ namespace tffr {
 // threshold decision is always made in FP64.
 // ---------------------------------------------------------------------------
 constexpr int kGCoefs = 16;
+constexpr int kG0Coefs = 12;       // piece 0 (the whole range for integer q): fixed length
 
 struct WeightArgs {
     int mode;              // 0 tFFR, 1 unit, 2 user (per-sample array)
@@ -32,7 +33,7 @@ struct WeightArgs {
     double tau_d;
     // fitted G: piece 0 on v in [0, vb] as a polynomial in s = 2 (v/vb)^2 - 1;
     // piece 1 on v in [vb, 1/2] as a polynomial in s = (2v - vb - 1/2)/(1/2 - vb)
-    float vb;
+    float vb, inv_vb;
     int n0, n1;
     float c0[kGCoefs], c1[kGCoefs];
     // closed-form parameters
@@ -100,8 +101,12 @@ __device__ __forceinline__ float g_fitted(int cell, float f, int M, const Weight
     const float v = fabsf(delta - 0.5f);
     if (v == A.vb || v == 0.5f) exact = true;                    // on a breakpoint of the truncation
     if (v < A.vb) {
-        const float r = v / A.vb;
-        return horner(A.c0, A.n0, 2.0f * r * r - 1.0f);
+        const float r = v * A.inv_vb;
+        const float s = fmaf(2.0f * r, r, -1.0f);
+        float g = A.c0[kG0Coefs - 1];
+#pragma unroll
+        for (int k = kG0Coefs - 2; k >= 0; --k) g = fmaf(g, s, A.c0[k]);
+        return g;
     }
     return horner(A.c1, A.n1, (2.0f * v - A.vb - 0.5f) / (0.5f - A.vb));
 }
@@ -120,7 +125,7 @@ __device__ __forceinline__ float weight_tffr(double lam_x, int cx, float fx, dou
     bool exact = false;
     float G = g_fitted(cx, fx, Mx, A, exact);
     if (A.separable) G *= g_fitted(cy, fy, My, A, exact);
-    const float d = (G != 0.0f) ? 1.0f / G : 0.0f;
+    const float d = (G != 0.0f) ? __frcp_rn(G) : 0.0f;
     if (!exact && fabsf(d - A.tau) > A.guard * fabsf(A.tau)) return (d >= A.tau) ? d : 0.0f;
     return weight_exact(lam_x, lam_y, Mx, My, A);
 }

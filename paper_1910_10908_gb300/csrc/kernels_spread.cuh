@@ -9,21 +9,10 @@
 
 #include "common.cuh"
 #include "kernels_points.cuh"
+#include "types.cuh"
 
 namespace tffr {
 
-struct RowsView {
-    int P;                          // pulse rows
-    const int* row_start;           // [P] first sample of the row (rows are contiguous runs)
-    const int* row_clo;             // [P] first fine x cell of the row buffer
-    const int* row_len;             // [P] cells in the row buffer (nx: periodic row)
-    const int* row_ly;              // [P] fine y cell floor(2 lam_y)
-    const float* row_fy;            // [P] fine y offset in [0, 1]
-    const double* row_lam_y;        // [P] lam_y of the row
-    const int64_t* row_off;         // [P] offset of the row buffer in R (cells)
-    const int* bucket_start;        // [ny + 1] rows grouped by row_ly mod ny
-    const int* bucket_rows;         // [P]
-};
 
 constexpr int kSpreadThreads = 256;
 constexpr int kSpreadPerThread = 8;                      // samples per thread per staged tile
@@ -102,7 +91,7 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
             } else {
                 bool exact = gy_exact;
                 float G = g_fitted(cell, f, Mx, wa, exact) * gy;
-                d = (G != 0.0f) ? 1.0f / G : 0.0f;
+                d = (G != 0.0f) ? __frcp_rn(G) : 0.0f;
                 if (exact || !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau)))
                     d = weight_exact(lam, lam_y_row, Mx, My, wa);
                 else if (d < wa.tau)
@@ -189,7 +178,7 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
             } else if (wa.mode == 0) {
                 bool exact = gy_exact;
                 float G = g_fitted(cell, f, Mx, wa, exact) * gy;
-                d = (G != 0.0f) ? 1.0f / G : 0.0f;
+                d = (G != 0.0f) ? __frcp_rn(G) : 0.0f;
                 if (exact || !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau)))
                     d = weight_exact(lam, lam_y_row, Mx, My, wa);
                 else if (d < wa.tau)
@@ -198,6 +187,14 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
         }
         ValueIO<VT>::store(out, n, cscale(acc, d));
     }
+}
+
+// General points: values in bucket order, weighted and converted to FP32.
+template <typename VT>
+__global__ void k_gather_values(int64_t N, const int* __restrict__ perm, const void* __restrict__ values,
+                                const float* __restrict__ sD, float2* __restrict__ sval) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
+        sval[q] = cscale(ValueIO<VT>::load(values, perm[q]), sD[q]);
 }
 
 // Forward, general points: y_{perm[q]} = D * acc[q].

@@ -1,0 +1,333 @@
+// The two FFT passes of the adjoint and of the forward twin, with the azimuth
+// taps, the mode pruning and the deapodisation fused in.
+//
+// Adjoint (type 1): grid b = spread of D_n v_n; B = FFT_{+}(b) over the
+// 2M_y x 2M_x fine grid; image f[jy][jx] = B[ky mod 2My][kx mod 2Mx] /
+// (phi_hat(kx / 2Mx) phi_hat(ky / 2My)), k = j - M/2 (Eq. (Anu): spread,
+// inverse FFT, divide by the window transform; Algorithm 1's final IFFT).
+//
+//   pass 1 (one CTA per fine row r): build row r in shared memory from the
+//     pulse-row buffers R (azimuth taps) or from bucketed samples, FFT along
+//     x, keep the M_x wanted modes, multiply by 1/phi_hat(kx), store row r of
+//     the intermediate T ([2M_y][M_x] complex64, row-major).
+//   pass 2 (clusters of 4 CTAs, one wanted x mode each): the cluster reads
+//     32-byte row chunks of T (4 columns) and scatters them to its CTAs
+//     through distributed shared memory; each CTA FFTs its column along y,
+//     keeps the M_y wanted modes and multiplies by 1/phi_hat(ky); the cluster
+//     gathers the results back and stores 32-byte chunks of 4 image columns.
+//
+// The forward runs the transposed steps in reverse order with FFT sign -1.
+// Every kernel is a template on log2 of its line length.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "fft_reg.cuh"
+#include "types.cuh"
+
+namespace tffr {
+
+namespace cg = cooperative_groups;
+
+constexpr int kColCluster = 4;
+
+__device__ __forceinline__ void atomic_add_f2_global(float2* p, float2 v) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
+    atomicAdd(p, v);
+#else
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+#endif
+}
+
+__device__ __forceinline__ bool row_has_taps(const int* bucket_start, int r, int ny, int w) {
+    const int h = w / 2;
+    for (int t = 0; t < w; ++t) {
+        const int b = wrapmod(r + h - 1 - t, ny);
+        if (bucket_start[b + 1] > bucket_start[b]) return true;
+    }
+    return false;
+}
+
+template <int LOGN>
+struct LineSmem {
+    float2* buf;
+    float2* twh;
+    float2* twl;
+    __device__ __forceinline__ explicit LineSmem(float2* base) {
+        buf = base;
+        twh = base + Line<LOGN>::PADLEN;
+        twl = twh + 128;
+    }
+};
+
+// Pass-1 epilogue: keep the M_x = N/2 wanted x modes, deapodise, store row r of T.
+template <int LOGN>
+struct RowOut {
+    int r;
+    const float* deap_x;
+    float2* T;
+    __device__ __forceinline__ void operator()(int o, float2 v) const {
+        constexpr int N = 1 << LOGN, MX = N / 2, HALF = MX / 2;
+        int jx;
+        if (o < HALF) jx = o + HALF;
+        else if (o >= N - HALF) jx = o - (N - HALF);
+        else return;
+        T[(size_t)r * MX + jx] = cscale(v, __ldg(&deap_x[jx]));
+    }
+};
+
+// Pass 1 of the adjoint, pulse rows: fine row r = sum over the pulse rows p
+// whose azimuth taps reach r of phi_y(r - v_p) R_p (shifted to its x cells).
+template <int LOGN>
+__global__ void __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_adj_rows(RowsView rv, const float2* __restrict__ R, int ny, int w, TapPoly tp, FftTables tab,
+           const float* __restrict__ deap_x, float2* __restrict__ T) {
+    using L = Line<LOGN>;
+    constexpr int NX = L::N, MX = NX / 2;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    const int r = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (!row_has_taps(rv.bucket_start, r, ny, w)) {
+        for (int jx = tid; jx < MX; jx += L::T) T[(size_t)r * MX + jx] = make_float2(0.f, 0.f);
+        return;
+    }
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
+    for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int h = w / 2;
+    for (int t = 0; t < w; ++t) {
+        const int b = wrapmod(r + h - 1 - t, ny);
+        for (int q = rv.bucket_start[b]; q < rv.bucket_start[b + 1]; ++q) {
+            const int p = rv.bucket_rows[q];
+            const float wy = tap_eval(tp, t, 2.0f * rv.row_fy[p] - 1.0f);
+            const int clo = rv.row_clo[p], len = rv.row_len[p];
+            const float2* Rp = R + rv.row_off[p];
+            for (int i = tid; i < len; i += L::T) {
+                const int c = wrapmod(clo + i, NX);
+                atomic_add_f2_shared(&S.buf[L::pad(c)], cscale(Rp[i], wy));
+            }
+        }
+    }
+    __syncthreads();
+    RowOut<LOGN> epi{r, deap_x, T};
+    fft_line_epilogue<LOGN>(S.buf, tw, +1.0f, epi);
+}
+
+// Pass 1 of the adjoint, general points: the samples of the w buckets whose
+// taps reach fine row r (values already weighted, sorted by bucket) are
+// spread straight into the shared row.
+template <int LOGN>
+__global__ void __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_adj_rows_general(GeneralView gv, const float2* __restrict__ sval, int ny, int w, TapPoly tp, FftTables tab,
+                   const float* __restrict__ deap_x, float2* __restrict__ T) {
+    using L = Line<LOGN>;
+    constexpr int NX = L::N, MX = NX / 2;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    const int r = blockIdx.x;
+    const int tid = threadIdx.x;
+    if (!row_has_taps(gv.bucket_start, r, ny, w)) {
+        for (int jx = tid; jx < MX; jx += L::T) T[(size_t)r * MX + jx] = make_float2(0.f, 0.f);
+        return;
+    }
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
+    for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int h = w / 2;
+    for (int t = 0; t < w; ++t) {
+        const int b = wrapmod(r + h - 1 - t, ny);
+        for (int q = gv.bucket_start[b] + tid; q < gv.bucket_start[b + 1]; q += L::T) {
+            const float2 v0 = sval[q];
+            if (v0.x == 0.0f && v0.y == 0.0f) continue;
+            const float2 v = cscale(v0, tap_eval(tp, t, 2.0f * gv.sfy[q] - 1.0f));
+            const int c0 = gv.slx[q] - (h - 1);
+            const float tx = 2.0f * gv.sfx[q] - 1.0f;
+            for (int s = 0; s < w; ++s)
+                atomic_add_f2_shared(&S.buf[L::pad(wrapmod(c0 + s, NX))], cscale(v, tap_eval(tp, s, tx)));
+        }
+    }
+    __syncthreads();
+    RowOut<LOGN> epi{r, deap_x, T};
+    fft_line_epilogue<LOGN>(S.buf, tw, +1.0f, epi);
+}
+
+// Pass-2 epilogue: keep the M_y = N/2 wanted y modes, deapodise, park them in
+// the CTA's own line buffer for the cluster gather.
+template <int LOGN>
+struct ColPark {
+    const float* deap_y;
+    float2* buf;
+    __device__ __forceinline__ void operator()(int o, float2 v) const {
+        constexpr int N = 1 << LOGN, HALF = N / 4;
+        int jy;
+        if (o < HALF) jy = o + HALF;
+        else if (o >= N - HALF) jy = o - (N - HALF);
+        else return;
+        buf[Line<LOGN>::pad(jy)] = cscale(v, __ldg(&deap_y[jy]));
+    }
+};
+
+template <int LOGN>
+__global__ void __cluster_dims__(kColCluster, 1, 1) __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_adj_cols(const float2* __restrict__ T, int Mx, FftTables tab, const float* __restrict__ deap_y,
+           float2* __restrict__ img) {
+    using L = Line<LOGN>;
+    constexpr int NY = L::N, MY = NY / 2, V = L::V;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int jx0 = (int)blockIdx.x - rank;           // first of the cluster's 4 columns
+    const int tid = threadIdx.x;
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
+    float2* peer[kColCluster];
+#pragma unroll
+    for (int k = 0; k < kColCluster; ++k) peer[k] = cluster.map_shared_rank(S.buf, k);
+    // scatter: this CTA reads rows [rank NY/4, (rank+1) NY/4) of the 4 columns,
+    // exactly V elements per thread, all loads issued before the remote stores
+    constexpr int ROWS = NY / kColCluster;
+    {
+        float2 tmp[V];
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int i = tid + u * L::T;
+            tmp[u] = __ldg(&T[(size_t)(rank * ROWS + i / kColCluster) * Mx + jx0 + i % kColCluster]);
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int i = tid + u * L::T;
+            peer[i % kColCluster][L::pad(rank * ROWS + i / kColCluster)] = tmp[u];
+        }
+    }
+    cluster.sync();
+    ColPark<LOGN> epi{deap_y, S.buf};
+    fft_line_epilogue<LOGN>(S.buf, tw, +1.0f, epi);
+    cluster.sync();
+    // gather: this CTA stores image rows [rank MY/4, (rank+1) MY/4) of the 4 columns
+    constexpr int OROWS = MY / kColCluster;
+    {
+        float2 tmp[V / 2];
+#pragma unroll
+        for (int u = 0; u < V / 2; ++u) {
+            const int i = tid + u * L::T;
+            tmp[u] = peer[i % kColCluster][L::pad(rank * OROWS + i / kColCluster)];
+        }
+#pragma unroll
+        for (int u = 0; u < V / 2; ++u) {
+            const int i = tid + u * L::T;
+            img[(size_t)(rank * OROWS + i / kColCluster) * Mx + jx0 + i % kColCluster] = tmp[u];
+        }
+    }
+    cluster.sync();                                    // peers may still read this CTA's buffer
+}
+
+template <int LOGN>
+__global__ void __cluster_dims__(kColCluster, 1, 1) __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_fwd_cols(const float2* __restrict__ img, int Mx, FftTables tab, const float* __restrict__ deap_y,
+           const float* __restrict__ deap_x, float2* __restrict__ T) {
+    using L = Line<LOGN>;
+    constexpr int NY = L::N, MY = NY / 2, V = L::V;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int jx0 = (int)blockIdx.x - rank;
+    const int tid = threadIdx.x;
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
+    for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
+    float2* peer[kColCluster];
+#pragma unroll
+    for (int k = 0; k < kColCluster; ++k) peer[k] = cluster.map_shared_rank(S.buf, k);
+    cluster.sync();                                    // every buffer zeroed before the scatter
+    constexpr int IROWS = MY / kColCluster;
+    {
+        float2 tmp[V / 2];
+#pragma unroll
+        for (int u = 0; u < V / 2; ++u) {
+            const int i = tid + u * L::T;
+            tmp[u] = __ldg(&img[(size_t)(rank * IROWS + i / kColCluster) * Mx + jx0 + i % kColCluster]);
+        }
+#pragma unroll
+        for (int u = 0; u < V / 2; ++u) {
+            const int i = tid + u * L::T;
+            const int jy = rank * IROWS + i / kColCluster;
+            const int k = i % kColCluster;
+            const float d = __ldg(&deap_y[jy]) * __ldg(&deap_x[jx0 + k]);
+            peer[k][L::pad(wrapmod(jy - MY / 2, NY))] = cscale(tmp[u], d);
+        }
+    }
+    cluster.sync();
+    fft_line_smem<LOGN>(S.buf, tw, -1.0f);
+    cluster.sync();
+    constexpr int ROWS = NY / kColCluster;
+    {
+        float2 tmp[V];
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int i = tid + u * L::T;
+            tmp[u] = peer[i % kColCluster][L::pad(rank * ROWS + i / kColCluster)];
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int i = tid + u * L::T;
+            T[(size_t)(rank * ROWS + i / kColCluster) * Mx + jx0 + i % kColCluster] = tmp[u];
+        }
+    }
+    cluster.sync();
+}
+
+template <int LOGN, bool ROWS>
+__global__ void __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int ny, int w, TapPoly tp, FftTables tab,
+           float2* __restrict__ R, float2* __restrict__ acc) {
+    using L = Line<LOGN>;
+    constexpr int NX = L::N, MX = NX / 2;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    const int r = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int* bstart = ROWS ? rv.bucket_start : gv.bucket_start;
+    if (!row_has_taps(bstart, r, ny, w)) return;
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
+    for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int jx = tid; jx < MX; jx += L::T) S.buf[L::pad(wrapmod(jx - MX / 2, NX))] = T[(size_t)r * MX + jx];
+    __syncthreads();
+    fft_line_smem<LOGN>(S.buf, tw, -1.0f);
+    const int h = w / 2;
+    for (int t = 0; t < w; ++t) {
+        const int b = wrapmod(r + h - 1 - t, ny);
+        const int q0 = bstart[b], q1 = bstart[b + 1];
+        if (ROWS) {
+            for (int q = q0; q < q1; ++q) {
+                const int p = rv.bucket_rows[q];
+                const float wy = tap_eval(tp, t, 2.0f * rv.row_fy[p] - 1.0f);
+                const int clo = rv.row_clo[p], len = rv.row_len[p];
+                float2* Rp = R + rv.row_off[p];
+                for (int i = tid; i < len; i += L::T) {
+                    const int c = wrapmod(clo + i, NX);
+                    atomic_add_f2_global(&Rp[i], cscale(S.buf[L::pad(c)], wy));
+                }
+            }
+        } else {
+            for (int q = q0 + tid; q < q1; q += L::T) {
+                const float wy = tap_eval(tp, t, 2.0f * gv.sfy[q] - 1.0f);
+                const int c0 = gv.slx[q] - (h - 1);
+                const float tx = 2.0f * gv.sfx[q] - 1.0f;
+                float2 a = make_float2(0.f, 0.f);
+                for (int s = 0; s < w; ++s) {
+                    const float wt = tap_eval(tp, s, tx);
+                    const float2 g = S.buf[L::pad(wrapmod(c0 + s, NX))];
+                    a.x = fmaf(wt, g.x, a.x);
+                    a.y = fmaf(wt, g.y, a.y);
+                }
+                atomic_add_f2_global(&acc[q], cscale(a, wy));
+            }
+        }
+    }
+}
+
+}  // namespace tffr

@@ -1,0 +1,28 @@
+// Host launchers of the FFT line kernels (compiled in line_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "types.cuh"
+
+namespace tffr {
+
+// Shared-memory limits of every line-kernel instantiation (once per device).
+cudaError_t line_set_attributes();
+
+// Pass 1 of the adjoint over the ny fine rows (line length 2^lognx).
+void launch_adj_rows(int lognx, int ny, cudaStream_t s, const RowsView& rv, const float2* R, int w,
+                     const TapPoly& tp, FftTables tab, const float* deap_x, float2* T);
+void launch_adj_rows_general(int lognx, int ny, cudaStream_t s, const GeneralView& gv, const float2* sval, int w,
+                             const TapPoly& tp, FftTables tab, const float* deap_x, float2* T);
+// Pass 2 of the adjoint over the Mx wanted x modes (line length 2^logny).
+void launch_adj_cols(int logny, int Mx, cudaStream_t s, const float2* T, FftTables tab, const float* deap_y,
+                     float2* img);
+// Forward twin: columns first, then rows.
+void launch_fwd_cols(int logny, int Mx, cudaStream_t s, const float2* img, FftTables tab, const float* deap_y,
+                     const float* deap_x, float2* T);
+void launch_fwd_rows(int lognx, int ny, bool rows, cudaStream_t s, const RowsView& rv, const GeneralView& gv,
+                     const float2* T, int w, const TapPoly& tp, FftTables tab, float2* R, float2* acc);
+
+}  // namespace tffr

@@ -15,8 +15,7 @@
 
 #include "../../include/tffr.h"
 #include "common.cuh"
-#include "fft_reg.cuh"
-#include "kernels_fft.cuh"
+#include "line_launch.h"
 #include "kernels_points.cuh"
 #include "kernels_spread.cuh"
 
@@ -288,14 +287,13 @@ void fit_weights(WeightArgs& A) {
     auto G = [&](double v) { return diag_psi_w(0.5 + v, 0, A.a, A.q, A.e_minus, A.e_plus, A.reach); };
     A.n0 = A.n1 = 1;
     A.c0[0] = A.c1[0] = 0.0f;
+    A.inv_vb = vb > 0.0 ? (float)(1.0 / vb) : 0.0f;
     if (vb > 0.0) {
+        // G is even in v about delta = 1/2, hence smooth in s = 2 (v/vb)^2 - 1
         auto f0 = [&](double s) { return G(vb * std::sqrt(std::max(0.0, 0.5 * (s + 1.0)))); };
-        for (int n = 8; n <= kGCoefs; ++n) {
-            std::vector<double> a = cheb_fit_power(f0, n);
-            A.n0 = n;
-            for (int k = 0; k < n; ++k) A.c0[k] = (float)a[k];
-            if (power_fit_error(a, f0) < 1e-10) break;
-        }
+        std::vector<double> a = cheb_fit_power(f0, kG0Coefs);
+        A.n0 = kG0Coefs;
+        for (int k = 0; k < kG0Coefs; ++k) A.c0[k] = (float)a[k];
     }
     if (vb < 0.5) {
         auto f1 = [&](double s) { return G(vb + (0.5 - vb) * 0.5 * (s + 1.0)); };
@@ -306,6 +304,16 @@ void fit_weights(WeightArgs& A) {
             if (power_fit_error(a, f1) < 1e-10) break;
         }
     }
+}
+
+// The fitted part of the weight evaluation (everything fit_weights sets).
+void copy_fit(WeightArgs& dst, const WeightArgs& src) {
+    dst.vb = src.vb;
+    dst.inv_vb = src.inv_vb;
+    dst.n0 = src.n0;
+    dst.n1 = src.n1;
+    std::memcpy(dst.c0, src.c0, sizeof(dst.c0));
+    std::memcpy(dst.c1, src.c1, sizeof(dst.c1));
 }
 
 int upload_tables(tffr_plan_s* p) {
@@ -364,28 +372,12 @@ cudaError_t spread_attrs() {
     return e;
 }
 
-template <int V>
-cudaError_t line_attrs() {
-    const size_t b = line_smem_bytes<V>(kFftNMax);
-    cudaError_t e = smem_attr(k_adj_rows<V>, b);
-    if (e == cudaSuccess) e = smem_attr(k_adj_rows_general<V>, b);
-    if (e == cudaSuccess) e = smem_attr(k_adj_cols<V>, b);
-    if (e == cudaSuccess) e = smem_attr(k_fwd_cols<V>, b);
-    if (e == cudaSuccess) e = smem_attr(k_fwd_rows<V, true>, b);
-    if (e == cudaSuccess) e = smem_attr(k_fwd_rows<V, false>, b);
-    return e;
-}
-
 int set_kernel_attributes(tffr_plan_s* p) {
     int dev = 0;
     CK(cudaGetDevice(&dev));
     static bool done[64] = {false};
     if (dev < 64 && done[dev]) return TFFR_OK;
-    CK(line_attrs<2>());
-    CK(line_attrs<4>());
-    CK(line_attrs<8>());
-    CK(line_attrs<16>());
-    CK(line_attrs<32>());
+    CK(line_set_attributes());
     CK(spread_attrs<float2>());
     CK(spread_attrs<double2>());
     CK(spread_attrs<__half2>());
@@ -543,16 +535,6 @@ int build_general(tffr_plan_s* p) {
 FftTables tables_x(const tffr_plan_s* p) { return FftTables{p->twh_x.ptr, p->twl_x.ptr}; }
 FftTables tables_y(const tffr_plan_s* p) { return FftTables{p->twh_y.ptr, p->twl_y.ptr}; }
 
-// Launch one line kernel family member for the values-per-thread of an n-point line.
-#define LINE_DISPATCH(n, LAUNCH)                \
-    switch (line_v(n)) {                        \
-        case 32: LAUNCH(32); break;             \
-        case 16: LAUNCH(16); break;             \
-        case 8: LAUNCH(8); break;               \
-        case 4: LAUNCH(4); break;               \
-        default: LAUNCH(2); break;              \
-    }
-
 template <typename VT, int W>
 void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values) {
     const size_t smem = (size_t)kSpreadStageBytes + (size_t)p->max_len * sizeof(float2);
@@ -562,7 +544,7 @@ void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values) {
 
 template <typename VT>
 int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
-    const int nx = p->nx, ny = p->ny;
+    const int ny = p->ny;
     if (p->layout == TFFR_POINTS_ROWS) {
         const RowsView rv = rows_view(p);
         STAGE_BEGIN(TFFR_STAGE_SPREAD);
@@ -575,12 +557,7 @@ int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
         CK_LAUNCH("k_spread_rows");
         STAGE_END(TFFR_STAGE_SPREAD);
         STAGE_BEGIN(TFFR_STAGE_ROW_FFT);
-#define ADJ_ROWS(V)                                                                                          \
-    k_adj_rows<V><<<ny, nx / V, line_smem_bytes<V>(nx), p->stream>>>(rv, p->R.ptr, nx, p->lognx, ny, p->Mx, \
-                                                                     p->w, p->taps, tables_x(p),            \
-                                                                     p->deap_x.ptr, p->T.ptr)
-        LINE_DISPATCH(nx, ADJ_ROWS)
-#undef ADJ_ROWS
+        launch_adj_rows(p->lognx, ny, p->stream, rv, p->R.ptr, p->w, p->taps, tables_x(p), p->deap_x.ptr, p->T.ptr);
         CK_LAUNCH("k_adj_rows");
         STAGE_END(TFFR_STAGE_ROW_FFT);
     } else {
@@ -589,23 +566,13 @@ int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
                                                                          p->acc.ptr);
         CK_LAUNCH("k_gather_values");
         const GeneralView gv = general_view(p);
-#define ADJ_ROWS_G(V)                                                                                        \
-    k_adj_rows_general<V><<<ny, nx / V, line_smem_bytes<V>(nx), p->stream>>>(gv, p->acc.ptr, nx, p->lognx, \
-                                                                             ny, p->Mx, p->w, p->taps,     \
-                                                                             tables_x(p), p->deap_x.ptr,   \
-                                                                             p->T.ptr)
-        LINE_DISPATCH(nx, ADJ_ROWS_G)
-#undef ADJ_ROWS_G
+        launch_adj_rows_general(p->lognx, ny, p->stream, gv, p->acc.ptr, p->w, p->taps, tables_x(p), p->deap_x.ptr,
+                                p->T.ptr);
         CK_LAUNCH("k_adj_rows_general");
         STAGE_END(TFFR_STAGE_ROW_FFT);
     }
     STAGE_BEGIN(TFFR_STAGE_COL_FFT);
-#define ADJ_COLS(V)                                                                                          \
-    k_adj_cols<V><<<p->Mx, ny / V, line_smem_bytes<V>(ny), p->stream>>>(p->T.ptr, ny, p->logny, p->My,    \
-                                                                        p->Mx, tables_y(p), p->deap_y.ptr, \
-                                                                        image)
-    LINE_DISPATCH(ny, ADJ_COLS)
-#undef ADJ_COLS
+    launch_adj_cols(p->logny, p->Mx, p->stream, p->T.ptr, tables_y(p), p->deap_y.ptr, image);
     CK_LAUNCH("k_adj_cols");
     STAGE_END(TFFR_STAGE_COL_FFT);
     return TFFR_OK;
@@ -619,14 +586,9 @@ void launch_interp(tffr_plan_s* p, const RowsView& rv, void* values, int apply_w
 
 template <typename VT>
 int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_weights) {
-    const int nx = p->nx, ny = p->ny;
+    const int ny = p->ny;
     STAGE_BEGIN(TFFR_STAGE_FWD_COL_FFT);
-#define FWD_COLS(V)                                                                                          \
-    k_fwd_cols<V><<<p->Mx, ny / V, line_smem_bytes<V>(ny), p->stream>>>(image, ny, p->logny, p->My, p->Mx, \
-                                                                        tables_y(p), p->deap_y.ptr,        \
-                                                                        p->deap_x.ptr, p->T.ptr)
-    LINE_DISPATCH(ny, FWD_COLS)
-#undef FWD_COLS
+    launch_fwd_cols(p->logny, p->Mx, p->stream, image, tables_y(p), p->deap_y.ptr, p->deap_x.ptr, p->T.ptr);
     CK_LAUNCH("k_fwd_cols");
     STAGE_END(TFFR_STAGE_FWD_COL_FFT);
     STAGE_BEGIN(TFFR_STAGE_FWD_ROW_FFT);
@@ -634,12 +596,8 @@ int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_we
     const GeneralView gv = general_view(p);
     if (p->layout == TFFR_POINTS_ROWS) {
         CK(cudaMemsetAsync(p->R.ptr, 0, (size_t)p->R_cells * sizeof(float2), p->stream));
-#define FWD_ROWS_R(V)                                                                                        \
-    k_fwd_rows<V, true><<<ny, nx / V, line_smem_bytes<V>(nx), p->stream>>>(rv, gv, p->T.ptr, nx, p->lognx, \
-                                                                           ny, p->Mx, p->w, p->taps,       \
-                                                                           tables_x(p), p->R.ptr, p->acc.ptr)
-        LINE_DISPATCH(nx, FWD_ROWS_R)
-#undef FWD_ROWS_R
+        launch_fwd_rows(p->lognx, ny, true, p->stream, rv, gv, p->T.ptr, p->w, p->taps, tables_x(p), p->R.ptr,
+                        p->acc.ptr);
         CK_LAUNCH("k_fwd_rows");
         STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
         STAGE_BEGIN(TFFR_STAGE_INTERP);
@@ -653,12 +611,8 @@ int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_we
         STAGE_END(TFFR_STAGE_INTERP);
     } else {
         CK(cudaMemsetAsync(p->acc.ptr, 0, (size_t)p->N * sizeof(float2), p->stream));
-#define FWD_ROWS_G(V)                                                                                         \
-    k_fwd_rows<V, false><<<ny, nx / V, line_smem_bytes<V>(nx), p->stream>>>(rv, gv, p->T.ptr, nx, p->lognx, \
-                                                                            ny, p->Mx, p->w, p->taps,       \
-                                                                            tables_x(p), p->R.ptr, p->acc.ptr)
-        LINE_DISPATCH(nx, FWD_ROWS_G)
-#undef FWD_ROWS_G
+        launch_fwd_rows(p->lognx, ny, false, p->stream, rv, gv, p->T.ptr, p->w, p->taps, tables_x(p), p->R.ptr,
+                        p->acc.ptr);
         CK_LAUNCH("k_fwd_rows");
         STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
         STAGE_BEGIN(TFFR_STAGE_INTERP);
@@ -876,17 +830,12 @@ int tffr_weights(tffr_plan_t p, const tffr_weight_opts* opts, float* D_out, int6
     A.e_minus = std::exp(-o.a / 2.0);
     A.e_plus = std::exp(o.a / 2.0);
     A.reach = (int)std::ceil(o.q) + 1;
-    if (p->fit_valid && p->fit_cache.a == A.a && p->fit_cache.q == A.q) {
-        A.vb = p->fit_cache.vb;
-        A.n0 = p->fit_cache.n0;
-        A.n1 = p->fit_cache.n1;
-        std::memcpy(A.c0, p->fit_cache.c0, sizeof(A.c0));
-        std::memcpy(A.c1, p->fit_cache.c1, sizeof(A.c1));
-    } else {
-        fit_weights(A);
+    if (!(p->fit_valid && p->fit_cache.a == A.a && p->fit_cache.q == A.q)) {
         p->fit_cache = A;
+        fit_weights(p->fit_cache);
         p->fit_valid = true;
     }
+    copy_fit(A, p->fit_cache);
     STAGE_BEGIN(TFFR_STAGE_WEIGHTS);
     if (N > 0 && o.mode == TFFR_WEIGHTS_USER) {
         CK(grow(p, p->D, N));

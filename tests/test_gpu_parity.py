@@ -298,3 +298,23 @@ def test_weights_dense_offsets_and_threshold_decisions(q, a):
     assert kept == np.count_nonzero(Dref)
     assert np.array_equal(D != 0, Dref != 0)
     assert d_err(D, Dref) < 3e-7
+
+
+def test_repeated_set_points_and_weights_calls():
+    """A plan reused across calls (new points, new weights, the same or other (a, q)) keeps
+    the oracle's answer; the plan-time fit of the weights is cached per (a, q)."""
+    from paper_1910_10908_gb300 import Plan
+    lx, ly, _, v = stolt_scene(64, 96, 64)
+    lx2, ly2, _, v2 = stolt_scene(48, 80, 64, seed=12)
+    vals, vals2 = dev(v.astype(np.complex64)), dev(v2.astype(np.complex64))
+    with Plan(64) as plan:
+        for rnd in range(3):
+            for (x, y, val, vv) in ((lx, ly, vals, v), (lx2, ly2, vals2, v2)):
+                tx, ty = dev(x), dev(y)
+                plan.set_points(tx, ty)
+                for kw in (dict(), dict(a=0.5, q=2.5), dict()):
+                    plan.weights(count=False, **kw)
+                    img = plan.adjoint(val).cpu().numpy().astype(np.complex128)
+                    Dref = oracle.tffr_weights(x, 64, **kw)
+                    ref = oracle.adjoint_image(x, y, vv.astype(np.complex64), Dref, 64, 64)
+                    assert rel_l2(img, ref) <= TOL, (rnd, kw)
