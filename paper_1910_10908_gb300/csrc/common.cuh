@@ -20,7 +20,12 @@ __device__ __forceinline__ int wrapmod(int c, int n) {  // n is a power of two
 // on this GPU).  The fraction is rounded to FP32 (it may round up to 1.0f,
 // which places the sample on the next cell edge: the taps stay consistent).
 // Returns false for |v| >= 2^28, infinities and NaN.
-static __device__ __noinline__ bool fine_coord_general(double v, int& cell, float& frac);
+struct FineCoord {
+    int cell;
+    float frac;
+    bool ok;
+};
+static __device__ __noinline__ FineCoord fine_coord_general(double v);
 
 __device__ __forceinline__ bool fine_coord(double v, int& cell, float& frac) {
     // Fast path for 1 <= |2v| < 2^21 with 32-bit integer operations: the
@@ -47,17 +52,22 @@ __device__ __forceinline__ bool fine_coord(double v, int& cell, float& frac) {
         }
         return true;
     }
-    return fine_coord_general(v, cell, frac);
+    const FineCoord g = fine_coord_general(v);
+    cell = g.cell;
+    frac = g.frac;
+    return g.ok;
 }
 
 // Any magnitude (see fine_coord): 64-bit integer operations.
-static __device__ __noinline__ bool fine_coord_general(double v, int& cell, float& frac) {
+static __device__ __noinline__ FineCoord fine_coord_general(double v) {
+    int cell;
+    float frac;
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     const int e = (int)((b >> 52) & 0x7ffu);
     cell = 0;
     frac = 0.0f;
-    if (e > 1050) return false;                 // |v| >= 2^28 (also inf, NaN)
-    if (e == 0) return true;                    // zero or subnormal
+    if (e > 1050) return FineCoord{0, 0.0f, false};   // |v| >= 2^28 (also inf, NaN)
+    if (e == 0) return FineCoord{0, 0.0f, true};      // zero or subnormal
     const bool neg = (b >> 63) != 0ull;
     const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
     const int sh = 1074 - e;                    // |2v| = m * 2^-sh, sh >= 24
@@ -73,7 +83,7 @@ static __device__ __noinline__ bool fine_coord_general(double v, int& cell, floa
         cell = -(int)I - 1;
         frac = (sh >= 64) ? 1.0f - __ull2float_rn(F) * scale : __ull2float_rn((1ull << sh) - F) * scale;
     }
-    return true;
+    return FineCoord{cell, frac, true};
 }
 
 // Spreading-kernel taps as polynomials in t = 2f - 1 (f the fine-cell offset

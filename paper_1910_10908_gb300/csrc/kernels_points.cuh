@@ -3,6 +3,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "types.cuh"
 
 namespace tffr {
 
@@ -111,12 +112,18 @@ __device__ __forceinline__ float g_fitted(int cell, float f, int M, const Weight
     return horner(A.c1, A.n1, (2.0f * v - A.vb - 0.5f) / (0.5f - A.vb));
 }
 
-__device__ __noinline__ float weight_exact(double lam_x, double lam_y, int Mx, int My, const WeightArgs& A) {
-    double G = diag_psi_w(lam_x, Mx, A.a, A.q, A.e_minus, A.e_plus, A.reach);
-    if (A.separable) G *= diag_psi_w(lam_y, My, A.a, A.q, A.e_minus, A.e_plus, A.reach);
+__device__ __noinline__ float weight_exact_args(double lam_x, double lam_y, int Mx, int My, double a, double q,
+                                                double e_minus, double e_plus, int reach, double tau, int separable) {
+    double G = diag_psi_w(lam_x, Mx, a, q, e_minus, e_plus, reach);
+    if (separable) G *= diag_psi_w(lam_y, My, a, q, e_minus, e_plus, reach);
     double d = (G != 0.0) ? 1.0 / G : 0.0;
-    if (!(d >= A.tau_d)) d = 0.0;
+    if (!(d >= tau)) d = 0.0;
     return (float)d;
+}
+
+// D_n by the closed form in FP64 (the FP64 decision path).
+__device__ __forceinline__ float weight_exact(double lam_x, double lam_y, int Mx, int My, const WeightArgs& A) {
+    return weight_exact_args(lam_x, lam_y, Mx, My, A.a, A.q, A.e_minus, A.e_plus, A.reach, A.tau_d, A.separable);
 }
 
 // D_n in tFFR mode from the x cell/offset (and the y ones in separable mode).
@@ -282,6 +289,71 @@ __global__ void k_row_info(int P, int64_t N, int nx, int w, const int* __restric
             row_lam_y[p] = ly;
         }
         __syncthreads();
+    }
+}
+
+// Row buffer offsets (exclusive scan of row_len, single block, any P), the
+// total cells and the longest row: out[0] = total (int64), out32[0] = max len.
+__global__ void k_row_offsets(int P, const int* __restrict__ row_len, int64_t* __restrict__ row_off,
+                              long long* __restrict__ total, int* __restrict__ max_len) {
+    __shared__ int s_warp[32];
+    long long carry = 0;
+    int mx = 0;
+    for (int base = 0; base < P; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int x = (i < P) ? row_len[i] : 0;
+        mx = max(mx, x);
+        int tot;
+        const int ex = block_exclusive_scan(x, s_warp, &tot);
+        if (i < P) row_off[i] = carry + ex;
+        carry += tot;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(max_len, mx);
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// Azimuth taps of every pulse row, grouped by the fine row they reach: pulse
+// row p adds phi(t - (w/2 - 1) - fy_p) R_p to fine row ly_p - (w/2 - 1) + t.
+__global__ void k_tap_count(int P, int ny, int w, const int* __restrict__ row_ly, int* __restrict__ count) {
+    const int h = w / 2;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+        for (int t = 0; t < w; ++t) atomicAdd(&count[wrapmod(row_ly[p] - (h - 1) + t, ny)], 1);
+}
+
+// Exclusive scan of n counts into start[0..n] (single block).
+__global__ void k_scan_counts(int n, const int* __restrict__ count, int* __restrict__ start) {
+    __shared__ int s_warp[32];
+    int carry = 0;
+    for (int base = 0; base < n; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const int x = (i < n) ? count[i] : 0;
+        int tot;
+        const int ex = block_exclusive_scan(x, s_warp, &tot);
+        if (i < n) start[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) start[n] = carry;
+}
+
+__global__ void k_tap_fill(int P, int ny, int w, TapPoly tp, const int* __restrict__ row_ly,
+                           const float* __restrict__ row_fy, const int* __restrict__ row_clo,
+                           const int* __restrict__ row_len, const int64_t* __restrict__ row_off,
+                           const int* __restrict__ start, int* __restrict__ cursor, TapEntry* __restrict__ taps) {
+    const int h = w / 2;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const float s = 2.0f * row_fy[p] - 1.0f;
+        for (int t = 0; t < w; ++t) {
+            const int r = wrapmod(row_ly[p] - (h - 1) + t, ny);
+            TapEntry e;
+            e.off = row_off[p];
+            e.clo = row_clo[p];
+            e.len = row_len[p];
+            e.wy = tap_eval(tp, t, s);
+            e.p = p;
+            taps[start[r] + atomicAdd(&cursor[r], 1)] = e;
+        }
     }
 }
 

@@ -72,11 +72,6 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
 #pragma unroll
         for (int s = 0; s < W; ++s) acc[s] = make_float2(0.f, 0.f);
         int wbase = INT_MIN;                               // first fine cell held in acc
-        auto flush = [&](int s) {
-            const int c = wbase + s;
-            const int idx = periodic ? wrapmod(c, nx) : (c - clo);
-            atomic_add_f2_shared(&s_row[idx], acc[s]);
-        };
         for (int i = i0; i < i1; ++i) {
             const int k = i + (i >> 6);
             const double lam = s_lam[k];
@@ -105,17 +100,21 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
             if (c0 != wbase) {
                 if (wbase != INT_MIN && c0 > wbase && c0 - wbase < W) {
                     // slide the footprint right, flushing the cells it leaves
-                    while (wbase < c0) {
-                        flush(0);
+                    do {
+                        const int idx = periodic ? wrapmod(wbase, nx) : (wbase - clo);
+                        atomic_add_f2_shared(&s_row[idx], acc[0]);
 #pragma unroll
                         for (int s = 0; s < W - 1; ++s) acc[s] = acc[s + 1];
                         acc[W - 1] = make_float2(0.f, 0.f);
                         ++wbase;
-                    }
+                    } while (wbase < c0);
                 } else {
                     if (wbase != INT_MIN) {
 #pragma unroll
-                        for (int s = 0; s < W; ++s) flush(s);
+                        for (int s = 0; s < W; ++s) {
+                            const int idx = periodic ? wrapmod(wbase + s, nx) : (wbase + s - clo);
+                            atomic_add_f2_shared(&s_row[idx], acc[s]);
+                        }
                     }
 #pragma unroll
                     for (int s = 0; s < W; ++s) acc[s] = make_float2(0.f, 0.f);
@@ -130,7 +129,10 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
         }
         if (wbase != INT_MIN) {
 #pragma unroll
-            for (int s = 0; s < W; ++s) flush(s);
+            for (int s = 0; s < W; ++s) {
+                const int idx = periodic ? wrapmod(wbase + s, nx) : (wbase + s - clo);
+                atomic_add_f2_shared(&s_row[idx], acc[s]);
+            }
         }
     }
     __syncthreads();

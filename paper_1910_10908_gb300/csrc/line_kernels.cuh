@@ -31,6 +31,7 @@ namespace tffr {
 namespace cg = cooperative_groups;
 
 constexpr int kColCluster = 4;
+constexpr int kTapChunk = 64;                          // tap entries staged per round
 
 __device__ __forceinline__ void atomic_add_f2_global(float2* p, float2 v) {
 #if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
@@ -90,25 +91,24 @@ k_adj_rows(RowsView rv, const float2* __restrict__ R, int ny, int w, TapPoly tp,
     LineSmem<LOGN> S(smem);
     const int r = blockIdx.x;
     const int tid = threadIdx.x;
-    if (!row_has_taps(rv.bucket_start, r, ny, w)) {
+    const int e0 = rv.tap_start[r], e1 = rv.tap_start[r + 1];
+    if (e0 == e1) {
         for (int jx = tid; jx < MX; jx += L::T) T[(size_t)r * MX + jx] = make_float2(0.f, 0.f);
         return;
     }
     const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
     for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
-    __syncthreads();
-    const int h = w / 2;
-    for (int t = 0; t < w; ++t) {
-        const int b = wrapmod(r + h - 1 - t, ny);
-        for (int q = rv.bucket_start[b]; q < rv.bucket_start[b + 1]; ++q) {
-            const int p = rv.bucket_rows[q];
-            const float wy = tap_eval(tp, t, 2.0f * rv.row_fy[p] - 1.0f);
-            const int clo = rv.row_clo[p], len = rv.row_len[p];
-            const float2* Rp = R + rv.row_off[p];
-            for (int i = tid; i < len; i += L::T) {
-                const int c = wrapmod(clo + i, NX);
-                atomic_add_f2_shared(&S.buf[L::pad(c)], cscale(Rp[i], wy));
-            }
+    __shared__ TapEntry s_tap[kTapChunk];
+    for (int base = e0; base < e1; base += kTapChunk) {
+        const int cnt = min(kTapChunk, e1 - base);
+        __syncthreads();                               // zeroing done / previous chunk consumed
+        if (tid < cnt) s_tap[tid] = rv.taps[base + tid];
+        __syncthreads();
+        for (int e = 0; e < cnt; ++e) {
+            const TapEntry te = s_tap[e];
+            const float2* Rp = R + te.off;
+            for (int i = tid; i < te.len; i += L::T)
+                atomic_add_f2_shared(&S.buf[L::pad(wrapmod(te.clo + i, NX))], cscale(__ldg(&Rp[i]), te.wy));
         }
     }
     __syncthreads();
@@ -289,30 +289,39 @@ k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int ny, in
     LineSmem<LOGN> S(smem);
     const int r = blockIdx.x;
     const int tid = threadIdx.x;
-    const int* bstart = ROWS ? rv.bucket_start : gv.bucket_start;
-    if (!row_has_taps(bstart, r, ny, w)) return;
+    if (ROWS) {
+        if (rv.tap_start[r] == rv.tap_start[r + 1]) return;
+    } else if (!row_has_taps(gv.bucket_start, r, ny, w)) {
+        return;
+    }
     const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
     for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int jx = tid; jx < MX; jx += L::T) S.buf[L::pad(wrapmod(jx - MX / 2, NX))] = T[(size_t)r * MX + jx];
     __syncthreads();
     fft_line_smem<LOGN>(S.buf, tw, -1.0f);
+    if (ROWS) {
+        __shared__ TapEntry s_tap[kTapChunk];
+        const int e0 = rv.tap_start[r], e1 = rv.tap_start[r + 1];
+        for (int base = e0; base < e1; base += kTapChunk) {
+            const int cnt = min(kTapChunk, e1 - base);
+            __syncthreads();
+            if (tid < cnt) s_tap[tid] = rv.taps[base + tid];
+            __syncthreads();
+            for (int e = 0; e < cnt; ++e) {
+                const TapEntry te = s_tap[e];
+                float2* Rp = R + te.off;
+                for (int i = tid; i < te.len; i += L::T)
+                    atomic_add_f2_global(&Rp[i], cscale(S.buf[L::pad(wrapmod(te.clo + i, NX))], te.wy));
+            }
+        }
+        return;
+    }
     const int h = w / 2;
     for (int t = 0; t < w; ++t) {
         const int b = wrapmod(r + h - 1 - t, ny);
-        const int q0 = bstart[b], q1 = bstart[b + 1];
-        if (ROWS) {
-            for (int q = q0; q < q1; ++q) {
-                const int p = rv.bucket_rows[q];
-                const float wy = tap_eval(tp, t, 2.0f * rv.row_fy[p] - 1.0f);
-                const int clo = rv.row_clo[p], len = rv.row_len[p];
-                float2* Rp = R + rv.row_off[p];
-                for (int i = tid; i < len; i += L::T) {
-                    const int c = wrapmod(clo + i, NX);
-                    atomic_add_f2_global(&Rp[i], cscale(S.buf[L::pad(c)], wy));
-                }
-            }
-        } else {
+        const int q0 = gv.bucket_start[b], q1 = gv.bucket_start[b + 1];
+        {
             for (int q = q0 + tid; q < q1; q += L::T) {
                 const float wy = tap_eval(tp, t, 2.0f * gv.sfy[q] - 1.0f);
                 const int c0 = gv.slx[q] - (h - 1);

@@ -51,7 +51,8 @@ struct tffr_plan_s {
     // plan-time tables and the intermediate of the FFT passes
     DevBuf<float2> twh_x, twl_x, twh_y, twl_y, T;
     DevBuf<float> deap_x, deap_y;
-    DevBuf<int> d_small;                   // [0] error flag, [1] scan sum
+    DevBuf<int> d_small;                   // [0] error flag, [1] scan sum, [2] longest row
+    DevBuf<long long> d_big;               // [0] total row-buffer cells
     DevBuf<unsigned long long> d_kept;
 
     // points (the caller's coordinate arrays are used in place)
@@ -68,11 +69,13 @@ struct tffr_plan_s {
     int P = 0;
     int64_t R_cells = 0;
     int max_len = 0;
-    DevBuf<int> row_start, row_clo, row_len, row_ly, bucket_rows, bucket_start;
+    DevBuf<int> row_start, row_clo, row_len, row_ly, bucket_start;
     DevBuf<float> row_fy;
     DevBuf<double> row_lam_y;
     DevBuf<int64_t> row_off;
     DevBuf<float2> R;
+    DevBuf<int> tap_start;                 // [ny + 1] taps of each fine row
+    DevBuf<TapEntry> tap_list;             // [P * w]
 
     // general points
     DevBuf<int> lx, ly, perm, slx, cursor;
@@ -401,8 +404,8 @@ RowsView rows_view(const tffr_plan_s* p) {
     v.row_fy = p->row_fy.ptr;
     v.row_lam_y = p->row_lam_y.ptr;
     v.row_off = p->row_off.ptr;
-    v.bucket_start = p->bucket_start.ptr;
-    v.bucket_rows = p->bucket_rows.ptr;
+    v.tap_start = p->tap_start.ptr;
+    v.taps = p->tap_list.ptr;
     return v;
 }
 
@@ -437,6 +440,8 @@ int count_runs(tffr_plan_s* p, int* P_out) {
 int build_rows(tffr_plan_s* p, int P) {
     const int64_t N = p->N;
     const int64_t ntiles = (N + kScanTile - 1) / kScanTile;
+    const int ny = p->ny, w = p->w;
+    const int prow = std::min(std::max(1, (P + 255) / 256), 152 * 8);
     p->P = P;
     CK(grow(p, p->row_start, P));
     CK(grow(p, p->row_clo, P));
@@ -445,47 +450,41 @@ int build_rows(tffr_plan_s* p, int P) {
     CK(grow(p, p->row_fy, P));
     CK(grow(p, p->row_lam_y, P));
     CK(grow(p, p->row_off, P));
-    CK(grow(p, p->bucket_rows, P));
-    CK(grow(p, p->bucket_start, p->ny + 1));
+    CK(grow(p, p->tap_start, ny + 1));
+    CK(grow(p, p->cursor, ny + 1));
+    CK(grow(p, p->tap_list, (int64_t)P * w));
+    CK(grow(p, p->d_big, 1));
     k_emit_run_starts<<<(unsigned)ntiles, kScanThreads, 0, p->stream>>>(N, p->lam_y, p->tiles.ptr,
                                                                          p->row_start.ptr);
     CK_LAUNCH("k_emit_run_starts");
-    k_row_info<<<std::min(P, 152 * 16), 256, 0, p->stream>>>(P, N, p->nx, p->w, p->row_start.ptr, p->lam_x,
+    k_row_info<<<std::min(P, 152 * 16), 256, 0, p->stream>>>(P, N, p->nx, w, p->row_start.ptr, p->lam_x,
                                                                p->lam_y, p->row_clo.ptr, p->row_len.ptr,
                                                                p->row_ly.ptr, p->row_fy.ptr, p->row_lam_y.ptr,
                                                                p->d_small.ptr);
     CK_LAUNCH("k_row_info");
-    // Per-row bookkeeping (P entries) on the host: buffer offsets and the
-    // grouping of rows by fine y cell.
-    std::vector<int> len(P), rly(P);
-    int err = 0;
-    CK(cudaMemcpyAsync(len.data(), p->row_len.ptr, (size_t)P * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaMemcpyAsync(rly.data(), p->row_ly.ptr, (size_t)P * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaMemcpyAsync(&err, p->d_small.ptr, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    k_row_offsets<<<1, kScanThreads, 0, p->stream>>>(P, p->row_len.ptr, p->row_off.ptr, p->d_big.ptr,
+                                                      p->d_small.ptr + 2);
+    CK_LAUNCH("k_row_offsets");
+    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
+    k_tap_count<<<prow, 256, 0, p->stream>>>(P, ny, w, p->row_ly.ptr, p->cursor.ptr);
+    CK_LAUNCH("k_tap_count");
+    k_scan_counts<<<1, kScanThreads, 0, p->stream>>>(ny, p->cursor.ptr, p->tap_start.ptr);
+    CK_LAUNCH("k_scan_counts");
+    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
+    k_tap_fill<<<prow, 256, 0, p->stream>>>(P, ny, w, p->taps, p->row_ly.ptr, p->row_fy.ptr, p->row_clo.ptr,
+                                            p->row_len.ptr, p->row_off.ptr, p->tap_start.ptr, p->cursor.ptr,
+                                            p->tap_list.ptr);
+    CK_LAUNCH("k_tap_fill");
+    // one read-back: error flag, longest row, total cells
+    int hs[3] = {0, 0, 0};
+    long long tot = 0;
+    CK(cudaMemcpyAsync(hs, p->d_small.ptr, 3 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(&tot, p->d_big.ptr, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
-    if (err) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_x or |lam_x| >= 2^28");
-    std::vector<int64_t> off(P);
-    int64_t tot = 0;
-    int mx = 0;
-    std::vector<int> bstart(p->ny + 1, 0);
-    for (int i = 0; i < P; ++i) {
-        off[i] = tot;
-        tot += len[i];
-        mx = std::max(mx, len[i]);
-        bstart[(rly[i] & (p->ny - 1)) + 1]++;
-    }
-    for (int b = 0; b < p->ny; ++b) bstart[b + 1] += bstart[b];
-    std::vector<int> brows(P), cur(bstart.begin(), bstart.end() - 1);
-    for (int i = 0; i < P; ++i) brows[cur[rly[i] & (p->ny - 1)]++] = i;
+    if (hs[0]) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_x or |lam_x| >= 2^28");
+    p->max_len = hs[2];
     p->R_cells = tot;
-    p->max_len = mx;
     CK(grow(p, p->R, tot));
-    CK(cudaMemcpyAsync(p->row_off.ptr, off.data(), (size_t)P * sizeof(int64_t), cudaMemcpyHostToDevice, p->stream));
-    CK(cudaMemcpyAsync(p->bucket_start.ptr, bstart.data(), (size_t)(p->ny + 1) * sizeof(int),
-                       cudaMemcpyHostToDevice, p->stream));
-    CK(cudaMemcpyAsync(p->bucket_rows.ptr, brows.data(), (size_t)P * sizeof(int), cudaMemcpyHostToDevice,
-                       p->stream));
-    CK(cudaStreamSynchronize(p->stream));
     return TFFR_OK;
 }
 
@@ -712,9 +711,10 @@ int tffr_destroy(tffr_plan_t p) {
     if (!p) return TFFR_OK;
     cudaStreamSynchronize(p->stream);
     release(p->twh_x); release(p->twl_x); release(p->twh_y); release(p->twl_y); release(p->T); release(p->deap_x); release(p->deap_y);
-    release(p->d_small); release(p->d_kept); release(p->D); release(p->tiles);
-    release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly); release(p->bucket_rows);
+    release(p->d_small); release(p->d_kept); release(p->d_big); release(p->D); release(p->tiles);
+    release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly);
     release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);
+    release(p->tap_start); release(p->tap_list);
     release(p->lx); release(p->ly); release(p->perm); release(p->slx); release(p->cursor);
     release(p->fx); release(p->fy); release(p->sfx); release(p->sfy); release(p->sD); release(p->acc);
     for (auto& sp : p->prof)

@@ -6,6 +6,16 @@
 
 namespace tffr {
 
+// One azimuth tap of a pulse row onto a fine row: add wy * R[off + i] to
+// fine x cell (clo + i) mod nx, i < len.
+struct TapEntry {
+    long long off;
+    int clo;
+    int len;
+    float wy;
+    int p;
+};
+
 struct RowsView {
     int P;                          // pulse rows
     const int* row_start;           // [P] first sample of the row (rows are contiguous runs)
@@ -15,8 +25,8 @@ struct RowsView {
     const float* row_fy;            // [P] fine y offset in [0, 1]
     const double* row_lam_y;        // [P] lam_y of the row
     const int64_t* row_off;         // [P] offset of the row buffer in R (cells)
-    const int* bucket_start;        // [ny + 1] rows grouped by row_ly mod ny
-    const int* bucket_rows;         // [P]
+    const int* tap_start;           // [ny + 1] taps of each fine row (CSR)
+    const TapEntry* taps;           // [P * w]
 };
 
 struct GeneralView {
