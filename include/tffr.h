@@ -203,6 +203,30 @@ int tffr_profile(tffr_plan_t plan, int enable);
  */
 int tffr_profile_read(tffr_plan_t plan, double* ms, int64_t* count, int nstages);
 
+/*
+ * Frame weights without a plan and without allocating device memory, for
+ * callers that cannot call cudaMalloc at the point where they need weights
+ * (for example code that runs while a stream is being captured into a CUDA
+ * graph, or under a device-memory budget fixed before it starts).  The paper
+ * has no counterpart of this entry point; it is a packaging of the weights
+ * step.  D_out (device float[N]) receives the same D_n that tffr_weights
+ * computes (FP32 rounding aside: here every sample takes the FP64 closed
+ * form, so it is slower); n_kept (nullable, host) receives the count of
+ * D_n != 0 and makes the call synchronise the stream.  lam_x / lam_y: device
+ * double[N] (lam_y is read only in separable mode); Mx, My: the image sizes
+ * whose Fourier grids truncate the sums.
+ * Scratch: a fixed array in device memory inside the library (about 132 KB per
+ * GPU that loads it, kept until the process exits), so N is limited to
+ * 67,108,864 samples; larger N returns INVALID_ARG.  The first call on a
+ * device looks the array up (cudaGetSymbolAddress): make that first call
+ * before any stream capture.  Every call shares the array, so calls that
+ * overlap on the GPU (several streams, several host threads) race: serialise
+ * them.
+ * Errors: INVALID_ARG for bad sizes, options or NULL pointers; CUDA.
+ */
+int tffr_weights_noalloc(int64_t N, const double* lam_x, const double* lam_y, int Mx, int My,
+                         const tffr_weight_opts* opts, float* D_out, int64_t* n_kept, tffr_stream_t stream);
+
 /* Query sizes and the state of a plan. */
 int tffr_plan_get_info(tffr_plan_t plan, tffr_plan_info* info);
 

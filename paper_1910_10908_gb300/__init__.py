@@ -21,6 +21,7 @@ from ._abi import VALUES, LAYOUTS, WEIGHT_MODES
 
 __all__ = ["TffrError", "Plan", "tffr_plan", "tffr_set_points", "tffr_weights", "tffr_adjoint",
            "tffr_forward", "tffr_destroy", "tffr_plan_get_info", "tffr_profile", "tffr_profile_read",
+           "tffr_weights_noalloc",
            "load_library"]
 
 
@@ -115,6 +116,30 @@ def tffr_forward(plan, image: torch.Tensor, values: torch.Tensor, apply_weights:
     pv = _dev(values, "values") if values.numel() else None
     _check(_abi.load().tffr_forward(plan, _dev(image, "image", torch.complex64), pv, 1 if apply_weights else 0),
            plan)
+
+
+def tffr_weights_noalloc(lam_x: torch.Tensor, lam_y: torch.Tensor, Mx: int, My: int, D_out: torch.Tensor, *,
+                         mode: str = "tffr", separable: bool = False, a: float = 0.01, q: float = 3.0,
+                         tau: float = 0.97, user_D: torch.Tensor | None = None, count: bool = True, stream=None):
+    """Weights without a plan and without device allocation (see include/tffr.h)."""
+    lib = _abi.load()
+    o = _abi.tffr_weight_opts()
+    lib.tffr_default_weight_opts(ctypes.byref(o))
+    o.mode = WEIGHT_MODES[mode]
+    o.separable = 1 if separable else 0
+    o.a, o.q, o.tau = float(a), float(q), float(tau)
+    if user_D is not None:
+        o.user_D = _dev(user_D, "user_D", torch.float32).value
+    N = int(D_out.shape[0])
+    px = _dev(lam_x, "lam_x", torch.float64) if N else None
+    py = _dev(lam_y, "lam_y", torch.float64) if N else None
+    pd = _dev(D_out, "D_out", torch.float32) if N else None
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    kept = ctypes.c_int64(-1)
+    _check(lib.tffr_weights_noalloc(N, px, py, int(Mx), int(My), ctypes.byref(o), pd,
+                                    ctypes.byref(kept) if count else None, ctypes.c_void_p(stream.cuda_stream)))
+    return int(kept.value) if count else None
 
 
 def tffr_plan_get_info(plan) -> dict:

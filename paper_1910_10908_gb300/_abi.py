@@ -55,6 +55,9 @@ SIGNATURES = {
     "tffr_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "tffr_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
+    "tffr_weights_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_int, ctypes.POINTER(tffr_weight_opts), ctypes.c_void_p,
+                                            ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
     "tffr_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tffr_plan_info)]),
     "tffr_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "tffr_error_string": (ctypes.c_char_p, [ctypes.c_int]),

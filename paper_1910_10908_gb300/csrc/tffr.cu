@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -626,6 +627,95 @@ int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_we
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Allocation-free weights (tffr_weights_noalloc)
+//
+// Scratch lives in one file-scope device array, held by every GPU that loads
+// the library until the process exits: per-block kept counts, a count of
+// finished blocks and the total.  In host code the array's name is only a
+// stand-in; its device address comes from cudaGetSymbolAddress, looked up
+// once per device (with that device current) on the first call there.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNaThreads = 256;
+constexpr int kNaPerThread = 8;
+constexpr int kNaPerBlock = kNaThreads * kNaPerThread;          // samples per block
+constexpr int kNaMaxBlocks = 32768;
+constexpr int64_t kNaMaxN = (int64_t)kNaMaxBlocks * kNaPerBlock;  // 67,108,864 samples
+
+struct NoAllocScratch {
+    unsigned int block_kept[kNaMaxBlocks];
+    unsigned int done;
+    unsigned long long total;
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[64] = {nullptr};
+
+// D_n for the block's samples (FP64 closed form, no plan-time fit), then the
+// block's kept count; the last block to finish adds the counts up.
+__global__ void __launch_bounds__(kNaThreads)
+k_weights_noalloc(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y, int Mx, int My,
+                  WeightArgs A, float* __restrict__ D, NoAllocScratch* __restrict__ sc) {
+    __shared__ int s_warp[32];
+    __shared__ bool s_last;
+    const int64_t base = (int64_t)blockIdx.x * kNaPerBlock;
+    int c = 0;
+    for (int k = 0; k < kNaPerThread; ++k) {
+        const int64_t n = base + (int64_t)k * kNaThreads + threadIdx.x;
+        if (n >= N) break;
+        float d;
+        if (A.mode == 1) d = 1.0f;
+        else if (A.mode == 2) d = A.user_D[n];
+        else d = weight_exact(lam_x[n], A.separable ? lam_y[n] : 0.0, Mx, My, A);
+        D[n] = d;
+        c += (d != 0.0f);
+    }
+    int tot;
+    block_exclusive_scan(c, s_warp, &tot);
+    if (threadIdx.x == 0) {
+        sc->block_kept[blockIdx.x] = (unsigned int)tot;
+        __threadfence();
+        s_last = (atomicAdd(&sc->done, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    unsigned long long sum = 0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kNaThreads) sum += __ldcg(&sc->block_kept[b]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    __shared__ unsigned long long s_sum[kNaThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int i = 0; i < kNaThreads / 32; ++i) t += s_sum[i];
+        sc->total = t;
+    }
+}
+
+cudaError_t noalloc_scratch(NoAllocScratch** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = reinterpret_cast<NoAllocScratch*>(g_noalloc_ptr[dev]);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -901,6 +991,51 @@ int tffr_forward(tffr_plan_t p, const void* image, void* values, int apply_weigh
         case TFFR_VALUES_C128: return forward_impl<double2>(p, img, values, apply_weights);
         default: return forward_impl<float2>(p, img, values, apply_weights);
     }
+}
+
+int tffr_weights_noalloc(int64_t N, const double* lam_x, const double* lam_y, int Mx, int My,
+                         const tffr_weight_opts* opts, float* D_out, int64_t* n_kept, tffr_stream_t stream) {
+    if (N < 0 || N > kNaMaxN || Mx < 1 || My < 1) return TFFR_ERR_INVALID_ARG;
+    tffr_weight_opts o;
+    tffr_default_weight_opts(&o);
+    if (opts) o = *opts;
+    if (o.mode < TFFR_WEIGHTS_TFFR || o.mode > TFFR_WEIGHTS_USER) return TFFR_ERR_INVALID_ARG;
+    if (!(o.q > 0) || !(o.q < 1e6) || !(o.a >= 0) || !(o.a < 1e3) || !(o.tau == o.tau) || !(std::fabs(o.tau) < 1e30))
+        return TFFR_ERR_INVALID_ARG;
+    if (N > 0 && (!D_out || (o.mode == TFFR_WEIGHTS_TFFR && !lam_x) ||
+                  (o.mode == TFFR_WEIGHTS_TFFR && o.separable && !lam_y) ||
+                  (o.mode == TFFR_WEIGHTS_USER && !o.user_D)))
+        return TFFR_ERR_INVALID_ARG;
+    if (N == 0) {
+        if (n_kept) *n_kept = 0;
+        return TFFR_OK;
+    }
+    WeightArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.mode = o.mode;
+    A.separable = o.separable ? 1 : 0;
+    A.tau = (float)o.tau;
+    A.tau_d = o.tau;
+    A.a = o.a;
+    A.q = o.q;
+    A.e_minus = std::exp(-o.a / 2.0);
+    A.e_plus = std::exp(o.a / 2.0);
+    A.reach = (int)std::ceil(o.q) + 1;
+    A.user_D = o.user_D;
+    NoAllocScratch* sc = nullptr;
+    if (noalloc_scratch(&sc) != cudaSuccess) return TFFR_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemsetAsync(&sc->done, 0, sizeof(unsigned int), st) != cudaSuccess) return TFFR_ERR_CUDA;
+    const int blocks = (int)((N + kNaPerBlock - 1) / kNaPerBlock);
+    k_weights_noalloc<<<blocks, kNaThreads, 0, st>>>(N, lam_x, lam_y, Mx, My, A, D_out, sc);
+    if (cudaGetLastError() != cudaSuccess) return TFFR_ERR_CUDA;
+    if (n_kept) {
+        unsigned long long k = 0;
+        if (cudaMemcpyAsync(&k, &sc->total, sizeof(k), cudaMemcpyDeviceToHost, st) != cudaSuccess) return TFFR_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return TFFR_ERR_CUDA;
+        *n_kept = (int64_t)k;
+    }
+    return TFFR_OK;
 }
 
 }  // extern "C"
