@@ -10,8 +10,9 @@
 // stride and twiddle shift is a compile-time constant.  Inner DFTs of radix
 // 2..32 are unrolled with constant roots of unity; the inter-stage twiddles
 // exp(2 pi i m / N) come from a two-level table (exp(2 pi i 64 h / N) *
-// exp(2 pi i l / N), m = 64 h + l) staged in shared memory, both levels built
-// in FP64 on the host.
+// exp(2 pi i l / N), m = 64 h + l) or, for the stages whose twiddles are
+// 1024-th roots of unity, from a direct table; all tables are built in FP64 on
+// the host and staged in shared memory.
 #pragma once
 
 #include "common.cuh"
@@ -31,22 +32,23 @@ __device__ __forceinline__ float w32c(int m) {
 }
 __device__ __forceinline__ float w32s(int m) { return w32c(m - 8); }   // sin x = cos(x - pi/2)
 
-// z * exp(sgn * 2 pi i m / 32) for a compile-time m
-template <int M>
-__device__ __forceinline__ float2 rot32(float2 z, float sgn) {
+// z * exp(SGN * 2 pi i m / 32) for a compile-time m
+template <int M, int SGN>
+__device__ __forceinline__ float2 rot32(float2 z) {
     constexpr int m = M & 31;
     if (m == 0) return z;
-    if (m == 8) return make_float2(-sgn * z.y, sgn * z.x);
+    if (m == 8) return SGN > 0 ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
     if (m == 16) return make_float2(-z.x, -z.y);
-    if (m == 24) return make_float2(sgn * z.y, -sgn * z.x);
-    const float c = w32c(m), s = sgn * w32s(m);
+    if (m == 24) return SGN > 0 ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
+    const float c = w32c(m), s = (SGN > 0) ? w32s(m) : -w32s(m);
     return make_float2(z.x * c - z.y * s, z.x * s + z.y * c);
 }
 
 template <int R> struct Dft;
 
 template <> struct Dft<2> {
-    static __device__ __forceinline__ void run(float2* v, float) {
+    template <int SGN>
+    static __device__ __forceinline__ void run(float2* v) {
         const float2 a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
@@ -54,10 +56,11 @@ template <> struct Dft<2> {
 };
 
 template <> struct Dft<4> {
-    static __device__ __forceinline__ void run(float2* v, float sgn) {
+    template <int SGN>
+    static __device__ __forceinline__ void run(float2* v) {
         const float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
         const float2 c = cadd(v[1], v[3]);
-        const float2 d = rot32<8>(csub(v[1], v[3]), sgn);
+        const float2 d = rot32<8, SGN>(csub(v[1], v[3]));
         v[0] = cadd(a, c);
         v[2] = csub(a, c);
         v[1] = cadd(b, d);
@@ -65,29 +68,23 @@ template <> struct Dft<4> {
     }
 };
 
-// w^k O[k] for radix R, w = exp(sgn 2 pi i / R)
-template <int R, int K>
-__device__ __forceinline__ float2 rotR(float2 z, float sgn) {
-    return rot32<(32 / R) * K>(z, sgn);
-}
-
-template <int R, int K>
+template <int R, int K, int SGN>
 struct Combine {
-    static __device__ __forceinline__ void run(float2* v, const float2* e, const float2* o, float sgn) {
-        const float2 t = rotR<R, K>(o[K], sgn);
+    static __device__ __forceinline__ void run(float2* v, const float2* e, const float2* o) {
+        const float2 t = rot32<(32 / R) * K, SGN>(o[K]);     // w^K O[K], w = exp(SGN 2 pi i / R)
         v[K] = cadd(e[K], t);
         v[K + R / 2] = csub(e[K], t);
-        Combine<R, K + 1>::run(v, e, o, sgn);
+        Combine<R, K + 1, SGN>::run(v, e, o);
     }
 };
-template <int R>
-struct Combine<R, R / 2> {
-    static __device__ __forceinline__ void run(float2*, const float2*, const float2*, float) {}
+template <int R, int SGN>
+struct Combine<R, R / 2, SGN> {
+    static __device__ __forceinline__ void run(float2*, const float2*, const float2*) {}
 };
 
 // radix 2 x radix R/2 split: X[k] = E[k] + w^k O[k], X[k + R/2] = E[k] - w^k O[k]
-template <int R>
-__device__ __forceinline__ void dft_split2(float2* v, float sgn) {
+template <int R, int SGN>
+__device__ __forceinline__ void dft_split2(float2* v) {
     constexpr int H = R / 2;
     float2 e[H], o[H];
 #pragma unroll
@@ -95,19 +92,22 @@ __device__ __forceinline__ void dft_split2(float2* v, float sgn) {
         e[i] = v[2 * i];
         o[i] = v[2 * i + 1];
     }
-    Dft<H>::run(e, sgn);
-    Dft<H>::run(o, sgn);
-    Combine<R, 0>::run(v, e, o, sgn);
+    Dft<H>::template run<SGN>(e);
+    Dft<H>::template run<SGN>(o);
+    Combine<R, 0, SGN>::run(v, e, o);
 }
 
 template <> struct Dft<8> {
-    static __device__ __forceinline__ void run(float2* v, float sgn) { dft_split2<8>(v, sgn); }
+    template <int SGN>
+    static __device__ __forceinline__ void run(float2* v) { dft_split2<8, SGN>(v); }
 };
 template <> struct Dft<16> {
-    static __device__ __forceinline__ void run(float2* v, float sgn) { dft_split2<16>(v, sgn); }
+    template <int SGN>
+    static __device__ __forceinline__ void run(float2* v) { dft_split2<16, SGN>(v); }
 };
 template <> struct Dft<32> {
-    static __device__ __forceinline__ void run(float2* v, float sgn) { dft_split2<32>(v, sgn); }
+    template <int SGN>
+    static __device__ __forceinline__ void run(float2* v) { dft_split2<32, SGN>(v); }
 };
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
@@ -128,38 +128,55 @@ struct Line {
     static constexpr int PADLEN = N + N / V + 1;          // padded shared line
     static constexpr int NH = N >= 64 ? N / 64 : 1;       // twiddle table levels
     static constexpr int NL = N >= 64 ? 64 : N;
-    static constexpr int SMEM_ELEMS = PADLEN + 128 + 64;
+    static constexpr int NT = N >= 1024 ? 1024 : N;       // direct table of the NT-th roots of unity
+    static constexpr int SMEM_ELEMS = PADLEN + 128 + 64 + 1024;
     __device__ __forceinline__ static int pad(int i) { return i + (i >> LV); }
 };
 
 struct Twiddles {
     const float2* h;        // shared: exp(2 pi i 64 h / N)
     const float2* l;        // shared: exp(2 pi i l / N)
+    const float2* t;        // shared: exp(2 pi i m / NT), NT = min(N, 1024)
     __device__ __forceinline__ float2 operator()(int m) const { return cmul(h[m >> 6], l[m & 63]); }
 };
 
+template <int SGN>
+__device__ __forceinline__ float2 conj_if(float2 w) {
+    return SGN > 0 ? w : make_float2(w.x, -w.y);
+}
+
 // Registers v hold the stage input as v[b*R + r] = x[j_b + r N/R], j_b = tid + b T
-// (B = V / R butterflies per thread).  Apply twiddles and DFTs in place.
-template <int LOGN, int R, int LOGNS>
-__device__ __forceinline__ void stage_compute(float2 (&v)[Line<LOGN>::V], const Twiddles& tw, float sgn) {
+// (B = V / R butterflies per thread).  Apply twiddles W_{NS R}^{SGN r k}
+// (k = j_b mod NS) and the radix-R DFTs in place.  When NS R divides 1024 the
+// twiddles come straight from the table of 1024-th roots; otherwise
+// w = W_{NS R}^k comes from the two-level table and w^r from a product tree
+// (w^{2i} = (w^i)^2, w^{2i+1} = w^{2i} w: at most five products deep).
+template <int LOGN, int R, int LOGNS, int SGN>
+__device__ __forceinline__ void stage_compute(float2 (&v)[Line<LOGN>::V], const Twiddles& tw) {
     using L = Line<LOGN>;
     constexpr int B = L::V / R;
     constexpr int NS = 1 << LOGNS;
-    constexpr int TSHIFT = LOGN - LOGNS - ilog2c(R);
+    constexpr int LOGR = ilog2c(R);
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        if (NS > 1) {
+        if constexpr (NS > 1) {
             const int k = (threadIdx.x + b * L::T) & (NS - 1);
-            if (k != 0) {
+            if constexpr (NS * R <= L::NT) {
+                constexpr int TS = ilog2c(L::NT) - LOGNS - LOGR;     // W_{NS R} = W_NT^(2^TS)
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    float2 t = tw((r * k) << TSHIFT);
-                    t.y *= sgn;
-                    v[b * R + r] = cmul(v[b * R + r], t);
-                }
+                for (int r = 1; r < R; ++r)
+                    v[b * R + r] = cmul(v[b * R + r], conj_if<SGN>(tw.t[(r * k) << TS]));
+            } else {
+                constexpr int TSHIFT = LOGN - LOGNS - LOGR;
+                float2 p[R];
+                p[1] = conj_if<SGN>(tw(k << TSHIFT));
+#pragma unroll
+                for (int r = 2; r < R; ++r) p[r] = (r & 1) ? cmul(p[r - 1], p[1]) : cmul(p[r / 2], p[r / 2]);
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[b * R + r] = cmul(v[b * R + r], p[r]);
             }
         }
-        Dft<R>::run(&v[b * R], sgn);
+        Dft<R>::template run<SGN>(&v[b * R]);
     }
 }
 
@@ -189,54 +206,54 @@ __device__ __forceinline__ void stage_store(const float2 (&v)[Line<LOGN>::V], fl
 }
 
 // One full stage in shared memory: load, sync, compute, store, sync.
-template <int LOGN, int R, int LOGNS>
-__device__ __forceinline__ void stage_smem(float2* buf, const Twiddles& tw, float sgn) {
+template <int LOGN, int R, int LOGNS, int SGN>
+__device__ __forceinline__ void stage_smem(float2* buf, const Twiddles& tw) {
     float2 v[Line<LOGN>::V];
     stage_load<LOGN, R>(v, buf);
     __syncthreads();
-    stage_compute<LOGN, R, LOGNS>(v, tw, sgn);
+    stage_compute<LOGN, R, LOGNS, SGN>(v, tw);
     stage_store<LOGN, R, LOGNS>(v, buf);
     __syncthreads();
 }
 
 // Stages S..NFULL-1 of radix V (S counts from 0), as a compile-time recursion.
-template <int LOGN, int S, int STOP>
+template <int LOGN, int S, int STOP, int SGN>
 struct FullStages {
-    static __device__ __forceinline__ void run(float2* buf, const Twiddles& tw, float sgn) {
+    static __device__ __forceinline__ void run(float2* buf, const Twiddles& tw) {
         using L = Line<LOGN>;
-        stage_smem<LOGN, L::V, S * L::LV>(buf, tw, sgn);
-        FullStages<LOGN, S + 1, STOP>::run(buf, tw, sgn);
+        stage_smem<LOGN, L::V, S * L::LV, SGN>(buf, tw);
+        FullStages<LOGN, S + 1, STOP, SGN>::run(buf, tw);
     }
 };
-template <int LOGN, int STOP>
-struct FullStages<LOGN, STOP, STOP> {
-    static __device__ __forceinline__ void run(float2*, const Twiddles&, float) {}
+template <int LOGN, int STOP, int SGN>
+struct FullStages<LOGN, STOP, STOP, SGN> {
+    static __device__ __forceinline__ void run(float2*, const Twiddles&) {}
 };
 
 // Whole FFT in shared memory (indexed with Line<LOGN>::pad); the caller has
 // synchronised after filling buf; the result is in buf, in natural order,
 // after the call (which ends with a barrier).
-template <int LOGN>
-__device__ __forceinline__ void fft_line_smem(float2* buf, const Twiddles& tw, float sgn) {
+template <int LOGN, int SGN>
+__device__ __forceinline__ void fft_line_smem(float2* buf, const Twiddles& tw) {
     using L = Line<LOGN>;
-    FullStages<LOGN, 0, L::NFULL>::run(buf, tw, sgn);
-    if constexpr (L::REM > 0) stage_smem<LOGN, (1 << L::REM), L::NFULL * L::LV>(buf, tw, sgn);
+    FullStages<LOGN, 0, L::NFULL, SGN>::run(buf, tw);
+    if constexpr (L::REM > 0) stage_smem<LOGN, (1 << L::REM), L::NFULL * L::LV, SGN>(buf, tw);
 }
 
 // As fft_line_smem, but the last stage hands each output to epi(index, value)
 // from registers instead of storing it (no barrier after; the stage's loads
 // are complete, so the epilogue may write buf).
-template <int LOGN, typename Epi>
-__device__ __forceinline__ void fft_line_epilogue(float2* buf, const Twiddles& tw, float sgn, Epi& epi) {
+template <int LOGN, int SGN, typename Epi>
+__device__ __forceinline__ void fft_line_epilogue(float2* buf, const Twiddles& tw, Epi& epi) {
     using L = Line<LOGN>;
     constexpr int NSMEM = L::REM ? L::NFULL : L::NFULL - 1;
     constexpr int R = L::REM ? (1 << L::REM) : L::V;
     constexpr int LOGNS = NSMEM * L::LV;
-    FullStages<LOGN, 0, NSMEM>::run(buf, tw, sgn);
+    FullStages<LOGN, 0, NSMEM, SGN>::run(buf, tw);
     float2 v[L::V];
     stage_load<LOGN, R>(v, buf);
     __syncthreads();
-    stage_compute<LOGN, R, LOGNS>(v, tw, sgn);
+    stage_compute<LOGN, R, LOGNS, SGN>(v, tw);
     constexpr int B = L::V / R;
 #pragma unroll
     for (int b = 0; b < B; ++b)
@@ -244,14 +261,17 @@ __device__ __forceinline__ void fft_line_epilogue(float2* buf, const Twiddles& t
         for (int r = 0; r < R; ++r) epi(threadIdx.x + b * L::T + r * (L::N / R), v[b * R + r]);
 }
 
-// Load the two-level twiddle table of an N-point line into shared memory.
+// Load the twiddle tables of an N-point line into shared memory: the two
+// levels for any exponent and the direct table of the NT-th roots.
 template <int LOGN>
-__device__ __forceinline__ Twiddles load_twiddles(float2* s_twh, float2* s_twl, const float2* __restrict__ twh,
-                                                  const float2* __restrict__ twl) {
+__device__ __forceinline__ Twiddles load_twiddles(float2* s_twh, float2* s_twl, float2* s_tt,
+                                                  const float2* __restrict__ twh, const float2* __restrict__ twl,
+                                                  const float2* __restrict__ tt) {
     using L = Line<LOGN>;
     for (int i = threadIdx.x; i < L::NH; i += L::T) s_twh[i] = twh[i];
     for (int i = threadIdx.x; i < L::NL; i += L::T) s_twl[i] = twl[i];
-    return Twiddles{s_twh, s_twl};
+    for (int i = threadIdx.x; i < L::NT; i += L::T) s_tt[i] = tt[i];
+    return Twiddles{s_twh, s_twl, s_tt};
 }
 
 }  // namespace tffr

@@ -11,7 +11,7 @@ namespace {
 
 template <int LOGN>
 size_t line_smem() {
-    return (size_t)Line<LOGN>::SMEM_ELEMS * sizeof(float2);
+    return line_smem_bytes<LOGN>();
 }
 
 template <typename K>

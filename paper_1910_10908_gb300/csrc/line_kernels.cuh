@@ -56,13 +56,19 @@ struct LineSmem {
     float2* buf;
     float2* twh;
     float2* twl;
+    float2* tt;
     __device__ __forceinline__ explicit LineSmem(float2* base) {
         buf = base;
         twh = base + Line<LOGN>::PADLEN;
         twl = twh + 128;
+        tt = twl + 64;
     }
 };
 
+template <int LOGN>
+__host__ __device__ constexpr size_t line_smem_bytes() {
+    return (size_t)Line<LOGN>::SMEM_ELEMS * sizeof(float2);
+}
 // Pass-1 epilogue: keep the M_x = N/2 wanted x modes, deapodise, store row r of T.
 template <int LOGN>
 struct RowOut {
@@ -96,7 +102,7 @@ k_adj_rows(RowsView rv, const float2* __restrict__ R, int ny, int w, TapPoly tp,
         for (int jx = tid; jx < MX; jx += L::T) T[(size_t)r * MX + jx] = make_float2(0.f, 0.f);
         return;
     }
-    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
     for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
     __shared__ TapEntry s_tap[kTapChunk];
     for (int base = e0; base < e1; base += kTapChunk) {
@@ -113,7 +119,7 @@ k_adj_rows(RowsView rv, const float2* __restrict__ R, int ny, int w, TapPoly tp,
     }
     __syncthreads();
     RowOut<LOGN> epi{r, deap_x, T};
-    fft_line_epilogue<LOGN>(S.buf, tw, +1.0f, epi);
+    fft_line_epilogue<LOGN, +1>(S.buf, tw, epi);
 }
 
 // Pass 1 of the adjoint, general points: the samples of the w buckets whose
@@ -133,7 +139,7 @@ k_adj_rows_general(GeneralView gv, const float2* __restrict__ sval, int ny, int 
         for (int jx = tid; jx < MX; jx += L::T) T[(size_t)r * MX + jx] = make_float2(0.f, 0.f);
         return;
     }
-    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
     for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
     __syncthreads();
     const int h = w / 2;
@@ -151,7 +157,7 @@ k_adj_rows_general(GeneralView gv, const float2* __restrict__ sval, int ny, int 
     }
     __syncthreads();
     RowOut<LOGN> epi{r, deap_x, T};
-    fft_line_epilogue<LOGN>(S.buf, tw, +1.0f, epi);
+    fft_line_epilogue<LOGN, +1>(S.buf, tw, epi);
 }
 
 // Pass-2 epilogue: keep the M_y = N/2 wanted y modes, deapodise, park them in
@@ -182,29 +188,33 @@ k_adj_cols(const float2* __restrict__ T, int Mx, FftTables tab, const float* __r
     const int rank = (int)cluster.block_rank();
     const int jx0 = (int)blockIdx.x - rank;           // first of the cluster's 4 columns
     const int tid = threadIdx.x;
-    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
-    float2* peer[kColCluster];
-#pragma unroll
-    for (int k = 0; k < kColCluster; ++k) peer[k] = cluster.map_shared_rank(S.buf, k);
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
+    // element i = tid + u T of the scatter/gather belongs to column i % 4 =
+    // tid % 4 (T is a multiple of 4), so each thread talks to one peer only
+    static_assert(L::T % kColCluster == 0, "line threads must be a multiple of the cluster size");
+    float2* const peer = cluster.map_shared_rank(S.buf, tid % kColCluster);
     // scatter: this CTA reads rows [rank NY/4, (rank+1) NY/4) of the 4 columns,
-    // exactly V elements per thread, all loads issued before the remote stores
+    // exactly V elements per thread; the global loads overlap the barrier that
+    // makes sure every CTA of the cluster runs before its memory is written
     constexpr int ROWS = NY / kColCluster;
     {
+        cluster.barrier_arrive();
         float2 tmp[V];
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int i = tid + u * L::T;
             tmp[u] = __ldg(&T[(size_t)(rank * ROWS + i / kColCluster) * Mx + jx0 + i % kColCluster]);
         }
+        cluster.barrier_wait();
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int i = tid + u * L::T;
-            peer[i % kColCluster][L::pad(rank * ROWS + i / kColCluster)] = tmp[u];
+            peer[L::pad(rank * ROWS + i / kColCluster)] = tmp[u];
         }
     }
     cluster.sync();
     ColPark<LOGN> epi{deap_y, S.buf};
-    fft_line_epilogue<LOGN>(S.buf, tw, +1.0f, epi);
+    fft_line_epilogue<LOGN, +1>(S.buf, tw, epi);
     cluster.sync();
     // gather: this CTA stores image rows [rank MY/4, (rank+1) MY/4) of the 4 columns
     constexpr int OROWS = MY / kColCluster;
@@ -213,15 +223,16 @@ k_adj_cols(const float2* __restrict__ T, int Mx, FftTables tab, const float* __r
 #pragma unroll
         for (int u = 0; u < V / 2; ++u) {
             const int i = tid + u * L::T;
-            tmp[u] = peer[i % kColCluster][L::pad(rank * OROWS + i / kColCluster)];
+            tmp[u] = peer[L::pad(rank * OROWS + i / kColCluster)];
         }
+        cluster.barrier_arrive();                      // peers may leave once every remote read is done
 #pragma unroll
         for (int u = 0; u < V / 2; ++u) {
             const int i = tid + u * L::T;
             img[(size_t)(rank * OROWS + i / kColCluster) * Mx + jx0 + i % kColCluster] = tmp[u];
         }
+        cluster.barrier_wait();
     }
-    cluster.sync();                                    // peers may still read this CTA's buffer
 }
 
 template <int LOGN>
@@ -236,31 +247,34 @@ k_fwd_cols(const float2* __restrict__ img, int Mx, FftTables tab, const float* _
     const int rank = (int)cluster.block_rank();
     const int jx0 = (int)blockIdx.x - rank;
     const int tid = threadIdx.x;
-    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
-    for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
-    float2* peer[kColCluster];
-#pragma unroll
-    for (int k = 0; k < kColCluster; ++k) peer[k] = cluster.map_shared_rank(S.buf, k);
-    cluster.sync();                                    // every buffer zeroed before the scatter
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
+    // the scatter below fills modes [-MY/2, MY/2); zero the rest of this CTA's line
+    for (int i = MY / 2 + tid; i < NY - MY / 2; i += L::T) S.buf[L::pad(i)] = make_float2(0.f, 0.f);
+    // element i = tid + u T of the scatter/gather belongs to column i % 4 =
+    // tid % 4 (T is a multiple of 4), so each thread talks to one peer only
+    static_assert(L::T % kColCluster == 0, "line threads must be a multiple of the cluster size");
+    float2* const peer = cluster.map_shared_rank(S.buf, tid % kColCluster);
     constexpr int IROWS = MY / kColCluster;
     {
+        cluster.barrier_arrive();                      // every CTA runs before its memory is written
         float2 tmp[V / 2];
 #pragma unroll
         for (int u = 0; u < V / 2; ++u) {
             const int i = tid + u * L::T;
             tmp[u] = __ldg(&img[(size_t)(rank * IROWS + i / kColCluster) * Mx + jx0 + i % kColCluster]);
         }
+        cluster.barrier_wait();
 #pragma unroll
         for (int u = 0; u < V / 2; ++u) {
             const int i = tid + u * L::T;
             const int jy = rank * IROWS + i / kColCluster;
             const int k = i % kColCluster;
             const float d = __ldg(&deap_y[jy]) * __ldg(&deap_x[jx0 + k]);
-            peer[k][L::pad(wrapmod(jy - MY / 2, NY))] = cscale(tmp[u], d);
+            peer[L::pad(wrapmod(jy - MY / 2, NY))] = cscale(tmp[u], d);
         }
     }
     cluster.sync();
-    fft_line_smem<LOGN>(S.buf, tw, -1.0f);
+    fft_line_smem<LOGN, -1>(S.buf, tw);
     cluster.sync();
     constexpr int ROWS = NY / kColCluster;
     {
@@ -268,15 +282,16 @@ k_fwd_cols(const float2* __restrict__ img, int Mx, FftTables tab, const float* _
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int i = tid + u * L::T;
-            tmp[u] = peer[i % kColCluster][L::pad(rank * ROWS + i / kColCluster)];
+            tmp[u] = peer[L::pad(rank * ROWS + i / kColCluster)];
         }
+        cluster.barrier_arrive();                      // peers may leave once every remote read is done
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int i = tid + u * L::T;
             T[(size_t)(rank * ROWS + i / kColCluster) * Mx + jx0 + i % kColCluster] = tmp[u];
         }
+        cluster.barrier_wait();
     }
-    cluster.sync();
 }
 
 template <int LOGN, bool ROWS>
@@ -294,12 +309,12 @@ k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int ny, in
     } else if (!row_has_taps(gv.bucket_start, r, ny, w)) {
         return;
     }
-    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, tab.twh, tab.twl);
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
     for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
     __syncthreads();
     for (int jx = tid; jx < MX; jx += L::T) S.buf[L::pad(wrapmod(jx - MX / 2, NX))] = T[(size_t)r * MX + jx];
     __syncthreads();
-    fft_line_smem<LOGN>(S.buf, tw, -1.0f);
+    fft_line_smem<LOGN, -1>(S.buf, tw);
     if (ROWS) {
         __shared__ TapEntry s_tap[kTapChunk];
         const int e0 = rv.tap_start[r], e1 = rv.tap_start[r + 1];

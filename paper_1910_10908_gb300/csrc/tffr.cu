@@ -50,7 +50,7 @@ struct tffr_plan_s {
     bool fit_valid = false;
 
     // plan-time tables and the intermediate of the FFT passes
-    DevBuf<float2> twh_x, twl_x, twh_y, twl_y, T;
+    DevBuf<float2> twh_x, twl_x, twh_y, twl_y, tt_x, tt_y, T;
     DevBuf<float> deap_x, deap_y;
     DevBuf<int> d_small;                   // [0] error flag, [1] scan sum, [2] longest row
     DevBuf<long long> d_big;               // [0] total row-buffer cells
@@ -343,6 +343,12 @@ int upload_tables(tffr_plan_s* p) {
     const int nhy = std::max(1, p->ny / 64), nly = std::min(64, p->ny);
     std::vector<float2> hx = level(p->nx, nhx, 64), lx = level(p->nx, nlx, 1);
     std::vector<float2> hy = level(p->ny, nhy, 64), ly = level(p->ny, nly, 1);
+    const int ntx = std::min(1024, p->nx), nty = std::min(1024, p->ny);
+    std::vector<float2> ttx = level(ntx, ntx, 1), tty = level(nty, nty, 1);
+    CK(grow(p, p->tt_x, ntx));
+    CK(grow(p, p->tt_y, nty));
+    CK(cudaMemcpyAsync(p->tt_x.ptr, ttx.data(), ttx.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
+    CK(cudaMemcpyAsync(p->tt_y.ptr, tty.data(), tty.size() * sizeof(float2), cudaMemcpyHostToDevice, p->stream));
     std::vector<float> dx = deapod(p->Mx, p->nx), dy = deapod(p->My, p->ny);
     CK(grow(p, p->twh_x, nhx));
     CK(grow(p, p->twl_x, nlx));
@@ -532,8 +538,8 @@ int build_general(tffr_plan_s* p) {
     return TFFR_OK;
 }
 
-FftTables tables_x(const tffr_plan_s* p) { return FftTables{p->twh_x.ptr, p->twl_x.ptr}; }
-FftTables tables_y(const tffr_plan_s* p) { return FftTables{p->twh_y.ptr, p->twl_y.ptr}; }
+FftTables tables_x(const tffr_plan_s* p) { return FftTables{p->twh_x.ptr, p->twl_x.ptr, p->tt_x.ptr}; }
+FftTables tables_y(const tffr_plan_s* p) { return FftTables{p->twh_y.ptr, p->twl_y.ptr, p->tt_y.ptr}; }
 
 template <typename VT, int W>
 void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values) {
@@ -800,7 +806,8 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
 int tffr_destroy(tffr_plan_t p) {
     if (!p) return TFFR_OK;
     cudaStreamSynchronize(p->stream);
-    release(p->twh_x); release(p->twl_x); release(p->twh_y); release(p->twl_y); release(p->T); release(p->deap_x); release(p->deap_y);
+    release(p->twh_x); release(p->twl_x); release(p->twh_y); release(p->twl_y); release(p->tt_x); release(p->tt_y);
+    release(p->T); release(p->deap_x); release(p->deap_y);
     release(p->d_small); release(p->d_kept); release(p->d_big); release(p->D); release(p->tiles);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly);
     release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);

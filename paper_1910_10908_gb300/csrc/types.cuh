@@ -41,6 +41,7 @@ struct GeneralView {
 struct FftTables {
     const float2* twh;              // exp(2 pi i 64 h / n), h < max(1, n / 64)
     const float2* twl;              // exp(2 pi i l / n), l < min(64, n)
+    const float2* tt;               // exp(2 pi i m / nt), m < nt = min(n, 1024)
 };
 
 }  // namespace tffr
