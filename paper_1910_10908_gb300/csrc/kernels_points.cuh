@@ -139,12 +139,13 @@ __device__ __forceinline__ float weight_tffr(double lam_x, int cx, float fx, dou
 
 // ---------------------------------------------------------------------------
 // Pulse rows: runs of samples with bit-equal lam_y (azimuth is uniform,
-// Sec. II.A).  Order-preserving compaction of the run starts in three passes.
+// Sec. II.A).  One pass over both coordinate arrays finds the run starts
+// (order-preserving compaction with a decoupled look-back across tiles),
+// checks every coordinate and takes each run's extent of fine x cells.
 // ---------------------------------------------------------------------------
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kScanThreads = 1024;                     // single-block scans below
 
+// Exclusive scan of one int per thread across the block; *total = block sum.
 __device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int* total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int v = x;
@@ -171,132 +172,216 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int* tot
     return before;
 }
 
-__device__ __forceinline__ int run_start_flag(const double* __restrict__ lam_y, int64_t n) {
-    if (n == 0) return 1;
-    return __double_as_longlong(lam_y[n]) != __double_as_longlong(lam_y[n - 1]) ? 1 : 0;
+constexpr int kRowScanWarps = 8;
+constexpr int kRowScanK = 16;                          // samples per lane
+constexpr int kRowScanTile = kRowScanWarps * 32 * kRowScanK;
+constexpr unsigned kLookbackSpins = 1u << 22;          // bound on the look-back wait (~0.3 s)
+
+// status word of one tile: flag in bits 62-63 (1: tile count, 2: inclusive
+// prefix), the count in the low 32 bits; zero means not yet published
+__device__ __forceinline__ void lb_publish(unsigned long long* a, unsigned flag, int v) {
+    const unsigned long long w = ((unsigned long long)flag << 62) | (unsigned)v;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a), "l"(w) : "memory");
+}
+__device__ __forceinline__ unsigned long long lb_read(const unsigned long long* a) {
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(a) : "memory");
+    return w;
 }
 
-// Per tile: number of run starts; also checks every lam_y (err bit 1).
-__global__ void k_count_runs(int64_t N, const double* __restrict__ lam_y, int* __restrict__ tile_count,
-                             int* __restrict__ err) {
-    __shared__ int s_warp[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int c = 0;
-    bool bad = false;
+struct RowScanArgs {
+    int* row_start;                                    // [cap] first sample of each run
+    int* row_min;                                      // [cap] smallest fine x cell, INT_MAX at entry
+    int* row_max;                                      // [cap] largest fine x cell, INT_MIN at entry
+    int cap;
+    unsigned long long* status;                        // [tiles] zeroed
+    int* flags;                                        // [0] error bits, [1] runs, [3] overflow, [4] tile ticket
+};
+
+__device__ __forceinline__ void row_extent_flush(const RowScanArgs& a, int id, int mn, int mx) {
+    if (id < a.cap) {
+        atomicMin(&a.row_min[id], mn);
+        atomicMax(&a.row_max[id], mx);
+    } else {
+        atomicOr(&a.flags[3], 1);
+    }
+}
+
+// Error bits: 1 bad lam_y, 2 bad lam_x, 4 look-back wait gave up.  Tiles are
+// taken in launch order from a ticket, so every tile waits only on tiles that
+// already run; the wait is bounded all the same.
+__global__ void __launch_bounds__(kRowScanWarps * 32)
+k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y, RowScanArgs a) {
+    __shared__ int s_tile, s_off;
+    __shared__ int s_cnt[kRowScanWarps];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&a.flags[4], 1);
+    __syncthreads();
+    const int tile = s_tile;
+    const int64_t wbase = (int64_t)tile * kRowScanTile + (int64_t)wid * (32 * kRowScanK);
+    unsigned ball[kRowScanK];
+    int cx[kRowScanK];
+    bool bad_x = false, bad_y = false;
+    int cnt = 0;
+    long long prev = (wbase > 0 && wbase <= N) ? __double_as_longlong(__ldg(&lam_y[wbase - 1])) : 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        const int64_t n = base + (int64_t)threadIdx.x * kScanItems + i;
-        if (n < N) {
-            c += run_start_flag(lam_y, n);
-            int cell;
+    for (int h = 0; h < kRowScanK; h += 8) {
+        long long yb[8];
+        double xv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t n = wbase + (h + k) * 32 + lane;
+            yb[k] = (n < N) ? __double_as_longlong(__ldg(&lam_y[n])) : 0;
+            xv[k] = (n < N) ? __ldg(&lam_x[n]) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int64_t n = wbase + (h + k) * 32 + lane;
+            long long up = __shfl_up_sync(FULL, yb[k], 1);
+            if (lane == 0) up = prev;
+            prev = __shfl_sync(FULL, yb[k], 31);
+            const bool in = n < N;
+            ball[h + k] = __ballot_sync(FULL, in && (n == 0 || yb[k] != up));
+            cnt += __popc(ball[h + k]);
+            int c = 0;
             float f;
-            bad |= !fine_coord(lam_y[n], cell, f);
+            if (in) {
+                bad_y |= !fine_coord(__longlong_as_double(yb[k]), c, f);
+                bad_x |= !fine_coord(xv[k], c, f);
+            }
+            cx[h + k] = c;
         }
     }
-    if (bad) atomicOr(err, 1);
-    int total;
-    block_exclusive_scan(c, s_warp, &total);
-    if (threadIdx.x == 0) tile_count[blockIdx.x] = total;
-}
-
-// Exclusive scan of tile counts in place (single block, any length); writes the sum to *sum.
-__global__ void k_scan_tile_counts(int ntiles, int* __restrict__ counts, int* __restrict__ sum) {
-    __shared__ int s_warp[32];
-    int carry = 0;
-    for (int base = 0; base < ntiles; base += kScanThreads) {
-        const int i = base + threadIdx.x;
-        const int x = (i < ntiles) ? counts[i] : 0;
-        int total;
-        const int ex = block_exclusive_scan(x, s_warp, &total);
-        if (i < ntiles) counts[i] = carry + ex;
-        carry += total;
+    if (bad_y) atomicOr(&a.flags[0], 1);
+    if (bad_x) atomicOr(&a.flags[0], 2);
+    if (lane == 0) s_cnt[wid] = cnt;
+    __syncthreads();
+    int woff = 0, agg = 0;
+#pragma unroll
+    for (int i = 0; i < kRowScanWarps; ++i) {
+        const int t = s_cnt[i];
+        woff += (i < wid) ? t : 0;
+        agg += t;
     }
-    if (threadIdx.x == 0) *sum = carry;
-}
-
-__global__ void k_emit_run_starts(int64_t N, const double* __restrict__ lam_y, const int* __restrict__ tile_off,
-                                  int* __restrict__ row_start) {
-    __shared__ int s_warp[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int c = 0;
-    int f[kScanItems];
+    // decoupled look-back, one warp: 32 predecessors per step, back to the
+    // nearest tile that published its inclusive prefix
+    if (wid == 0) {
+        int excl = 0;
+        if (tile == 0) {
+            if (lane == 0) lb_publish(&a.status[0], 2, agg);
+        } else {
+            if (lane == 0) lb_publish(&a.status[tile], 1, agg);
+            int top = tile - 1;
+            unsigned spins = 0;
+            while (true) {
+                const int j = top - lane;
+                const unsigned long long w = (j >= 0) ? lb_read(&a.status[j]) : (2ull << 62);
+                const unsigned fl = (unsigned)(w >> 62);
+                const unsigned incl = __ballot_sync(FULL, fl == 2), pending = __ballot_sync(FULL, fl == 0);
+                const int first_incl = incl ? __ffs(incl) - 1 : 32;
+                const int first_pending = pending ? __ffs(pending) - 1 : 32;
+                if (first_pending < first_incl) {              // a tile before the nearest prefix is not ready
+                    if (++spins > kLookbackSpins) {
+                        if (lane == 0) atomicOr(&a.flags[0], 4);
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                const int last = incl ? first_incl : 31;       // nearest inclusive lane
+                int v = (lane <= last) ? (int)(unsigned)w : 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        const int64_t n = base + (int64_t)threadIdx.x * kScanItems + i;
-        f[i] = (n < N) ? run_start_flag(lam_y, n) : 0;
-        c += f[i];
-    }
-    int total;
-    int pos = tile_off[blockIdx.x] + block_exclusive_scan(c, s_warp, &total);
-#pragma unroll
-    for (int i = 0; i < kScanItems; ++i)
-        if (f[i]) row_start[pos++] = (int)(base + (int64_t)threadIdx.x * kScanItems + i);
-}
-
-// Per pulse row: extent of its x footprint (checking every lam_x, err bit 1),
-// and its y cell/offset.  row_clo is the first fine x cell of the row buffer,
-// row_len its cells; a row whose footprint spans >= nx cells uses the whole
-// periodic row (row_clo = 0, row_len = nx, cells reduced modulo nx).
-__global__ void k_row_info(int P, int64_t N, int nx, int w, const int* __restrict__ row_start,
-                           const double* __restrict__ lam_x, const double* __restrict__ lam_y,
-                           int* __restrict__ row_clo, int* __restrict__ row_len, int* __restrict__ row_ly,
-                           float* __restrict__ row_fy, double* __restrict__ row_lam_y, int* __restrict__ err) {
-    __shared__ int s_min[32], s_max[32];
-    for (int p = blockIdx.x; p < P; p += gridDim.x) {
-        const int64_t s = row_start[p];
-        const int64_t e = (p + 1 < P) ? row_start[p + 1] : N;
-        int mn = 0x7fffffff, mx = -0x7fffffff;
-        bool bad = false;
-        for (int64_t n = s + threadIdx.x; n < e; n += blockDim.x) {
-            int c;
-            float f;
-            bad |= !fine_coord(lam_x[n], c, f);
-            mn = min(mn, c);
-            mx = max(mx, c);
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                excl += v;
+                if (incl) break;
+                top -= 32;
+            }
+            if (lane == 0) lb_publish(&a.status[tile], 2, excl + agg);
         }
-        if (bad) atomicOr(err, 1);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         if (lane == 0) {
-            s_min[wid] = mn;
-            s_max[wid] = mx;
+            s_off = excl;
+            if (tile == (int)gridDim.x - 1) a.flags[1] = excl + agg;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
-                mn = min(mn, s_min[i]);
-                mx = max(mx, s_max[i]);
+    }
+    __syncthreads();
+    // emit run starts in sample order and fold each lane's cells into the
+    // extent of its run (runs are contiguous, so a lane's run ids only grow)
+    const unsigned le = FULL >> (31 - lane);
+    int pre = s_off + woff;
+    int cur = -1, mn = 0x7fffffff, mx = -0x7fffffff - 1;
+    bool over = false;
+#pragma unroll
+    for (int k = 0; k < kRowScanK; ++k) {
+        const int64_t n = wbase + k * 32 + lane;
+        const int id = pre + __popc(ball[k] & le) - 1;
+        if (n < N) {
+            if ((ball[k] >> lane) & 1u) {
+                if (id < a.cap) a.row_start[id] = (int)n;
+                else over = true;
             }
-            const int h = w / 2;
-            const long long span = (long long)mx - (long long)mn + w;
-            if (span >= nx) {
-                row_clo[p] = 0;
-                row_len[p] = nx;
+            if (id != cur) {
+                if (cur >= 0) row_extent_flush(a, cur, mn, mx);
+                cur = id;
+                mn = mx = cx[k];
             } else {
-                row_clo[p] = mn - (h - 1);
-                row_len[p] = (int)span;
+                mn = min(mn, cx[k]);
+                mx = max(mx, cx[k]);
             }
-            const double ly = lam_y[s];
-            int cy;
-            float fy;
-            fine_coord(ly, cy, fy);
-            row_ly[p] = cy;
-            row_fy[p] = fy;
-            row_lam_y[p] = ly;
         }
-        __syncthreads();
+        pre += __popc(ball[k]);
+    }
+    if (over) atomicOr(&a.flags[3], 1);
+    if (__all_sync(FULL, cur == __shfl_sync(FULL, cur, 0))) {
+        const int m0 = __reduce_min_sync(FULL, mn), m1 = __reduce_max_sync(FULL, mx);
+        if (lane == 0 && cur >= 0) row_extent_flush(a, cur, m0, m1);
+    } else if (cur >= 0) {
+        row_extent_flush(a, cur, mn, mx);
+    }
+}
+
+__global__ void k_fill_int(int n, int v, int* __restrict__ a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
+}
+
+// Per pulse row: x footprint from the cell extent (the row buffer's first
+// fine cell row_clo and its length row_len; a footprint of >= nx cells takes
+// the whole periodic row, row_clo = 0, row_len = nx) and the row's y cell.
+// Puts the extent arrays back to their identities for the next scan.
+__global__ void k_row_finish(const int* __restrict__ runs, int cap, int nx, int w, const double* __restrict__ lam_y,
+                             const int* __restrict__ row_start, int* __restrict__ row_min, int* __restrict__ row_max,
+                             int* __restrict__ row_clo, int* __restrict__ row_len, int* __restrict__ row_ly,
+                             float* __restrict__ row_fy, double* __restrict__ row_lam_y) {
+    const int P = min(*runs, cap);
+    const int h = w / 2;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const int mn = row_min[p], mx = row_max[p];
+        row_min[p] = 0x7fffffff;
+        row_max[p] = -0x7fffffff - 1;
+        const long long span = (long long)mx - (long long)mn + w;
+        if (span >= nx) {
+            row_clo[p] = 0;
+            row_len[p] = nx;
+        } else {
+            row_clo[p] = mn - (h - 1);
+            row_len[p] = (int)span;
+        }
+        const double ly = lam_y[row_start[p]];
+        int cy;
+        float fy;
+        fine_coord(ly, cy, fy);
+        row_ly[p] = cy;
+        row_fy[p] = fy;
+        row_lam_y[p] = ly;
     }
 }
 
 // Row buffer offsets (exclusive scan of row_len, single block, any P), the
 // total cells and the longest row: out[0] = total (int64), out32[0] = max len.
-__global__ void k_row_offsets(int P, const int* __restrict__ row_len, int64_t* __restrict__ row_off,
-                              long long* __restrict__ total, int* __restrict__ max_len) {
+__global__ void k_row_offsets(const int* __restrict__ runs, int cap, const int* __restrict__ row_len,
+                              int64_t* __restrict__ row_off, long long* __restrict__ total, int* __restrict__ max_len) {
     __shared__ int s_warp[32];
+    const int P = min(*runs, cap);
     long long carry = 0;
     int mx = 0;
     for (int base = 0; base < P; base += kScanThreads) {
@@ -316,7 +401,9 @@ __global__ void k_row_offsets(int P, const int* __restrict__ row_len, int64_t* _
 
 // Azimuth taps of every pulse row, grouped by the fine row they reach: pulse
 // row p adds phi(t - (w/2 - 1) - fy_p) R_p to fine row ly_p - (w/2 - 1) + t.
-__global__ void k_tap_count(int P, int ny, int w, const int* __restrict__ row_ly, int* __restrict__ count) {
+__global__ void k_tap_count(const int* __restrict__ runs, int cap, int ny, int w, const int* __restrict__ row_ly,
+                            int* __restrict__ count) {
+    const int P = min(*runs, cap);
     const int h = w / 2;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
         for (int t = 0; t < w; ++t) atomicAdd(&count[wrapmod(row_ly[p] - (h - 1) + t, ny)], 1);
@@ -337,10 +424,11 @@ __global__ void k_scan_counts(int n, const int* __restrict__ count, int* __restr
     if (threadIdx.x == 0) start[n] = carry;
 }
 
-__global__ void k_tap_fill(int P, int ny, int w, TapPoly tp, const int* __restrict__ row_ly,
+__global__ void k_tap_fill(const int* __restrict__ runs, int cap, int ny, int w, TapPoly tp, const int* __restrict__ row_ly,
                            const float* __restrict__ row_fy, const int* __restrict__ row_clo,
                            const int* __restrict__ row_len, const int64_t* __restrict__ row_off,
                            const int* __restrict__ start, int* __restrict__ cursor, TapEntry* __restrict__ taps) {
+    const int P = min(*runs, cap);
     const int h = w / 2;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         const float s = 2.0f * row_fy[p] - 1.0f;

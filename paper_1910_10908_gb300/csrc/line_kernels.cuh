@@ -33,6 +33,14 @@ namespace cg = cooperative_groups;
 constexpr int kColCluster = 4;
 constexpr int kTapChunk = 64;                          // tap entries staged per round
 
+// Cluster barrier without memory ordering (the caller needs none).
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void atomic_add_f2_global(float2* p, float2 v) {
 #if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
     atomicAdd(p, v);
@@ -108,7 +116,7 @@ k_adj_rows(RowsView rv, const float2* __restrict__ R, int ny, int w, TapPoly tp,
     for (int base = e0; base < e1; base += kTapChunk) {
         const int cnt = min(kTapChunk, e1 - base);
         __syncthreads();                               // zeroing done / previous chunk consumed
-        if (tid < cnt) s_tap[tid] = rv.taps[base + tid];
+        for (int i = tid; i < cnt; i += L::T) s_tap[i] = rv.taps[base + i];   // T may be < chunk
         __syncthreads();
         for (int e = 0; e < cnt; ++e) {
             const TapEntry te = s_tap[e];
@@ -198,14 +206,14 @@ k_adj_cols(const float2* __restrict__ T, int Mx, FftTables tab, const float* __r
     // makes sure every CTA of the cluster runs before its memory is written
     constexpr int ROWS = NY / kColCluster;
     {
-        cluster.barrier_arrive();
+        cluster_arrive_relaxed();                      // existence only: the sync below orders the data
         float2 tmp[V];
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int i = tid + u * L::T;
             tmp[u] = __ldg(&T[(size_t)(rank * ROWS + i / kColCluster) * Mx + jx0 + i % kColCluster]);
         }
-        cluster.barrier_wait();
+        cluster_wait();
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int i = tid + u * L::T;
@@ -225,14 +233,16 @@ k_adj_cols(const float2* __restrict__ T, int Mx, FftTables tab, const float* __r
             const int i = tid + u * L::T;
             tmp[u] = peer[L::pad(rank * OROWS + i / kColCluster)];
         }
-        cluster.barrier_arrive();                      // peers may leave once every remote read is done
 #pragma unroll
         for (int u = 0; u < V / 2; ++u) {
             const int i = tid + u * L::T;
             img[(size_t)(rank * OROWS + i / kColCluster) * Mx + jx0 + i % kColCluster] = tmp[u];
         }
-        cluster.barrier_wait();
     }
+    // the stores above consumed every remote load, so peers may leave once all
+    // threads got here; no memory ordering is needed
+    cluster_arrive_relaxed();
+    cluster_wait();
 }
 
 template <int LOGN>
@@ -256,14 +266,14 @@ k_fwd_cols(const float2* __restrict__ img, int Mx, FftTables tab, const float* _
     float2* const peer = cluster.map_shared_rank(S.buf, tid % kColCluster);
     constexpr int IROWS = MY / kColCluster;
     {
-        cluster.barrier_arrive();                      // every CTA runs before its memory is written
+        cluster_arrive_relaxed();                      // every CTA runs before its memory is written
         float2 tmp[V / 2];
 #pragma unroll
         for (int u = 0; u < V / 2; ++u) {
             const int i = tid + u * L::T;
             tmp[u] = __ldg(&img[(size_t)(rank * IROWS + i / kColCluster) * Mx + jx0 + i % kColCluster]);
         }
-        cluster.barrier_wait();
+        cluster_wait();
 #pragma unroll
         for (int u = 0; u < V / 2; ++u) {
             const int i = tid + u * L::T;
@@ -284,14 +294,14 @@ k_fwd_cols(const float2* __restrict__ img, int Mx, FftTables tab, const float* _
             const int i = tid + u * L::T;
             tmp[u] = peer[L::pad(rank * ROWS + i / kColCluster)];
         }
-        cluster.barrier_arrive();                      // peers may leave once every remote read is done
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int i = tid + u * L::T;
             T[(size_t)(rank * ROWS + i / kColCluster) * Mx + jx0 + i % kColCluster] = tmp[u];
         }
-        cluster.barrier_wait();
     }
+    cluster_arrive_relaxed();                          // every remote load was consumed above
+    cluster_wait();
 }
 
 template <int LOGN, bool ROWS>
@@ -321,7 +331,7 @@ k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int ny, in
         for (int base = e0; base < e1; base += kTapChunk) {
             const int cnt = min(kTapChunk, e1 - base);
             __syncthreads();
-            if (tid < cnt) s_tap[tid] = rv.taps[base + tid];
+            for (int i = tid; i < cnt; i += L::T) s_tap[i] = rv.taps[base + i];   // T may be < chunk
             __syncthreads();
             for (int e = 0; e < cnt; ++e) {
                 const TapEntry te = s_tap[e];

@@ -52,7 +52,7 @@ struct tffr_plan_s {
     // plan-time tables and the intermediate of the FFT passes
     DevBuf<float2> twh_x, twl_x, twh_y, twl_y, tt_x, tt_y, T;
     DevBuf<float> deap_x, deap_y;
-    DevBuf<int> d_small;                   // [0] error flag, [1] scan sum, [2] longest row
+    DevBuf<int> d_small;                   // [0] error bits, [1] runs, [2] longest row, [3] overflow, [4] ticket
     DevBuf<long long> d_big;               // [0] total row-buffer cells
     DevBuf<unsigned long long> d_kept;
 
@@ -64,13 +64,14 @@ struct tffr_plan_s {
     int layout = 0;
     int64_t n_kept = -1;
     DevBuf<float> D;                       // per-sample weights when materialised
-    DevBuf<int> tiles;
+    DevBuf<unsigned long long> tiles;      // look-back status of the pulse-row scan
 
     // pulse rows
     int P = 0;
     int64_t R_cells = 0;
     int max_len = 0;
-    DevBuf<int> row_start, row_clo, row_len, row_ly, bucket_start;
+    int row_cap = 0;                       // capacity of the per-row arrays
+    DevBuf<int> row_start, row_clo, row_len, row_ly, row_min, row_max, bucket_start;
     DevBuf<float> row_fy;
     DevBuf<double> row_lam_y;
     DevBuf<int64_t> row_off;
@@ -427,68 +428,86 @@ GeneralView general_view(const tffr_plan_s* p) {
     return v;
 }
 
-// Number of runs of bit-equal lam_y (pulse rows); checks lam_y.
-int count_runs(tffr_plan_s* p, int* P_out) {
-    const int64_t N = p->N;
-    const int64_t ntiles = (N + kScanTile - 1) / kScanTile;
-    CK(grow(p, p->tiles, ntiles));
-    k_count_runs<<<(unsigned)ntiles, kScanThreads, 0, p->stream>>>(N, p->lam_y, p->tiles.ptr, p->d_small.ptr);
-    CK_LAUNCH("k_count_runs");
-    k_scan_tile_counts<<<1, kScanThreads, 0, p->stream>>>((int)ntiles, p->tiles.ptr, p->d_small.ptr + 1);
-    CK_LAUNCH("k_scan_tile_counts");
-    int h[2] = {0, 0};
-    CK(cudaMemcpyAsync(h, p->d_small.ptr, 2 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
-    if (h[0]) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_y or |lam_y| >= 2^28");
-    *P_out = h[1];
+// Per-row arrays for up to cap pulse rows; the extent arrays start at their
+// identities (the scan folds cells in with atomic min / max).
+int reserve_rows(tffr_plan_s* p, int cap) {
+    if (cap <= p->row_cap) return TFFR_OK;
+    const int w = p->w;
+    p->row_cap = 0;
+    CK(grow(p, p->row_start, cap));
+    CK(grow(p, p->row_min, cap));
+    CK(grow(p, p->row_max, cap));
+    CK(grow(p, p->row_clo, cap));
+    CK(grow(p, p->row_len, cap));
+    CK(grow(p, p->row_ly, cap));
+    CK(grow(p, p->row_fy, cap));
+    CK(grow(p, p->row_lam_y, cap));
+    CK(grow(p, p->row_off, cap));
+    CK(grow(p, p->tap_list, (int64_t)cap * w));
+    k_fill_int<<<grid_for(cap, 256), 256, 0, p->stream>>>(cap, 0x7fffffff, p->row_min.ptr);
+    CK_LAUNCH("k_fill_int");
+    k_fill_int<<<grid_for(cap, 256), 256, 0, p->stream>>>(cap, -0x7fffffff - 1, p->row_max.ptr);
+    CK_LAUNCH("k_fill_int");
+    p->row_cap = cap;
     return TFFR_OK;
 }
 
-int build_rows(tffr_plan_s* p, int P) {
+// Pulse rows (runs of bit-equal lam_y) with their buffers and azimuth tap
+// lists, and one read-back (error bits, runs, longest row, total cells).  On
+// return *P_out holds the number of runs; the row structures are complete
+// only when the function returns OK and *P_out <= p->row_cap.
+int scan_rows(tffr_plan_s* p, int* P_out) {
     const int64_t N = p->N;
-    const int64_t ntiles = (N + kScanTile - 1) / kScanTile;
-    const int ny = p->ny, w = p->w;
-    const int prow = std::min(std::max(1, (P + 255) / 256), 152 * 8);
-    p->P = P;
-    CK(grow(p, p->row_start, P));
-    CK(grow(p, p->row_clo, P));
-    CK(grow(p, p->row_len, P));
-    CK(grow(p, p->row_ly, P));
-    CK(grow(p, p->row_fy, P));
-    CK(grow(p, p->row_lam_y, P));
-    CK(grow(p, p->row_off, P));
+    const int64_t ntiles = (N + kRowScanTile - 1) / kRowScanTile;
+    const int ny = p->ny, w = p->w, cap = p->row_cap;
+    const int prow = std::min(std::max(1, (cap + 255) / 256), 152 * 8);
+    CK(grow(p, p->tiles, ntiles));
     CK(grow(p, p->tap_start, ny + 1));
     CK(grow(p, p->cursor, ny + 1));
-    CK(grow(p, p->tap_list, (int64_t)P * w));
     CK(grow(p, p->d_big, 1));
-    k_emit_run_starts<<<(unsigned)ntiles, kScanThreads, 0, p->stream>>>(N, p->lam_y, p->tiles.ptr,
-                                                                         p->row_start.ptr);
-    CK_LAUNCH("k_emit_run_starts");
-    k_row_info<<<std::min(P, 152 * 16), 256, 0, p->stream>>>(P, N, p->nx, w, p->row_start.ptr, p->lam_x,
-                                                               p->lam_y, p->row_clo.ptr, p->row_len.ptr,
-                                                               p->row_ly.ptr, p->row_fy.ptr, p->row_lam_y.ptr,
-                                                               p->d_small.ptr);
-    CK_LAUNCH("k_row_info");
-    k_row_offsets<<<1, kScanThreads, 0, p->stream>>>(P, p->row_len.ptr, p->row_off.ptr, p->d_big.ptr,
+    CK(cudaMemsetAsync(p->tiles.ptr, 0, (size_t)ntiles * sizeof(unsigned long long), p->stream));
+    CK(cudaMemsetAsync(p->d_small.ptr, 0, 5 * sizeof(int), p->stream));
+    RowScanArgs a;
+    a.row_start = p->row_start.ptr;
+    a.row_min = p->row_min.ptr;
+    a.row_max = p->row_max.ptr;
+    a.cap = cap;
+    a.status = p->tiles.ptr;
+    a.flags = p->d_small.ptr;
+    k_scan_rows<<<(unsigned)ntiles, kRowScanWarps * 32, 0, p->stream>>>(N, p->lam_x, p->lam_y, a);
+    CK_LAUNCH("k_scan_rows");
+    const int* runs = p->d_small.ptr + 1;
+    k_row_finish<<<prow, 256, 0, p->stream>>>(runs, cap, p->nx, w, p->lam_y, p->row_start.ptr, p->row_min.ptr,
+                                              p->row_max.ptr, p->row_clo.ptr, p->row_len.ptr, p->row_ly.ptr,
+                                              p->row_fy.ptr, p->row_lam_y.ptr);
+    CK_LAUNCH("k_row_finish");
+    k_row_offsets<<<1, kScanThreads, 0, p->stream>>>(runs, cap, p->row_len.ptr, p->row_off.ptr, p->d_big.ptr,
                                                       p->d_small.ptr + 2);
     CK_LAUNCH("k_row_offsets");
     CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
-    k_tap_count<<<prow, 256, 0, p->stream>>>(P, ny, w, p->row_ly.ptr, p->cursor.ptr);
+    k_tap_count<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->cursor.ptr);
     CK_LAUNCH("k_tap_count");
     k_scan_counts<<<1, kScanThreads, 0, p->stream>>>(ny, p->cursor.ptr, p->tap_start.ptr);
     CK_LAUNCH("k_scan_counts");
     CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
-    k_tap_fill<<<prow, 256, 0, p->stream>>>(P, ny, w, p->taps, p->row_ly.ptr, p->row_fy.ptr, p->row_clo.ptr,
-                                            p->row_len.ptr, p->row_off.ptr, p->tap_start.ptr, p->cursor.ptr,
-                                            p->tap_list.ptr);
+    k_tap_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->taps, p->row_ly.ptr, p->row_fy.ptr,
+                                            p->row_clo.ptr, p->row_len.ptr, p->row_off.ptr, p->tap_start.ptr,
+                                            p->cursor.ptr, p->tap_list.ptr);
     CK_LAUNCH("k_tap_fill");
-    // one read-back: error flag, longest row, total cells
-    int hs[3] = {0, 0, 0};
+    int hs[4] = {0, 0, 0, 0};
     long long tot = 0;
-    CK(cudaMemcpyAsync(hs, p->d_small.ptr, 3 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(hs, p->d_small.ptr, 4 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaMemcpyAsync(&tot, p->d_big.ptr, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
-    if (hs[0]) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_x or |lam_x| >= 2^28");
+    if (hs[0] & 1) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_y or |lam_y| >= 2^28");
+    if (hs[0] & 2) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_x or |lam_x| >= 2^28");
+    if (hs[0] & 4) {
+        p->row_cap = 0;                                // extent arrays may be left dirty: refill next time
+        return fail(p, TFFR_ERR_TIMEOUT, "pulse-row scan: look-back wait gave up");
+    }
+    *P_out = hs[1];
+    if (hs[1] > cap || hs[3]) return TFFR_OK;          // caller grows the row arrays and scans again
+    p->P = hs[1];
     p->max_len = hs[2];
     p->R_cells = tot;
     CK(grow(p, p->R, tot));
@@ -791,7 +810,8 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
     if (s == TFFR_OK) s = upload_tables(p);
     if (s == TFFR_OK) {
         cudaError_t e = grow(p, p->T, (int64_t)Mx * p->ny);
-        if (e == cudaSuccess) e = grow(p, p->d_small, 4);
+        if (e == cudaSuccess) e = grow(p, p->d_small, 8);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_small.ptr, 0, 8 * sizeof(int), p->stream);
         if (e == cudaSuccess) e = grow(p, p->d_kept, 1);
         if (e != cudaSuccess) s = cuda_fail(p, e, "tffr_plan: allocation");
     }
@@ -810,6 +830,7 @@ int tffr_destroy(tffr_plan_t p) {
     release(p->T); release(p->deap_x); release(p->deap_y);
     release(p->d_small); release(p->d_kept); release(p->d_big); release(p->D); release(p->tiles);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly);
+    release(p->row_min); release(p->row_max);
     release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);
     release(p->tap_start); release(p->tap_list);
     release(p->lx); release(p->ly); release(p->perm); release(p->slx); release(p->cursor);
@@ -884,18 +905,28 @@ int tffr_set_points(tffr_plan_t p, int64_t N, const double* lam_x, const double*
         return TFFR_OK;
     }
     STAGE_BEGIN(TFFR_STAGE_POINTS);
-    CK(cudaMemsetAsync(p->d_small.ptr, 0, 4 * sizeof(int), p->stream));
     int layout = p->layout_hint;
-    int P = 0;
     int s = TFFR_OK;
     if (layout != TFFR_POINTS_GENERAL) {
-        s = count_runs(p, &P);
+        // pulse rows are tried first; a second scan runs only when the row
+        // arrays were too small for this set of points
+        s = reserve_rows(p, std::max(p->row_cap, (int)std::min<int64_t>(N, 4096)));
+        int P = 0;
+        if (s == TFFR_OK) s = scan_rows(p, &P);
         if (s != TFFR_OK) return s;
         if (layout == TFFR_POINTS_AUTO) layout = (N >= 8 * (int64_t)P) ? TFFR_POINTS_ROWS : TFFR_POINTS_GENERAL;
+        if (layout == TFFR_POINTS_ROWS && P > p->row_cap) {
+            s = reserve_rows(p, P);
+            if (s == TFFR_OK) s = scan_rows(p, &P);
+            if (s != TFFR_OK) return s;
+            if (P > p->row_cap) return fail(p, TFFR_ERR_INVALID_ARG, "pulse rows changed between two scans");
+        }
     }
     p->layout = layout;
-    s = (layout == TFFR_POINTS_ROWS) ? build_rows(p, P) : build_general(p);
-    if (s != TFFR_OK) return s;
+    if (layout == TFFR_POINTS_GENERAL) {
+        s = build_general(p);
+        if (s != TFFR_OK) return s;
+    }
     STAGE_END(TFFR_STAGE_POINTS);
     p->have_points = true;
     return TFFR_OK;

@@ -318,3 +318,47 @@ def test_repeated_set_points_and_weights_calls():
                     Dref = oracle.tffr_weights(x, 64, **kw)
                     ref = oracle.adjoint_image(x, y, vv.astype(np.complex64), Dref, 64, 64)
                     assert rel_l2(img, ref) <= TOL, (rnd, kw)
+
+
+def expected_rows(lx, ly, nx, w):
+    """Runs of bit-equal lam_y and the summed / longest row-buffer lengths (fine cells floor(2 lam))."""
+    bits = ly.view(np.int64)
+    starts = np.flatnonzero(np.concatenate([[True], bits[1:] != bits[:-1]]))
+    ends = np.append(starts[1:], lx.shape[0])
+    cells = np.floor(2.0 * lx).astype(np.int64)
+    lens = [min(int(cells[s:e].max() - cells[s:e].min()) + w, nx) for s, e in zip(starts, ends)]
+    return len(starts), int(np.sum(lens)), int(np.max(lens))
+
+
+@pytest.mark.parametrize("case", ["long_rows_across_tiles", "more_rows_than_first_capacity", "repeated_lam_y"])
+def test_pulse_row_scan(case):
+    """Pulse rows found by the one-pass scan: rows longer than a scan tile (4096 samples),
+    more rows than the plan's first row capacity (4096, so the scan runs twice), a lam_y
+    value that comes back after another row (two separate rows), single-sample rows."""
+    M, w = 64, 8
+    g = np.random.default_rng({"long_rows_across_tiles": 21, "more_rows_than_first_capacity": 22,
+                               "repeated_lam_y": 23}[case])
+    if case == "long_rows_across_tiles":
+        lens = [1, 5000, 9000, 2, 4095, 4097, 1, 300]
+    elif case == "more_rows_than_first_capacity":
+        lens = list(g.integers(1, 12, 5000))
+    else:
+        lens = [700, 1, 900, 5, 4200, 33]
+    ly_rows = g.uniform(-0.45 * M, 0.45 * M, len(lens))
+    if case == "repeated_lam_y":
+        ly_rows[2] = ly_rows[0]
+        ly_rows[4] = ly_rows[0]
+    ly = np.repeat(ly_rows, lens)
+    lx = np.empty(ly.shape[0])
+    pos = 0
+    for n in lens:                              # each row covers a random stretch of x
+        c = g.uniform(-0.4 * M, 0.4 * M)
+        lx[pos:pos + n] = np.clip(c + g.uniform(-6.0, 6.0, n), -M / 2, M / 2 - 1e-9)
+        pos += n
+    v = (g.standard_normal(lx.shape[0]) + 1j * g.standard_normal(lx.shape[0])).astype(np.complex64)
+    img, D, kept, info = gpu_adjoint(lx, ly, v, M, layout="rows", width=w)
+    P, cells, longest = expected_rows(lx, ly, 2 * M, w)
+    assert info["layout"] == 2
+    assert (info["n_rows"], info["row_cells"], info["max_row_cells"]) == (P, cells, longest)
+    ref = oracle.adjoint_image(lx, ly, v, oracle.tffr_weights(lx, M), M, M)
+    assert rel_l2(img, ref) <= TOL
