@@ -139,9 +139,12 @@ __device__ __forceinline__ float weight_tffr(double lam_x, int cx, float fx, dou
 
 // ---------------------------------------------------------------------------
 // Pulse rows: runs of samples with bit-equal lam_y (azimuth is uniform,
-// Sec. II.A).  One pass over both coordinate arrays finds the run starts
-// (order-preserving compaction with a decoupled look-back across tiles),
+// Sec. II.A).  One pass over both coordinate arrays finds the run starts,
 // checks every coordinate and takes each run's extent of fine x cells.
+// Tiles number their runs from one atomic counter (row ids follow sample
+// order inside a tile, not across tiles: nothing downstream needs more), so
+// no tile waits on another; a single-block pass then hands each tile's
+// leading samples to the row they continue and closes each tile's last row.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;                     // single-block scans below
 
@@ -173,53 +176,36 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int* tot
 }
 
 constexpr int kRowScanWarps = 8;
-constexpr int kRowScanK = 16;                          // samples per lane
+constexpr int kRowScanK = 8;                           // samples per lane
 constexpr int kRowScanTile = kRowScanWarps * 32 * kRowScanK;
-constexpr unsigned kLookbackSpins = 1u << 22;          // bound on the look-back wait (~0.3 s)
-
-// status word of one tile: flag in bits 62-63 (1: tile count, 2: inclusive
-// prefix), the count in the low 32 bits; zero means not yet published
-__device__ __forceinline__ void lb_publish(unsigned long long* a, unsigned flag, int v) {
-    const unsigned long long w = ((unsigned long long)flag << 62) | (unsigned)v;
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(a), "l"(w) : "memory");
-}
-__device__ __forceinline__ unsigned long long lb_read(const unsigned long long* a) {
-    unsigned long long w;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(a) : "memory");
-    return w;
-}
+constexpr int kIntMax = 0x7fffffff, kIntMin = -0x7fffffff - 1;
 
 struct RowScanArgs {
-    int* row_start;                                    // [cap] first sample of each run
-    int* row_min;                                      // [cap] smallest fine x cell, INT_MAX at entry
-    int* row_max;                                      // [cap] largest fine x cell, INT_MIN at entry
+    int* row_start;                                    // [cap] first sample of each row
+    int* row_end;                                      // [cap] one past its last sample
+    int* row_min;                                      // [cap] smallest fine x cell, kIntMax at entry
+    int* row_max;                                      // [cap] largest fine x cell, kIntMin at entry
     int cap;
-    unsigned long long* status;                        // [tiles] zeroed
-    int* flags;                                        // [0] error bits, [1] runs, [3] overflow, [4] tile ticket
+    int4* tile;                                        // [tiles] first row id (-1: none), last row id, first row start
+    int2* head;                                        // [tiles] cell extent of the samples before the first start
+    int* flags;                                        // [0] error bits, [1] rows, [3] overflow
 };
 
-__device__ __forceinline__ void row_extent_flush(const RowScanArgs& a, int id, int mn, int mx) {
-    if (id < a.cap) {
-        atomicMin(&a.row_min[id], mn);
-        atomicMax(&a.row_max[id], mx);
-    } else {
-        atomicOr(&a.flags[3], 1);
-    }
-}
-
-// Error bits: 1 bad lam_y, 2 bad lam_x, 4 look-back wait gave up.  Tiles are
-// taken in launch order from a ticket, so every tile waits only on tiles that
-// already run; the wait is bounded all the same.
-__global__ void __launch_bounds__(kRowScanWarps * 32)
+// Error bits: 1 bad lam_y, 2 bad lam_x.  Local run index -1 marks the samples
+// of a tile that continue a row started in an earlier tile.
+__global__ void __launch_bounds__(kRowScanWarps * 32, 4)
 k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y, RowScanArgs a) {
-    __shared__ int s_tile, s_off;
     __shared__ int s_cnt[kRowScanWarps];
+    __shared__ int s_base, s_first, s_hmin, s_hmax;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&a.flags[4], 1);
-    __syncthreads();
-    const int tile = s_tile;
+    const int tile = blockIdx.x;
     const int64_t wbase = (int64_t)tile * kRowScanTile + (int64_t)wid * (32 * kRowScanK);
+    if (threadIdx.x == 0) {
+        s_first = -1;
+        s_hmin = kIntMax;
+        s_hmax = kIntMin;
+    }
     unsigned ball[kRowScanK];
     int cx[kRowScanK];
     bool bad_x = false, bad_y = false;
@@ -264,65 +250,45 @@ k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restric
         woff += (i < wid) ? t : 0;
         agg += t;
     }
-    // decoupled look-back, one warp: 32 predecessors per step, back to the
-    // nearest tile that published its inclusive prefix
-    if (wid == 0) {
-        int excl = 0;
-        if (tile == 0) {
-            if (lane == 0) lb_publish(&a.status[0], 2, agg);
-        } else {
-            if (lane == 0) lb_publish(&a.status[tile], 1, agg);
-            int top = tile - 1;
-            unsigned spins = 0;
-            while (true) {
-                const int j = top - lane;
-                const unsigned long long w = (j >= 0) ? lb_read(&a.status[j]) : (2ull << 62);
-                const unsigned fl = (unsigned)(w >> 62);
-                const unsigned incl = __ballot_sync(FULL, fl == 2), pending = __ballot_sync(FULL, fl == 0);
-                const int first_incl = incl ? __ffs(incl) - 1 : 32;
-                const int first_pending = pending ? __ffs(pending) - 1 : 32;
-                if (first_pending < first_incl) {              // a tile before the nearest prefix is not ready
-                    if (++spins > kLookbackSpins) {
-                        if (lane == 0) atomicOr(&a.flags[0], 4);
-                        break;
-                    }
-                    __nanosleep(32);
-                    continue;
-                }
-                const int last = incl ? first_incl : 31;       // nearest inclusive lane
-                int v = (lane <= last) ? (int)(unsigned)w : 0;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-                excl += v;
-                if (incl) break;
-                top -= 32;
-            }
-            if (lane == 0) lb_publish(&a.status[tile], 2, excl + agg);
-        }
-        if (lane == 0) {
-            s_off = excl;
-            if (tile == (int)gridDim.x - 1) a.flags[1] = excl + agg;
-        }
-    }
+    if (threadIdx.x == 0) s_base = agg ? atomicAdd(&a.flags[1], agg) : 0;
     __syncthreads();
-    // emit run starts in sample order and fold each lane's cells into the
-    // extent of its run (runs are contiguous, so a lane's run ids only grow)
+    const int base = s_base;
+    // emit the starts, close the rows that end inside the tile, and fold each
+    // lane's cells into the extent of its row (a lane's run index only grows)
     const unsigned le = FULL >> (31 - lane);
-    int pre = s_off + woff;
-    int cur = -1, mn = 0x7fffffff, mx = -0x7fffffff - 1;
+    constexpr int kNone = -2;
+    int pre = woff;
+    int cur = kNone, mn = kIntMax, mx = kIntMin;
     bool over = false;
+    auto flush = [&](int local, int lo, int hi) {
+        if (local < 0) {
+            atomicMin(&s_hmin, lo);
+            atomicMax(&s_hmax, hi);
+        } else if (base + local < a.cap) {
+            atomicMin(&a.row_min[base + local], lo);
+            atomicMax(&a.row_max[base + local], hi);
+        } else {
+            over = true;
+        }
+    };
 #pragma unroll
     for (int k = 0; k < kRowScanK; ++k) {
         const int64_t n = wbase + k * 32 + lane;
-        const int id = pre + __popc(ball[k] & le) - 1;
+        const int local = pre + __popc(ball[k] & le) - 1;
         if (n < N) {
             if ((ball[k] >> lane) & 1u) {
-                if (id < a.cap) a.row_start[id] = (int)n;
+                const int p = base + local;
+                if (p < a.cap) a.row_start[p] = (int)n;
                 else over = true;
+                if (local > 0) {
+                    if (p - 1 < a.cap) a.row_end[p - 1] = (int)n;
+                } else {
+                    s_first = (int)n;
+                }
             }
-            if (id != cur) {
-                if (cur >= 0) row_extent_flush(a, cur, mn, mx);
-                cur = id;
+            if (local != cur) {
+                if (cur != kNone) flush(cur, mn, mx);
+                cur = local;
                 mn = mx = cx[k];
             } else {
                 mn = min(mn, cx[k]);
@@ -331,12 +297,108 @@ k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restric
         }
         pre += __popc(ball[k]);
     }
-    if (over) atomicOr(&a.flags[3], 1);
     if (__all_sync(FULL, cur == __shfl_sync(FULL, cur, 0))) {
         const int m0 = __reduce_min_sync(FULL, mn), m1 = __reduce_max_sync(FULL, mx);
-        if (lane == 0 && cur >= 0) row_extent_flush(a, cur, m0, m1);
-    } else if (cur >= 0) {
-        row_extent_flush(a, cur, mn, mx);
+        if (lane == 0 && cur != kNone) flush(cur, m0, m1);
+    } else if (cur != kNone) {
+        flush(cur, mn, mx);
+    }
+    if (over) atomicOr(&a.flags[3], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a.tile[tile] = make_int4(agg ? base : -1, base + agg - 1, s_first, 0);
+        a.head[tile] = make_int2(s_hmin, s_hmax);
+    }
+}
+
+// Single block: the leading samples of tile t belong to the last row of the
+// nearest earlier tile that starts a row; the last row of tile t ends at the
+// first start of the nearest later tile that has one (or at N).
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_fixup(int ntiles, int64_t N, RowScanArgs a) {
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    // forward: latest row id (non-negative) strictly before each tile
+    if (threadIdx.x == 0) s_carry = -1;
+    __syncthreads();
+    for (int c0 = 0; c0 < ntiles; c0 += blockDim.x) {
+        const int t = c0 + threadIdx.x;
+        const int4 ti = (t < ntiles) ? a.tile[t] : make_int4(-1, -1, -1, 0);
+        int v = (ti.x >= 0) ? ti.y : -1;               // inclusive "latest row id" scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o && v < 0) v = u;
+        }
+        if (lane == 31) s_warp[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int w = (lane < nwarps) ? s_warp[lane] : -1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o && w < 0) w = u;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int carry = s_carry;
+        int before = __shfl_up_sync(0xffffffffu, v, 1);    // exclusive within the warp
+        if (lane == 0) before = -1;
+        if (before < 0 && wid > 0) before = s_warp[wid - 1];
+        if (before < 0) before = carry;
+        if (t < ntiles) {
+            const int2 h = a.head[t];
+            if (h.x != kIntMax && before >= 0 && before < a.cap) {
+                atomicMin(&a.row_min[before], h.x);
+                atomicMax(&a.row_max[before], h.y);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int last = s_warp[nwarps - 1];
+            if (last >= 0) s_carry = last;
+        }
+        __syncthreads();
+    }
+    // backward: first row start strictly after each tile
+    if (threadIdx.x == 0) s_carry = (int)N;
+    __syncthreads();
+    for (int c1 = ntiles; c1 > 0; c1 -= blockDim.x) {
+        const int t = c1 - 1 - threadIdx.x;            // thread order runs backwards over tiles
+        const int4 ti = (t >= 0) ? a.tile[t] : make_int4(-1, -1, -1, 0);
+        int v = (ti.x >= 0) ? ti.z : -1;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o && v < 0) v = u;
+        }
+        if (lane == 31) s_warp[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int w = (lane < nwarps) ? s_warp[lane] : -1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o && w < 0) w = u;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int carry = s_carry;
+        int after = __shfl_up_sync(0xffffffffu, v, 1);
+        if (lane == 0) after = -1;
+        if (after < 0 && wid > 0) after = s_warp[wid - 1];
+        if (after < 0) after = carry;
+        if (t >= 0 && ti.x >= 0 && ti.y < a.cap) a.row_end[ti.y] = after;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int last = s_warp[nwarps - 1];
+            if (last >= 0) s_carry = last;
+        }
+        __syncthreads();
     }
 }
 

@@ -41,7 +41,7 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
     const int clo = rv.row_clo[p];
     const bool periodic = (len == nx) && (clo == 0);
     const int64_t s0 = rv.row_start[p];
-    const int64_t s1 = (p + 1 < rv.P) ? rv.row_start[p + 1] : N;
+    const int64_t s1 = rv.row_end[p];
     const int L = (int)(s1 - s0);
     const int tid = threadIdx.x;
     for (int i = tid; i < len; i += kSpreadThreads) s_row[i] = make_float2(0.f, 0.f);
@@ -151,7 +151,7 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
     const int clo = rv.row_clo[p];
     const bool periodic = (len == nx) && (clo == 0);
     const int64_t s0 = rv.row_start[p];
-    const int64_t s1 = (p + 1 < rv.P) ? rv.row_start[p + 1] : N;
+    const int64_t s1 = rv.row_end[p];
     const float2* Rp = R + rv.row_off[p];
     float gy = 1.0f;
     bool gy_exact = false;

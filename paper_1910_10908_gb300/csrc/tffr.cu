@@ -52,7 +52,8 @@ struct tffr_plan_s {
     // plan-time tables and the intermediate of the FFT passes
     DevBuf<float2> twh_x, twl_x, twh_y, twl_y, tt_x, tt_y, T;
     DevBuf<float> deap_x, deap_y;
-    DevBuf<int> d_small;                   // [0] error bits, [1] runs, [2] longest row, [3] overflow, [4] ticket
+    DevBuf<int> d_small;                   // [0] error bits, [1] rows, [2] longest row, [3] row overflow
+    int* h_small = nullptr;                // pinned read-back: d_small[0..3], then the total cells (int64)
     DevBuf<long long> d_big;               // [0] total row-buffer cells
     DevBuf<unsigned long long> d_kept;
 
@@ -64,14 +65,15 @@ struct tffr_plan_s {
     int layout = 0;
     int64_t n_kept = -1;
     DevBuf<float> D;                       // per-sample weights when materialised
-    DevBuf<unsigned long long> tiles;      // look-back status of the pulse-row scan
+    DevBuf<int4> tile_info;                // pulse-row scan: per tile first / last row id, first start
+    DevBuf<int2> tile_head;                // pulse-row scan: cell extent of each tile's leading samples
 
     // pulse rows
     int P = 0;
     int64_t R_cells = 0;
     int max_len = 0;
     int row_cap = 0;                       // capacity of the per-row arrays
-    DevBuf<int> row_start, row_clo, row_len, row_ly, row_min, row_max, bucket_start;
+    DevBuf<int> row_start, row_end, row_clo, row_len, row_ly, row_min, row_max, bucket_start;
     DevBuf<float> row_fy;
     DevBuf<double> row_lam_y;
     DevBuf<int64_t> row_off;
@@ -406,6 +408,7 @@ RowsView rows_view(const tffr_plan_s* p) {
     RowsView v;
     v.P = p->P;
     v.row_start = p->row_start.ptr;
+    v.row_end = p->row_end.ptr;
     v.row_clo = p->row_clo.ptr;
     v.row_len = p->row_len.ptr;
     v.row_ly = p->row_ly.ptr;
@@ -435,6 +438,7 @@ int reserve_rows(tffr_plan_s* p, int cap) {
     const int w = p->w;
     p->row_cap = 0;
     CK(grow(p, p->row_start, cap));
+    CK(grow(p, p->row_end, cap));
     CK(grow(p, p->row_min, cap));
     CK(grow(p, p->row_max, cap));
     CK(grow(p, p->row_clo, cap));
@@ -444,9 +448,9 @@ int reserve_rows(tffr_plan_s* p, int cap) {
     CK(grow(p, p->row_lam_y, cap));
     CK(grow(p, p->row_off, cap));
     CK(grow(p, p->tap_list, (int64_t)cap * w));
-    k_fill_int<<<grid_for(cap, 256), 256, 0, p->stream>>>(cap, 0x7fffffff, p->row_min.ptr);
+    k_fill_int<<<grid_for(cap, 256), 256, 0, p->stream>>>(cap, kIntMax, p->row_min.ptr);
     CK_LAUNCH("k_fill_int");
-    k_fill_int<<<grid_for(cap, 256), 256, 0, p->stream>>>(cap, -0x7fffffff - 1, p->row_max.ptr);
+    k_fill_int<<<grid_for(cap, 256), 256, 0, p->stream>>>(cap, kIntMin, p->row_max.ptr);
     CK_LAUNCH("k_fill_int");
     p->row_cap = cap;
     return TFFR_OK;
@@ -461,21 +465,25 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     const int64_t ntiles = (N + kRowScanTile - 1) / kRowScanTile;
     const int ny = p->ny, w = p->w, cap = p->row_cap;
     const int prow = std::min(std::max(1, (cap + 255) / 256), 152 * 8);
-    CK(grow(p, p->tiles, ntiles));
+    CK(grow(p, p->tile_info, ntiles));
+    CK(grow(p, p->tile_head, ntiles));
     CK(grow(p, p->tap_start, ny + 1));
     CK(grow(p, p->cursor, ny + 1));
     CK(grow(p, p->d_big, 1));
-    CK(cudaMemsetAsync(p->tiles.ptr, 0, (size_t)ntiles * sizeof(unsigned long long), p->stream));
-    CK(cudaMemsetAsync(p->d_small.ptr, 0, 5 * sizeof(int), p->stream));
+    CK(cudaMemsetAsync(p->d_small.ptr, 0, 4 * sizeof(int), p->stream));
     RowScanArgs a;
     a.row_start = p->row_start.ptr;
+    a.row_end = p->row_end.ptr;
     a.row_min = p->row_min.ptr;
     a.row_max = p->row_max.ptr;
     a.cap = cap;
-    a.status = p->tiles.ptr;
+    a.tile = p->tile_info.ptr;
+    a.head = p->tile_head.ptr;
     a.flags = p->d_small.ptr;
     k_scan_rows<<<(unsigned)ntiles, kRowScanWarps * 32, 0, p->stream>>>(N, p->lam_x, p->lam_y, a);
     CK_LAUNCH("k_scan_rows");
+    k_scan_fixup<<<1, kScanThreads, 0, p->stream>>>((int)ntiles, N, a);
+    CK_LAUNCH("k_scan_fixup");
     const int* runs = p->d_small.ptr + 1;
     k_row_finish<<<prow, 256, 0, p->stream>>>(runs, cap, p->nx, w, p->lam_y, p->row_start.ptr, p->row_min.ptr,
                                               p->row_max.ptr, p->row_clo.ptr, p->row_len.ptr, p->row_ly.ptr,
@@ -494,17 +502,15 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
                                             p->row_clo.ptr, p->row_len.ptr, p->row_off.ptr, p->tap_start.ptr,
                                             p->cursor.ptr, p->tap_list.ptr);
     CK_LAUNCH("k_tap_fill");
-    int hs[4] = {0, 0, 0, 0};
-    long long tot = 0;
-    CK(cudaMemcpyAsync(hs, p->d_small.ptr, 4 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaMemcpyAsync(&tot, p->d_big.ptr, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 4 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(p->h_small + 4, p->d_big.ptr, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
+    int hs[4];
+    long long tot;
+    std::memcpy(hs, p->h_small, sizeof(hs));
+    std::memcpy(&tot, p->h_small + 4, sizeof(tot));
     if (hs[0] & 1) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_y or |lam_y| >= 2^28");
     if (hs[0] & 2) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_x or |lam_x| >= 2^28");
-    if (hs[0] & 4) {
-        p->row_cap = 0;                                // extent arrays may be left dirty: refill next time
-        return fail(p, TFFR_ERR_TIMEOUT, "pulse-row scan: look-back wait gave up");
-    }
     *P_out = hs[1];
     if (hs[1] > cap || hs[3]) return TFFR_OK;          // caller grows the row arrays and scans again
     p->P = hs[1];
@@ -812,6 +818,7 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
         cudaError_t e = grow(p, p->T, (int64_t)Mx * p->ny);
         if (e == cudaSuccess) e = grow(p, p->d_small, 8);
         if (e == cudaSuccess) e = cudaMemsetAsync(p->d_small.ptr, 0, 8 * sizeof(int), p->stream);
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_small, 8 * sizeof(int));
         if (e == cudaSuccess) e = grow(p, p->d_kept, 1);
         if (e != cudaSuccess) s = cuda_fail(p, e, "tffr_plan: allocation");
     }
@@ -828,9 +835,11 @@ int tffr_destroy(tffr_plan_t p) {
     cudaStreamSynchronize(p->stream);
     release(p->twh_x); release(p->twl_x); release(p->twh_y); release(p->twl_y); release(p->tt_x); release(p->tt_y);
     release(p->T); release(p->deap_x); release(p->deap_y);
-    release(p->d_small); release(p->d_kept); release(p->d_big); release(p->D); release(p->tiles);
+    release(p->d_small); release(p->d_kept); release(p->d_big); release(p->D);
+    release(p->tile_info); release(p->tile_head);
+    if (p->h_small) cudaFreeHost(p->h_small);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly);
-    release(p->row_min); release(p->row_max);
+    release(p->row_min); release(p->row_max); release(p->row_end);
     release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);
     release(p->tap_start); release(p->tap_list);
     release(p->lx); release(p->ly); release(p->perm); release(p->slx); release(p->cursor);

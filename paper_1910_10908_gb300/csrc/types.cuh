@@ -19,6 +19,7 @@ struct TapEntry {
 struct RowsView {
     int P;                          // pulse rows
     const int* row_start;           // [P] first sample of the row (rows are contiguous runs)
+    const int* row_end;             // [P] one past its last sample
     const int* row_clo;             // [P] first fine x cell of the row buffer
     const int* row_len;             // [P] cells in the row buffer (nx: periodic row)
     const int* row_ly;              // [P] fine y cell floor(2 lam_y)
