@@ -58,6 +58,29 @@ __device__ __forceinline__ bool fine_coord(double v, int& cell, float& frac) {
     return g.ok;
 }
 
+// floor(2v) alone (same rules as fine_coord, no offset).
+__device__ __forceinline__ bool fine_cell(double v, int& cell) {
+    const int hi = __double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const int sh = 1074 - ((hi >> 20) & 0x7ff);
+    if (sh >= 32 && sh <= 52) {
+        const unsigned mh = ((unsigned)hi & 0xFFFFFu) | 0x100000u;
+        const int s = sh - 32;
+        const unsigned I = mh >> s;
+        const bool whole = ((mh & ((1u << s) - 1u)) | lo) == 0u;
+        cell = (hi >= 0) ? (int)I : (whole ? -(int)I : -(int)I - 1);
+        return true;
+    }
+    const FineCoord g = fine_coord_general(v);
+    cell = g.cell;
+    return g.ok;
+}
+
+// |v| < 2^28 and finite: the range fine_coord accepts.
+__device__ __forceinline__ bool coord_in_range(double v) {
+    return ((__double2hiint(v) >> 20) & 0x7ff) <= 1050;
+}
+
 // Any magnitude (see fine_coord): 64-bit integer operations.
 static __device__ __noinline__ FineCoord fine_coord_general(double v) {
     int cell;

@@ -231,10 +231,9 @@ k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restric
             ball[h + k] = __ballot_sync(FULL, in && (n == 0 || yb[k] != up));
             cnt += __popc(ball[h + k]);
             int c = 0;
-            float f;
             if (in) {
-                bad_y |= !fine_coord(__longlong_as_double(yb[k]), c, f);
-                bad_x |= !fine_coord(xv[k], c, f);
+                bad_y |= !coord_in_range(__longlong_as_double(yb[k]));
+                bad_x |= !fine_cell(xv[k], c);
             }
             cx[h + k] = c;
         }

@@ -21,6 +21,15 @@ constexpr int kSpreadTile = kSpreadThreads * kSpreadPerThread;
 constexpr int kSpreadStageElems = kSpreadTile + kSpreadTile / 64 + 1;
 constexpr int kSpreadStageBytes = kSpreadStageElems * (int)(sizeof(double) + sizeof(float2));
 
+// Samples whose weight needs the FP64 decision (1/G within the guard band of
+// tau, a grid edge or a truncation breakpoint; rare) are not spread inline:
+// k_spread_rows lists them and k_spread_deferred adds them afterwards.  The
+// FP64 closed form then stays out of the hot kernel (and its registers).
+struct DeferList {
+    int* count;                     // zero before the spread
+    int2* item;                     // [N] (sample, pulse row)
+};
+
 // Adjoint, step 1: R_p[c] = sum_{n in row p} D_n v_n phi(c - u_n) over the W
 // taps of each sample.  Samples are staged tile by tile with coalesced loads;
 // each thread then walks a contiguous run of samples (which move slowly along
@@ -28,9 +37,9 @@ constexpr int kSpreadStageBytes = kSpreadStageElems * (int)(sizeof(double) + siz
 // a cell into the shared row (atomic add) only when the footprint moves past
 // it.  D_n is evaluated inline from lam_x (tFFR mode) or read (user mode).
 template <typename VT, int W>
-__global__ void __launch_bounds__(kSpreadThreads, 3)
+__global__ void __launch_bounds__(kSpreadThreads, 4)
 k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __restrict__ lam_x,
-              const void* __restrict__ values, WeightArgs wa, TapPoly tp, float2* __restrict__ R) {
+              const void* __restrict__ values, WeightArgs wa, TapPoly tp, DeferList defer, float2* __restrict__ R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* s_lam = reinterpret_cast<double*>(smem_raw);
     float2* s_val = reinterpret_cast<float2*>(s_lam + kSpreadStageElems);
@@ -49,7 +58,6 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
     // azimuth factor of the separable weight variant: one value per row
     float gy = 1.0f;
     bool gy_exact = false;
-    const double lam_y_row = rv.row_lam_y[p];
     if (wa.mode == 0 && wa.separable) gy = g_fitted(rv.row_ly[p], rv.row_fy[p], My, wa, gy_exact);
 
     // Thread (warp wid, lane) walks run number wid + 8 * lane of the tile: the
@@ -87,10 +95,11 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
                 bool exact = gy_exact;
                 float G = g_fitted(cell, f, Mx, wa, exact) * gy;
                 d = (G != 0.0f) ? __frcp_rn(G) : 0.0f;
-                if (exact || !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau)))
-                    d = weight_exact(lam, lam_y_row, Mx, My, wa);
-                else if (d < wa.tau)
-                    d = 0.0f;
+                if (exact || !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau))) {
+                    defer.item[atomicAdd(defer.count, 1)] = make_int2((int)(s0 + t0 + i), p);
+                    continue;
+                }
+                if (d < wa.tau) d = 0.0f;
             }
             if (d == 0.0f) continue;
             const float2 v = cscale(s_val[k], d);
@@ -138,6 +147,38 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
     __syncthreads();
     float2* out = R + rv.row_off[p];
     for (int i = tid; i < len; i += kSpreadThreads) out[i] = s_row[i];
+}
+
+// The deferred samples of k_spread_rows: D_n decided in FP64, then added into
+// their pulse-row buffers with global atomics (after k_spread_rows stored them).
+template <typename VT, int W>
+__global__ void __launch_bounds__(256)
+k_spread_deferred(RowsView rv, int nx, int Mx, int My, const double* __restrict__ lam_x,
+                  const void* __restrict__ values, WeightArgs wa, TapPoly tp, DeferList defer,
+                  float2* __restrict__ R) {
+    constexpr int H = W / 2;
+    const int count = *defer.count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const int2 e = defer.item[i];
+        const int n = e.x, p = e.y;
+        const double lam = lam_x[n];
+        int cell;
+        float f;
+        fine_coord(lam, cell, f);
+        const float d = weight_exact(lam, rv.row_lam_y[p], Mx, My, wa);
+        if (d == 0.0f) continue;
+        const float2 v = cscale(ValueIO<VT>::load(values, n), d);
+        float wt[W];
+        taps_all<W>(tp, f, wt);
+        const int len = rv.row_len[p], clo = rv.row_clo[p];
+        const bool periodic = (len == nx) && (clo == 0);
+        float2* out = R + rv.row_off[p];
+#pragma unroll
+        for (int s = 0; s < W; ++s) {
+            const int c = cell - (H - 1) + s;
+            atomicAdd(&out[periodic ? wrapmod(c, nx) : (c - clo)], cscale(v, wt[s]));
+        }
+    }
 }
 
 // Forward, last step: y_n = D_n sum_s phi(c_s - u_n) R_p[c_s] (or without D_n).

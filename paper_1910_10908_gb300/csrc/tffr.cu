@@ -52,7 +52,9 @@ struct tffr_plan_s {
     // plan-time tables and the intermediate of the FFT passes
     DevBuf<float2> twh_x, twl_x, twh_y, twl_y, tt_x, tt_y, T;
     DevBuf<float> deap_x, deap_y;
-    DevBuf<int> d_small;                   // [0] error bits, [1] rows, [2] longest row, [3] row overflow
+    DevBuf<int> d_small;                   // [0] error bits, [1] rows, [2] longest row, [3] row overflow,
+                                           // [5] samples deferred to the FP64 weight decision
+    DevBuf<int2> defer;                    // [N] deferred (sample, pulse row)
     int* h_small = nullptr;                // pinned read-back: d_small[0..3], then the total cells (int64)
     DevBuf<long long> d_big;               // [0] total row-buffer cells
     DevBuf<unsigned long long> d_kept;
@@ -569,8 +571,12 @@ FftTables tables_y(const tffr_plan_s* p) { return FftTables{p->twh_y.ptr, p->twl
 template <typename VT, int W>
 void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values) {
     const size_t smem = (size_t)kSpreadStageBytes + (size_t)p->max_len * sizeof(float2);
+    const DeferList defer{p->d_small.ptr + 5, p->defer.ptr};
     k_spread_rows<VT, W><<<p->P, kSpreadThreads, smem, p->stream>>>(rv, p->N, p->nx, p->Mx, p->My, p->lam_x, values,
-                                                                     p->wargs, p->taps, p->R.ptr);
+                                                                     p->wargs, p->taps, defer, p->R.ptr);
+    if (p->wargs.mode == TFFR_WEIGHTS_TFFR)
+        k_spread_deferred<VT, W><<<152 * 2, 256, 0, p->stream>>>(rv, p->nx, p->Mx, p->My, p->lam_x, values, p->wargs,
+                                                                  p->taps, defer, p->R.ptr);
 }
 
 template <typename VT>
@@ -579,6 +585,7 @@ int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
     if (p->layout == TFFR_POINTS_ROWS) {
         const RowsView rv = rows_view(p);
         STAGE_BEGIN(TFFR_STAGE_SPREAD);
+        if (p->wargs.mode == TFFR_WEIGHTS_TFFR) CK(cudaMemsetAsync(p->d_small.ptr + 5, 0, sizeof(int), p->stream));
         switch (p->w) {
             case 2: launch_spread<VT, 2>(p, rv, values); break;
             case 4: launch_spread<VT, 4>(p, rv, values); break;
@@ -836,7 +843,7 @@ int tffr_destroy(tffr_plan_t p) {
     release(p->twh_x); release(p->twl_x); release(p->twh_y); release(p->twl_y); release(p->tt_x); release(p->tt_y);
     release(p->T); release(p->deap_x); release(p->deap_y);
     release(p->d_small); release(p->d_kept); release(p->d_big); release(p->D);
-    release(p->tile_info); release(p->tile_head);
+    release(p->tile_info); release(p->tile_head); release(p->defer);
     if (p->h_small) cudaFreeHost(p->h_small);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly);
     release(p->row_min); release(p->row_max); release(p->row_end);
@@ -973,6 +980,7 @@ int tffr_weights(tffr_plan_t p, const tffr_weight_opts* opts, float* D_out, int6
         p->fit_valid = true;
     }
     copy_fit(A, p->fit_cache);
+    if (N > 0 && o.mode == TFFR_WEIGHTS_TFFR && p->layout == TFFR_POINTS_ROWS) CK(grow(p, p->defer, N));
     STAGE_BEGIN(TFFR_STAGE_WEIGHTS);
     if (N > 0 && o.mode == TFFR_WEIGHTS_USER) {
         CK(grow(p, p->D, N));

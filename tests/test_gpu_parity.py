@@ -362,3 +362,32 @@ def test_pulse_row_scan(case):
     assert (info["n_rows"], info["row_cells"], info["max_row_cells"]) == (P, cells, longest)
     ref = oracle.adjoint_image(lx, ly, v, oracle.tffr_weights(lx, M), M, M)
     assert rel_l2(img, ref) <= TOL
+
+
+@pytest.mark.parametrize("tau", [0.97, 1.0, 1.02])
+def test_deferred_fp64_weight_decisions_pulse_rows(tau):
+    """Pulse-row samples whose weight is decided in FP64 after the spread: samples within q
+    of the grid edges (every tau) and samples with 1/G within the guard band of tau (tau = 1.0
+    catches those near integer frequencies, where G is within 1e-5 of 1)."""
+    M = 64
+    g = np.random.default_rng(31)
+    lens = [60] * 40
+    ly = np.repeat(g.uniform(-0.45 * M, 0.45 * M, len(lens)), lens)
+    lx = np.empty(ly.shape[0])
+    pos = 0
+    for r, n in enumerate(lens):
+        if r % 4 == 0:                          # rows hugging the low and high grid edges
+            base = -M / 2 if r % 8 == 0 else M / 2 - 5.0
+            lx[pos:pos + n] = base + np.sort(g.uniform(0.0, 5.0 - 1e-9, n))
+        elif r % 4 == 1:                        # rows on and near integer frequencies
+            lx[pos:pos + n] = np.round(g.uniform(-20, 20, n)) + g.choice([0.0, 1e-7, -1e-7, 0.5], n)
+        else:
+            lx[pos:pos + n] = np.sort(g.uniform(-0.45 * M, 0.45 * M, n))
+        pos += n
+    v = (g.standard_normal(lx.shape[0]) + 1j * g.standard_normal(lx.shape[0])).astype(np.complex64)
+    img, D, kept, info = gpu_adjoint(lx, ly, v, M, layout="rows", width=8, wkw=dict(tau=tau))
+    assert info["layout"] == 2
+    Dref = oracle.tffr_weights(lx, M, tau=tau)
+    assert kept == np.count_nonzero(Dref)
+    ref = oracle.adjoint_image(lx, ly, v, Dref, M, M)
+    assert rel_l2(img, ref) <= TOL
