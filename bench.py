@@ -121,6 +121,12 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+def whole_job_rate(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Units per second over all ranks: each rank processes its own units (weak
+    scaling), and the job takes as long as the slowest rank."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def gpu_id_for_smi(local_rank: int):
     try:
         import torch
@@ -250,7 +256,7 @@ def run_gpu(args, world, rank, local):
     launches = plan.info()["kernel_launches"] - launches0
     ms = ev0.elapsed_time(ev1) / args.steps
     ms_max = max_over_ranks(ms, world)
-    value = world * N / (ms_max * 1e-3)
+    value = whole_job_rate(N, world, ms_max)
 
     # ---- per-kernel times: a separate pass with stage events on the stream ----
     kp = min(args.steps, 200)
@@ -359,7 +365,7 @@ def run_gpu(args, world, rank, local):
                                                    for k in ("spread", "row_fft", "col_fft")) * 1e-3),
             "forward": {"value": N / (fwd_ms * 1e-3), "unit": UNIT, "ms": fwd_ms},
             "accuracy": {"rel_l2_vs_fp64_oracle": rel, "pixels": int(jx.shape[0])},
-            "e2e": {"value": world * N / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+            "e2e": {"value": whole_job_rate(N, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),

@@ -56,7 +56,8 @@ typedef enum {
     TFFR_ERR_NOT_READY = 2,   /* adjoint/forward before set_points and weights */
     TFFR_ERR_CUDA = 3,        /* a CUDA call failed; see tffr_last_error */
     TFFR_ERR_OOM = 4,         /* device allocation failed */
-    TFFR_ERR_TIMEOUT = 5      /* a bounded device wait gave up */
+    TFFR_ERR_TIMEOUT = 5      /* a bounded device wait gave up (reserved: no kernel of this
+                                 version waits on another CTA or on the host) */
 } tffr_status;
 
 /* Storage type of the sample values read by tffr_adjoint (and written by
