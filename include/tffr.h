@@ -76,12 +76,22 @@ typedef enum {
     TFFR_POINTS_ROWS = 2     /* consecutive samples with bit-equal lam_y form one pulse row */
 } tffr_points_layout;
 
+/* Order of the two FFT passes on pulse rows.  Both compute the same image
+ * (the x transform is linear, so it may come before or after the azimuth
+ * taps); the pulse-row order transforms P pulse rows instead of 2 My fine
+ * rows and keeps a P x Mx intermediate instead of 2 My x Mx. */
+typedef enum {
+    TFFR_ORDER_AUTO = 0,      /* pulse rows first when there are at most My of them */
+    TFFR_ORDER_FINE_ROWS = 1  /* azimuth taps first, then the x FFT of every fine row */
+} tffr_pass_order;
+
 typedef struct {
     int sigma;      /* oversampling of the FFT grid; only 2 is supported */
     int width;      /* spreading-kernel width w in fine cells: 2, 4, 6 or 8 (default 6) */
     double beta;    /* exponential-of-semicircle shape; <= 0 selects 2.30 * width */
     int values;     /* tffr_values (default TFFR_VALUES_C64) */
     int layout;     /* tffr_points_layout (default TFFR_POINTS_AUTO) */
+    int order;      /* tffr_pass_order (default TFFR_ORDER_AUTO) */
 } tffr_opts;
 
 typedef enum {
@@ -112,6 +122,7 @@ typedef struct {
     int64_t n_kept;            /* samples with D_n != 0 after the last tffr_weights (-1 if unknown) */
     size_t device_bytes;       /* device memory held by the plan */
     int64_t kernel_launches;   /* kernels this plan has launched since it was created */
+    int pulse_order;           /* 1 when the pulse-row order of the FFT passes is in use */
 } tffr_plan_info;
 
 /* Stages of the pipeline, for tffr_profile_read. */

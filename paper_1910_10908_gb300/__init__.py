@@ -17,7 +17,7 @@ import ctypes
 import torch
 
 from . import _abi
-from ._abi import VALUES, LAYOUTS, WEIGHT_MODES
+from ._abi import VALUES, LAYOUTS, ORDERS, WEIGHT_MODES
 
 __all__ = ["TffrError", "Plan", "tffr_plan", "tffr_set_points", "tffr_weights", "tffr_adjoint",
            "tffr_forward", "tffr_destroy", "tffr_plan_get_info", "tffr_profile", "tffr_profile_read",
@@ -64,7 +64,7 @@ def _dev(t: torch.Tensor, name: str, dtype=None):
 # ---- the C entry points, one to one ----
 
 def tffr_plan(Mx: int, My: int, *, width: int = 6, beta: float = 0.0, values: str = "c64",
-              layout: str = "auto", stream=None) -> ctypes.c_void_p:
+              layout: str = "auto", order: str = "auto", stream=None) -> ctypes.c_void_p:
     lib = _abi.load()
     o = _abi.tffr_opts()
     lib.tffr_default_opts(ctypes.byref(o))
@@ -72,6 +72,7 @@ def tffr_plan(Mx: int, My: int, *, width: int = 6, beta: float = 0.0, values: st
     o.beta = float(beta)
     o.values = VALUES[values]
     o.layout = LAYOUTS[layout]
+    o.order = ORDERS[order]
     if stream is None:
         stream = torch.cuda.current_stream()
     handle = ctypes.c_void_p()
@@ -174,14 +175,14 @@ class Plan:
     """One image size, one point set, one set of weights; adjoint and forward on demand."""
 
     def __init__(self, Mx: int, My: int | None = None, *, width: int = 6, beta: float = 0.0,
-                 values: str = "c64", layout: str = "auto", device=None):
+                 values: str = "c64", layout: str = "auto", order: str = "auto", device=None):
         self.Mx, self.My = int(Mx), int(My if My is not None else Mx)
         self.values = values
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         with torch.cuda.device(self.device):
             self.stream = torch.cuda.current_stream()
             self._h = tffr_plan(self.Mx, self.My, width=width, beta=beta, values=values, layout=layout,
-                                stream=self.stream)
+                                order=order, stream=self.stream)
         self.N = None          # samples of the last set_points (None before)
 
     def _handle(self):

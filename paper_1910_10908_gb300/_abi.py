@@ -17,12 +17,13 @@ TFFR_ERR_TIMEOUT = 5
 
 VALUES = {"c64": 0, "c128": 1, "f16": 2, "bf16": 3}
 LAYOUTS = {"auto": 0, "general": 1, "rows": 2}
+ORDERS = {"auto": 0, "fine_rows": 1}
 WEIGHT_MODES = {"tffr": 0, "unit": 1, "user": 2}
 
 
 class tffr_opts(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_int), ("width", ctypes.c_int), ("beta", ctypes.c_double),
-                ("values", ctypes.c_int), ("layout", ctypes.c_int)]
+                ("values", ctypes.c_int), ("layout", ctypes.c_int), ("order", ctypes.c_int)]
 
 
 class tffr_weight_opts(ctypes.Structure):
@@ -35,7 +36,7 @@ class tffr_plan_info(ctypes.Structure):
                 ("width", ctypes.c_int), ("beta", ctypes.c_double), ("N", ctypes.c_int64),
                 ("layout", ctypes.c_int), ("n_rows", ctypes.c_int64), ("row_cells", ctypes.c_int64),
                 ("max_row_cells", ctypes.c_int), ("n_kept", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("pulse_order", ctypes.c_int)]
 
 
 STAGES = ["points", "weights", "spread", "row_fft", "col_fft", "fwd_col_fft", "fwd_row_fft", "interp"]

@@ -261,6 +261,31 @@ __device__ __forceinline__ void fft_line_epilogue(float2* buf, const Twiddles& t
         for (int r = 0; r < R; ++r) epi(threadIdx.x + b * L::T + r * (L::N / R), v[b * R + r]);
 }
 
+// As fft_line_epilogue, but the first stage's input arrives in registers,
+// v[r] = x[tid + r T] (the layout the first stage loads); buf is free to be
+// overwritten when this is called.
+template <int LOGN, int SGN, typename Epi>
+__device__ __forceinline__ void fft_line_epilogue_regs(float2 (&v)[Line<LOGN>::V], float2* buf, const Twiddles& tw,
+                                                       Epi& epi) {
+    using L = Line<LOGN>;
+    constexpr int NSMEM = L::REM ? L::NFULL : L::NFULL - 1;
+    constexpr int R = L::REM ? (1 << L::REM) : L::V;
+    constexpr int LOGNS = NSMEM * L::LV;
+    static_assert(NSMEM >= 1, "the first stage must not be the last");
+    stage_compute<LOGN, L::V, 0, SGN>(v, tw);
+    stage_store<LOGN, L::V, 0>(v, buf);
+    __syncthreads();
+    FullStages<LOGN, 1, NSMEM, SGN>::run(buf, tw);
+    stage_load<LOGN, R>(v, buf);
+    __syncthreads();
+    stage_compute<LOGN, R, LOGNS, SGN>(v, tw);
+    constexpr int B = L::V / R;
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+        for (int r = 0; r < R; ++r) epi(threadIdx.x + b * L::T + r * (L::N / R), v[b * R + r]);
+}
+
 // Load the twiddle tables of an N-point line into shared memory: the two
 // levels for any exponent and the direct table of the NT-th roots.
 template <int LOGN>

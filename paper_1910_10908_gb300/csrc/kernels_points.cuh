@@ -409,10 +409,12 @@ __global__ void k_fill_int(int n, int v, int* __restrict__ a) {
 // fine cell row_clo and its length row_len; a footprint of >= nx cells takes
 // the whole periodic row, row_clo = 0, row_len = nx) and the row's y cell.
 // Puts the extent arrays back to their identities for the next scan.
-__global__ void k_row_finish(const int* __restrict__ runs, int cap, int nx, int w, const double* __restrict__ lam_y,
-                             const int* __restrict__ row_start, int* __restrict__ row_min, int* __restrict__ row_max,
-                             int* __restrict__ row_clo, int* __restrict__ row_len, int* __restrict__ row_ly,
-                             float* __restrict__ row_fy, double* __restrict__ row_lam_y) {
+// Also the row's w azimuth taps, row_wy[p][s] = phi(s - (w/2 - 1) - fy) (stride 8).
+__global__ void k_row_finish(const int* __restrict__ runs, int cap, int nx, int w, TapPoly tp,
+                             const double* __restrict__ lam_y, const int* __restrict__ row_start,
+                             int* __restrict__ row_min, int* __restrict__ row_max, int* __restrict__ row_clo,
+                             int* __restrict__ row_len, int* __restrict__ row_ly, float* __restrict__ row_fy,
+                             double* __restrict__ row_lam_y, float* __restrict__ row_wy) {
     const int P = min(*runs, cap);
     const int h = w / 2;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
@@ -434,6 +436,9 @@ __global__ void k_row_finish(const int* __restrict__ runs, int cap, int nx, int 
         row_ly[p] = cy;
         row_fy[p] = fy;
         row_lam_y[p] = ly;
+        const float t = 2.0f * fy - 1.0f;
+#pragma unroll
+        for (int s = 0; s < 8; ++s) row_wy[(size_t)p * 8 + s] = (s < w) ? tap_eval(tp, s, t) : 0.0f;
     }
 }
 
@@ -470,19 +475,40 @@ __global__ void k_tap_count(const int* __restrict__ runs, int cap, int ny, int w
         for (int t = 0; t < w; ++t) atomicAdd(&count[wrapmod(row_ly[p] - (h - 1) + t, ny)], 1);
 }
 
-// Exclusive scan of n counts into start[0..n] (single block).
-__global__ void k_scan_counts(int n, const int* __restrict__ count, int* __restrict__ start) {
+// Exclusive scan of n counts into start[0..n] (single block); *max_count =
+// the largest count.
+__global__ void k_scan_counts(int n, const int* __restrict__ count, int* __restrict__ start,
+                              int* __restrict__ max_count) {
     __shared__ int s_warp[32];
-    int carry = 0;
+    int carry = 0, mx = 0;
     for (int base = 0; base < n; base += kScanThreads) {
         const int i = base + threadIdx.x;
         const int x = (i < n) ? count[i] : 0;
+        mx = max(mx, x);
         int tot;
         const int ex = block_exclusive_scan(x, s_warp, &tot);
         if (i < n) start[i] = carry + ex;
         carry += tot;
     }
     if (threadIdx.x == 0) start[n] = carry;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(max_count, mx);
+}
+
+// Azimuth taps as a table of fixed width per fine row (pulse-row order of
+// the FFT passes): slot k of fine row r holds (pulse row, tap weight) in
+// ell[k * ny + r]; slots past the row's count stay (0, 0).  cursor: zeroed.
+__global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny, int w, const int* __restrict__ row_ly,
+                           const float* __restrict__ row_wy, int* __restrict__ cursor, int2* __restrict__ ell) {
+    const int P = min(*runs, cap);
+    const int h = w / 2;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+        for (int t = 0; t < w; ++t) {
+            const int r = wrapmod(row_ly[p] - (h - 1) + t, ny);
+            const int k = atomicAdd(&cursor[r], 1);
+            if (k < kEllMax) ell[(size_t)k * ny + r] = make_int2(p, __float_as_int(row_wy[(size_t)p * 8 + t]));
+        }
 }
 
 __global__ void k_tap_fill(const int* __restrict__ runs, int cap, int ny, int w, TapPoly tp, const int* __restrict__ row_ly,

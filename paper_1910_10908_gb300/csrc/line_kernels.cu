@@ -28,6 +28,10 @@ cudaError_t attrs_for() {
     if (e == cudaSuccess) e = smem_attr(k_fwd_cols<LOGN>, b);
     if (e == cudaSuccess) e = smem_attr(k_fwd_rows<LOGN, true>, b);
     if (e == cudaSuccess) e = smem_attr(k_fwd_rows<LOGN, false>, b);
+    if (e == cudaSuccess) e = smem_attr(k_adj_rows_pulse<LOGN>, b);
+    if (e == cudaSuccess) e = smem_attr(k_fwd_rows_pulse<LOGN>, b);
+    if (e == cudaSuccess) e = smem_attr(k_adj_cols_pulse<LOGN>, line_smem_pulse_cols<LOGN>());
+    if (e == cudaSuccess) e = smem_attr(k_fwd_cols_pulse<LOGN>, line_smem_pulse_cols<LOGN>());
     return e;
 }
 
@@ -93,6 +97,37 @@ void launch_fwd_rows(int lognx, int ny, bool rows, cudaStream_t s, const RowsVie
         TFFR_LOGN_SWITCH(lognx, L)
 #undef L
     }
+}
+
+void launch_adj_rows_pulse(int lognx, int P, cudaStream_t s, const RowsView& rv, const float2* R, FftTables tab,
+                           const float* deap_x, float2* F) {
+#define L(LG) k_adj_rows_pulse<LG><<<P, Line<LG>::T, line_smem<LG>(), s>>>(rv, R, tab, deap_x, F)
+    TFFR_LOGN_SWITCH(lognx, L)
+#undef L
+}
+
+void launch_adj_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float2* F, FftTables tab,
+                           const int2* ell, int K, const float* deap_y, float2* img) {
+#define L(LG) k_adj_cols_pulse<LG><<<Mx, Line<LG>::T, line_smem_pulse_cols<LG>(), s>>>(F, P, Mx, tab, ell, K, \
+                                                                                      deap_y, img)
+    TFFR_LOGN_SWITCH(logny, L)
+#undef L
+}
+
+void launch_fwd_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float2* img, FftTables tab,
+                           const float* deap_y, const float* deap_x, const int* row_ly, const float* row_wy, int w,
+                           float2* F) {
+#define L(LG) k_fwd_cols_pulse<LG><<<Mx, Line<LG>::T, line_smem_pulse_cols<LG>(), s>>>(img, Mx, tab, deap_y, deap_x, \
+                                                                                      row_ly, row_wy, w, P, F)
+    TFFR_LOGN_SWITCH(logny, L)
+#undef L
+}
+
+void launch_fwd_rows_pulse(int lognx, int P, cudaStream_t s, const RowsView& rv, const float2* F, FftTables tab,
+                           float2* R) {
+#define L(LG) k_fwd_rows_pulse<LG><<<P, Line<LG>::T, line_smem<LG>(), s>>>(rv, F, tab, R)
+    TFFR_LOGN_SWITCH(lognx, L)
+#undef L
 }
 
 }  // namespace tffr

@@ -364,4 +364,238 @@ k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int ny, in
     }
 }
 
+// ---------------------------------------------------------------------------
+// Pulse-row order of the two passes (rows layout with at most M_y pulse rows).
+// The FFT along x is linear, so it can run on the P pulse-row buffers before
+// the azimuth taps instead of on the 2 M_y fine rows after them:
+//   F_p = prune(FFT_x(R_p)) / phi_hat(kx)                       ([P][M_x])
+//   fine row r of the column line = sum_p phi_y(r - v_p) F_p[kx]
+// The taps then become a 1-D spread along y inside the column pass, the x
+// FFTs drop from 2 M_y to P lines and the intermediate from 2 M_y M_x to
+// P M_x entries.  The forward twin runs the transposed steps.
+// row_wy holds the w azimuth taps of each pulse row (stride 8 floats).
+// ---------------------------------------------------------------------------
+
+// Column-pass shared memory: the line plus one column of F (up to N/2 pulse rows).
+template <int LOGN>
+__host__ __device__ constexpr size_t line_smem_pulse_cols() {
+    return line_smem_bytes<LOGN>() + (size_t)(Line<LOGN>::N / 2) * sizeof(float2);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_adj_rows_pulse(RowsView rv, const float2* __restrict__ R, FftTables tab, const float* __restrict__ deap_x,
+                 float2* __restrict__ F) {
+    using L = Line<LOGN>;
+    constexpr int NX = L::N;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    const int p = blockIdx.x;
+    const int tid = threadIdx.x;
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
+    for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int len = rv.row_len[p], clo = rv.row_clo[p];
+    const float2* Rp = R + rv.row_off[p];
+    for (int i = tid; i < len; i += L::T) S.buf[L::pad(wrapmod(clo + i, NX))] = __ldg(&Rp[i]);
+    __syncthreads();
+    RowOut<LOGN> epi{p, deap_x, F};
+    fft_line_epilogue<LOGN, +1>(S.buf, tw, epi);
+}
+
+constexpr int kPulseBatch = 4;                         // pulse rows whose taps are loaded together
+
+// The w azimuth taps of pulse row p, two 16-byte loads.
+__device__ __forceinline__ void load_row_taps(const float* __restrict__ row_wy, int p, float (&wy)[8]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(row_wy + (size_t)p * 8));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(row_wy + (size_t)p * 8 + 4));
+    wy[0] = a.x; wy[1] = a.y; wy[2] = a.z; wy[3] = a.w;
+    wy[4] = b.x; wy[5] = b.y; wy[6] = b.z; wy[7] = b.w;
+}
+
+template <int LOGN>
+__global__ void __cluster_dims__(kColCluster, 1, 1) __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, const int2* __restrict__ ell, int K,
+                 const float* __restrict__ deap_y, float2* __restrict__ img) {
+    using L = Line<LOGN>;
+    constexpr int NY = L::N, MY = NY / 2, V = L::V;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    float2* fcol = smem + L::SMEM_ELEMS;               // this CTA's column of F, P entries
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int jx0 = (int)blockIdx.x - rank;
+    const int tid = threadIdx.x;
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
+    static_assert(L::T % kColCluster == 0, "line threads must be a multiple of the cluster size");
+    // element i of this CTA's share (pulse row p0 + i / 4, column i % 4 = tid % 4)
+    float2* const peer_f = cluster.map_shared_rank(fcol, tid % kColCluster);
+    const int PQ = (P + kColCluster - 1) / kColCluster;
+    const int p0 = min(P, rank * PQ), nel = (min(P, p0 + PQ) - p0) * kColCluster;
+    cluster_arrive_relaxed();                          // every CTA runs before its memory is written
+    cluster_wait();
+    for (int base = 0; base < nel; base += V * L::T) {
+        float2 tmp[V];
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int i = base + tid + u * L::T;
+            tmp[u] = (i < nel) ? __ldg(&F[(size_t)(p0 + i / kColCluster) * Mx + jx0 + i % kColCluster])
+                               : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int i = base + tid + u * L::T;
+            if (i < nel) peer_f[p0 + i / kColCluster] = tmp[u];
+        }
+    }
+    cluster.sync();
+    // azimuth taps, gathered: fine row r = sum over its table slots k < K of
+    // weight_k F[p_k] (K: the most pulse rows any fine row receives), straight
+    // into the registers of the first FFT stage (row tid + u T)
+    float2 v[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) v[u] = make_float2(0.f, 0.f);
+    constexpr int UB = V >= 8 ? 8 : V;
+#pragma unroll
+    for (int u0 = 0; u0 < V; u0 += UB) {
+        for (int k = 0; k < K; ++k) {
+            int2 e[UB];
+#pragma unroll
+            for (int j = 0; j < UB; ++j) e[j] = __ldg(&ell[(size_t)k * NY + tid + (u0 + j) * L::T]);
+#pragma unroll
+            for (int j = 0; j < UB; ++j) {
+                const float2 f = fcol[e[j].x];
+                const float g = __int_as_float(e[j].y);
+                v[u0 + j].x = fmaf(g, f.x, v[u0 + j].x);
+                v[u0 + j].y = fmaf(g, f.y, v[u0 + j].y);
+            }
+        }
+    }
+    ColPark<LOGN> epi{deap_y, S.buf};
+    fft_line_epilogue_regs<LOGN, +1>(v, S.buf, tw, epi);
+    cluster.sync();
+    float2* const peer = cluster.map_shared_rank(S.buf, tid % kColCluster);
+    constexpr int OROWS = MY / kColCluster;
+    {
+        float2 tmp[V / 2];
+#pragma unroll
+        for (int u = 0; u < V / 2; ++u) {
+            const int i = tid + u * L::T;
+            tmp[u] = peer[L::pad(rank * OROWS + i / kColCluster)];
+        }
+#pragma unroll
+        for (int u = 0; u < V / 2; ++u) {
+            const int i = tid + u * L::T;
+            img[(size_t)(rank * OROWS + i / kColCluster) * Mx + jx0 + i % kColCluster] = tmp[u];
+        }
+    }
+    cluster_arrive_relaxed();                          // every remote load was consumed above
+    cluster_wait();
+}
+
+template <int LOGN>
+__global__ void __cluster_dims__(kColCluster, 1, 1) __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_fwd_cols_pulse(const float2* __restrict__ img, int Mx, FftTables tab, const float* __restrict__ deap_y,
+                 const float* __restrict__ deap_x, const int* __restrict__ row_ly, const float* __restrict__ row_wy,
+                 int w, int P, float2* __restrict__ F) {
+    using L = Line<LOGN>;
+    constexpr int NY = L::N, MY = NY / 2, V = L::V;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    float2* fcol = smem + L::SMEM_ELEMS;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int jx0 = (int)blockIdx.x - rank;
+    const int tid = threadIdx.x;
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
+    for (int i = MY / 2 + tid; i < NY - MY / 2; i += L::T) S.buf[L::pad(i)] = make_float2(0.f, 0.f);
+    static_assert(L::T % kColCluster == 0, "line threads must be a multiple of the cluster size");
+    float2* const peer = cluster.map_shared_rank(S.buf, tid % kColCluster);
+    constexpr int IROWS = MY / kColCluster;
+    {
+        cluster_arrive_relaxed();                      // every CTA runs before its memory is written
+        float2 tmp[V / 2];
+#pragma unroll
+        for (int u = 0; u < V / 2; ++u) {
+            const int i = tid + u * L::T;
+            tmp[u] = __ldg(&img[(size_t)(rank * IROWS + i / kColCluster) * Mx + jx0 + i % kColCluster]);
+        }
+        cluster_wait();
+        const float dx = __ldg(&deap_x[jx0 + tid % kColCluster]);
+#pragma unroll
+        for (int u = 0; u < V / 2; ++u) {
+            const int i = tid + u * L::T;
+            const int jy = rank * IROWS + i / kColCluster;
+            peer[L::pad(wrapmod(jy - MY / 2, NY))] = cscale(tmp[u], __ldg(&deap_y[jy]) * dx);
+        }
+    }
+    cluster.sync();
+    fft_line_smem<LOGN, -1>(S.buf, tw);
+    // transposed azimuth taps: F_p = sum_s phi_y(s - (w/2 - 1) - fy_p) line[ly_p - (w/2 - 1) + s]
+    const int h = w / 2;
+    for (int base = 0; base < P; base += kPulseBatch * L::T) {
+        int c0[kPulseBatch];
+        float wy[kPulseBatch][8];
+#pragma unroll
+        for (int b = 0; b < kPulseBatch; ++b) {
+            const int p = min(base + tid + b * L::T, P - 1);
+            c0[b] = __ldg(&row_ly[p]) - (h - 1);
+            load_row_taps(row_wy, p, wy[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < kPulseBatch; ++b) {
+            const int p = base + tid + b * L::T;
+            if (p >= P) break;
+            float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                if (s < w) {
+                    const float2 g = S.buf[L::pad(wrapmod(c0[b] + s, NY))];
+                    a.x = fmaf(wy[b][s], g.x, a.x);
+                    a.y = fmaf(wy[b][s], g.y, a.y);
+                }
+            }
+            fcol[p] = a;
+        }
+    }
+    cluster.sync();
+    float2* const peer_f = cluster.map_shared_rank(fcol, tid % kColCluster);
+    const int PQ = (P + kColCluster - 1) / kColCluster;
+    const int p0 = min(P, rank * PQ), nel = (min(P, p0 + PQ) - p0) * kColCluster;
+    for (int base = 0; base < nel; base += V * L::T) {
+        float2 tmp[V];
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int i = base + tid + u * L::T;
+            tmp[u] = (i < nel) ? peer_f[p0 + i / kColCluster] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int i = base + tid + u * L::T;
+            if (i < nel) F[(size_t)(p0 + i / kColCluster) * Mx + jx0 + i % kColCluster] = tmp[u];
+        }
+    }
+    cluster_arrive_relaxed();                          // every remote load was consumed above
+    cluster_wait();
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_fwd_rows_pulse(RowsView rv, const float2* __restrict__ F, FftTables tab, float2* __restrict__ R) {
+    using L = Line<LOGN>;
+    constexpr int NX = L::N, MX = NX / 2;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    const int p = blockIdx.x;
+    const int tid = threadIdx.x;
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
+    for (int i = MX / 2 + tid; i < NX - MX / 2; i += L::T) S.buf[L::pad(i)] = make_float2(0.f, 0.f);
+    for (int jx = tid; jx < MX; jx += L::T) S.buf[L::pad(wrapmod(jx - MX / 2, NX))] = F[(size_t)p * MX + jx];
+    __syncthreads();
+    fft_line_smem<LOGN, -1>(S.buf, tw);
+    const int len = rv.row_len[p], clo = rv.row_clo[p];
+    float2* Rp = R + rv.row_off[p];
+    for (int i = tid; i < len; i += L::T) Rp[i] = S.buf[L::pad(wrapmod(clo + i, NX))];
+}
+
 }  // namespace tffr

@@ -41,6 +41,7 @@ struct tffr_plan_s {
     double beta = 0.0;
     int values = TFFR_VALUES_C64;
     int layout_hint = TFFR_POINTS_AUTO;
+    int order_hint = TFFR_ORDER_AUTO;
     cudaStream_t stream = nullptr;
     std::string last_error;
     size_t device_bytes = 0;
@@ -53,9 +54,10 @@ struct tffr_plan_s {
     DevBuf<float2> twh_x, twl_x, twh_y, twl_y, tt_x, tt_y, T;
     DevBuf<float> deap_x, deap_y;
     DevBuf<int> d_small;                   // [0] error bits, [1] rows, [2] longest row, [3] row overflow,
+                                           // [4] most pulse rows reaching one fine row,
                                            // [5] samples deferred to the FP64 weight decision
     DevBuf<int2> defer;                    // [N] deferred (sample, pulse row)
-    int* h_small = nullptr;                // pinned read-back: d_small[0..3], then the total cells (int64)
+    int* h_small = nullptr;                // pinned read-back: d_small[0..4]; [6..7] the total cells (int64)
     DevBuf<long long> d_big;               // [0] total row-buffer cells
     DevBuf<unsigned long long> d_kept;
 
@@ -75,6 +77,10 @@ struct tffr_plan_s {
     int64_t R_cells = 0;
     int max_len = 0;
     int row_cap = 0;                       // capacity of the per-row arrays
+    bool pulse_order = false;              // FFT passes in pulse-row order (F [P][Mx] in T's memory)
+    DevBuf<float> row_wy;                  // [cap][8] azimuth taps of each pulse row
+    DevBuf<int2> ell;                      // [kEllMax][ny] fine-row tap table (pulse-row order)
+    int ell_k = 0;                         // slots in use: the most pulse rows a fine row receives
     DevBuf<int> row_start, row_end, row_clo, row_len, row_ly, row_min, row_max, bucket_start;
     DevBuf<float> row_fy;
     DevBuf<double> row_lam_y;
@@ -449,6 +455,7 @@ int reserve_rows(tffr_plan_s* p, int cap) {
     CK(grow(p, p->row_fy, cap));
     CK(grow(p, p->row_lam_y, cap));
     CK(grow(p, p->row_off, cap));
+    CK(grow(p, p->row_wy, (int64_t)cap * 8));
     CK(grow(p, p->tap_list, (int64_t)cap * w));
     k_fill_int<<<grid_for(cap, 256), 256, 0, p->stream>>>(cap, kIntMax, p->row_min.ptr);
     CK_LAUNCH("k_fill_int");
@@ -472,7 +479,7 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     CK(grow(p, p->tap_start, ny + 1));
     CK(grow(p, p->cursor, ny + 1));
     CK(grow(p, p->d_big, 1));
-    CK(cudaMemsetAsync(p->d_small.ptr, 0, 4 * sizeof(int), p->stream));
+    CK(cudaMemsetAsync(p->d_small.ptr, 0, 5 * sizeof(int), p->stream));
     RowScanArgs a;
     a.row_start = p->row_start.ptr;
     a.row_end = p->row_end.ptr;
@@ -487,30 +494,27 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     k_scan_fixup<<<1, kScanThreads, 0, p->stream>>>((int)ntiles, N, a);
     CK_LAUNCH("k_scan_fixup");
     const int* runs = p->d_small.ptr + 1;
-    k_row_finish<<<prow, 256, 0, p->stream>>>(runs, cap, p->nx, w, p->lam_y, p->row_start.ptr, p->row_min.ptr,
-                                              p->row_max.ptr, p->row_clo.ptr, p->row_len.ptr, p->row_ly.ptr,
-                                              p->row_fy.ptr, p->row_lam_y.ptr);
+    k_row_finish<<<prow, 256, 0, p->stream>>>(runs, cap, p->nx, w, p->taps, p->lam_y, p->row_start.ptr,
+                                              p->row_min.ptr, p->row_max.ptr, p->row_clo.ptr, p->row_len.ptr,
+                                              p->row_ly.ptr, p->row_fy.ptr, p->row_lam_y.ptr, p->row_wy.ptr);
     CK_LAUNCH("k_row_finish");
     k_row_offsets<<<1, kScanThreads, 0, p->stream>>>(runs, cap, p->row_len.ptr, p->row_off.ptr, p->d_big.ptr,
                                                       p->d_small.ptr + 2);
     CK_LAUNCH("k_row_offsets");
+    // fine rows reached by each pulse row's azimuth taps: counts (and the
+    // largest, which picks the order of the FFT passes) before the read-back
     CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
     k_tap_count<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->cursor.ptr);
     CK_LAUNCH("k_tap_count");
-    k_scan_counts<<<1, kScanThreads, 0, p->stream>>>(ny, p->cursor.ptr, p->tap_start.ptr);
+    k_scan_counts<<<1, kScanThreads, 0, p->stream>>>(ny, p->cursor.ptr, p->tap_start.ptr, p->d_small.ptr + 4);
     CK_LAUNCH("k_scan_counts");
-    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
-    k_tap_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->taps, p->row_ly.ptr, p->row_fy.ptr,
-                                            p->row_clo.ptr, p->row_len.ptr, p->row_off.ptr, p->tap_start.ptr,
-                                            p->cursor.ptr, p->tap_list.ptr);
-    CK_LAUNCH("k_tap_fill");
-    CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 4 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaMemcpyAsync(p->h_small + 4, p->d_big.ptr, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 5 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaMemcpyAsync(p->h_small + 6, p->d_big.ptr, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
-    int hs[4];
+    int hs[5];
     long long tot;
     std::memcpy(hs, p->h_small, sizeof(hs));
-    std::memcpy(&tot, p->h_small + 4, sizeof(tot));
+    std::memcpy(&tot, p->h_small + 6, sizeof(tot));
     if (hs[0] & 1) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_y or |lam_y| >= 2^28");
     if (hs[0] & 2) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_x or |lam_x| >= 2^28");
     *P_out = hs[1];
@@ -519,6 +523,24 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     p->max_len = hs[2];
     p->R_cells = tot;
     CK(grow(p, p->R, tot));
+    // the fine-row order needs the azimuth tap lists of every fine row (built
+    // after the read-back, ordered on the stream like everything else)
+    p->pulse_order = p->order_hint == TFFR_ORDER_AUTO && p->P >= 1 && p->P <= p->My && hs[4] <= kEllMax;
+    if (p->pulse_order) {
+        p->ell_k = hs[4];
+        CK(grow(p, p->ell, (int64_t)kEllMax * ny));
+        CK(cudaMemsetAsync(p->ell.ptr, 0, (size_t)p->ell_k * ny * sizeof(int2), p->stream));
+        CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
+        k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, p->cursor.ptr,
+                                                p->ell.ptr);
+        CK_LAUNCH("k_ell_fill");
+    } else {
+        CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
+        k_tap_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->taps, p->row_ly.ptr, p->row_fy.ptr,
+                                                p->row_clo.ptr, p->row_len.ptr, p->row_off.ptr, p->tap_start.ptr,
+                                                p->cursor.ptr, p->tap_list.ptr);
+        CK_LAUNCH("k_tap_fill");
+    }
     return TFFR_OK;
 }
 
@@ -595,6 +617,17 @@ int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
         CK_LAUNCH("k_spread_rows");
         STAGE_END(TFFR_STAGE_SPREAD);
         STAGE_BEGIN(TFFR_STAGE_ROW_FFT);
+        if (p->pulse_order) {
+            launch_adj_rows_pulse(p->lognx, p->P, p->stream, rv, p->R.ptr, tables_x(p), p->deap_x.ptr, p->T.ptr);
+            CK_LAUNCH("k_adj_rows_pulse");
+            STAGE_END(TFFR_STAGE_ROW_FFT);
+            STAGE_BEGIN(TFFR_STAGE_COL_FFT);
+            launch_adj_cols_pulse(p->logny, p->Mx, p->P, p->stream, p->T.ptr, tables_y(p), p->ell.ptr, p->ell_k,
+                                  p->deap_y.ptr, image);
+            CK_LAUNCH("k_adj_cols_pulse");
+            STAGE_END(TFFR_STAGE_COL_FFT);
+            return TFFR_OK;
+        }
         launch_adj_rows(p->lognx, ny, p->stream, rv, p->R.ptr, p->w, p->taps, tables_x(p), p->deap_x.ptr, p->T.ptr);
         CK_LAUNCH("k_adj_rows");
         STAGE_END(TFFR_STAGE_ROW_FFT);
@@ -625,18 +658,30 @@ void launch_interp(tffr_plan_s* p, const RowsView& rv, void* values, int apply_w
 template <typename VT>
 int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_weights) {
     const int ny = p->ny;
-    STAGE_BEGIN(TFFR_STAGE_FWD_COL_FFT);
-    launch_fwd_cols(p->logny, p->Mx, p->stream, image, tables_y(p), p->deap_y.ptr, p->deap_x.ptr, p->T.ptr);
-    CK_LAUNCH("k_fwd_cols");
-    STAGE_END(TFFR_STAGE_FWD_COL_FFT);
-    STAGE_BEGIN(TFFR_STAGE_FWD_ROW_FFT);
+    const bool pulse = p->layout == TFFR_POINTS_ROWS && p->pulse_order;
     const RowsView rv = rows_view(p);
     const GeneralView gv = general_view(p);
+    STAGE_BEGIN(TFFR_STAGE_FWD_COL_FFT);
+    if (pulse) {
+        launch_fwd_cols_pulse(p->logny, p->Mx, p->P, p->stream, image, tables_y(p), p->deap_y.ptr, p->deap_x.ptr,
+                              p->row_ly.ptr, p->row_wy.ptr, p->w, p->T.ptr);
+        CK_LAUNCH("k_fwd_cols_pulse");
+    } else {
+        launch_fwd_cols(p->logny, p->Mx, p->stream, image, tables_y(p), p->deap_y.ptr, p->deap_x.ptr, p->T.ptr);
+        CK_LAUNCH("k_fwd_cols");
+    }
+    STAGE_END(TFFR_STAGE_FWD_COL_FFT);
+    STAGE_BEGIN(TFFR_STAGE_FWD_ROW_FFT);
     if (p->layout == TFFR_POINTS_ROWS) {
-        CK(cudaMemsetAsync(p->R.ptr, 0, (size_t)p->R_cells * sizeof(float2), p->stream));
-        launch_fwd_rows(p->lognx, ny, true, p->stream, rv, gv, p->T.ptr, p->w, p->taps, tables_x(p), p->R.ptr,
-                        p->acc.ptr);
-        CK_LAUNCH("k_fwd_rows");
+        if (pulse) {
+            launch_fwd_rows_pulse(p->lognx, p->P, p->stream, rv, p->T.ptr, tables_x(p), p->R.ptr);
+            CK_LAUNCH("k_fwd_rows_pulse");
+        } else {
+            CK(cudaMemsetAsync(p->R.ptr, 0, (size_t)p->R_cells * sizeof(float2), p->stream));
+            launch_fwd_rows(p->lognx, ny, true, p->stream, rv, gv, p->T.ptr, p->w, p->taps, tables_x(p), p->R.ptr,
+                            p->acc.ptr);
+            CK_LAUNCH("k_fwd_rows");
+        }
         STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
         STAGE_BEGIN(TFFR_STAGE_INTERP);
         switch (p->w) {
@@ -765,6 +810,7 @@ void tffr_default_opts(tffr_opts* o) {
     o->beta = 0.0;
     o->values = TFFR_VALUES_C64;
     o->layout = TFFR_POINTS_AUTO;
+    o->order = TFFR_ORDER_AUTO;
 }
 
 void tffr_default_weight_opts(tffr_weight_opts* o) {
@@ -803,6 +849,7 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
     if (o.width < 2 || o.width > 8 || (o.width & 1)) return TFFR_ERR_INVALID_ARG;
     if (o.values < TFFR_VALUES_C64 || o.values > TFFR_VALUES_BF16) return TFFR_ERR_INVALID_ARG;
     if (o.layout < TFFR_POINTS_AUTO || o.layout > TFFR_POINTS_ROWS) return TFFR_ERR_INVALID_ARG;
+    if (o.order < TFFR_ORDER_AUTO || o.order > TFFR_ORDER_FINE_ROWS) return TFFR_ERR_INVALID_ARG;
     if (!(o.beta == o.beta) || o.beta > 100.0) return TFFR_ERR_INVALID_ARG;
     tffr_plan_s* p = new (std::nothrow) tffr_plan_s();
     if (!p) return TFFR_ERR_OOM;
@@ -816,6 +863,7 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
     p->beta = o.beta > 0 ? o.beta : 2.30 * o.width;
     p->values = o.values;
     p->layout_hint = o.layout;
+    p->order_hint = o.order;
     p->stream = (cudaStream_t)stream;
     fit_taps(p);
     std::memset(&p->wargs, 0, sizeof(p->wargs));
@@ -846,7 +894,8 @@ int tffr_destroy(tffr_plan_t p) {
     release(p->tile_info); release(p->tile_head); release(p->defer);
     if (p->h_small) cudaFreeHost(p->h_small);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly);
-    release(p->row_min); release(p->row_max); release(p->row_end);
+    release(p->row_min); release(p->row_max); release(p->row_end); release(p->row_wy);
+    release(p->ell);
     release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);
     release(p->tap_start); release(p->tap_list);
     release(p->lx); release(p->ly); release(p->perm); release(p->slx); release(p->cursor);
@@ -875,6 +924,7 @@ int tffr_plan_get_info(tffr_plan_t p, tffr_plan_info* info) {
     info->n_kept = p->have_weights ? p->n_kept : -1;
     info->device_bytes = p->device_bytes;
     info->kernel_launches = p->launches;
+    info->pulse_order = (rows && p->pulse_order) ? 1 : 0;
     return TFFR_OK;
 }
 

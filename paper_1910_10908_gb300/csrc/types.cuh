@@ -16,6 +16,9 @@ struct TapEntry {
     int p;
 };
 
+// Slots of the fine-row azimuth-tap table (pulse-row order of the FFT passes).
+constexpr int kEllMax = 8;
+
 struct RowsView {
     int P;                          // pulse rows
     const int* row_start;           // [P] first sample of the row (rows are contiguous runs)

@@ -38,10 +38,10 @@ def d_err(D, Dref):
     return float(np.max(np.abs(D - Dref) / np.maximum(1.0, np.abs(Dref))))
 
 
-def gpu_adjoint(lx, ly, vals, Mx, My=None, values="c64", layout="auto", width=6, wkw=None):
+def gpu_adjoint(lx, ly, vals, Mx, My=None, values="c64", layout="auto", width=6, wkw=None, order="auto"):
     from paper_1910_10908_gb300 import Plan
     My = Mx if My is None else My
-    with Plan(Mx, My, values=values, layout=layout, width=width) as plan:
+    with Plan(Mx, My, values=values, layout=layout, width=width, order=order) as plan:
         plan.set_points(dev(lx), dev(ly))
         D = torch.empty(lx.shape[0], dtype=torch.float32, device="cuda")
         kept = plan.weights(D_out=D, **(wkw or {}))
@@ -391,3 +391,35 @@ def test_deferred_fp64_weight_decisions_pulse_rows(tau):
     assert kept == np.count_nonzero(Dref)
     ref = oracle.adjoint_image(lx, ly, v, Dref, M, M)
     assert rel_l2(img, ref) <= TOL
+
+
+@pytest.mark.parametrize("order", ["auto", "fine_rows"])
+def test_both_orders_of_the_fft_passes(order):
+    """Pulse rows first (x FFT of the P pulse rows, azimuth taps inside the column pass) and
+    fine rows first (azimuth taps, then the x FFT of every fine row) give the oracle's image
+    and forward samples; non-square, so the two axes' sizes are not interchangeable."""
+    from paper_1910_10908_gb300 import Plan
+    lx, ly, _, v = stolt_scene(100, 160, 128, seed=41)
+    ly = ly * 0.5                                   # azimuth grid of 64 rows
+    Mx, My = 128, 64
+    v = v.astype(np.complex64)
+    img, D, kept, info = gpu_adjoint(lx, ly, v, Mx, My, layout="rows", width=8, order=order)
+    assert info["layout"] == 2 and info["n_rows"] == 100
+    assert info["pulse_order"] == 0                 # 100 pulse rows > My = 64: fine rows either way
+    Dref = oracle.tffr_weights(lx, Mx)
+    ref = oracle.adjoint_image(lx, ly, v, Dref, Mx, My)
+    assert rel_l2(img, ref) <= TOL
+    lx2, ly2, _, v2 = stolt_scene(48, 160, 128, seed=42)
+    v2 = v2.astype(np.complex64)
+    img2, _, _, info2 = gpu_adjoint(lx2, ly2, v2, Mx, Mx, layout="rows", width=8, order=order)
+    assert info2["pulse_order"] == (1 if order == "auto" else 0)
+    Dref2 = oracle.tffr_weights(lx2, Mx)
+    assert rel_l2(img2, oracle.adjoint_image(lx2, ly2, v2, Dref2, Mx, Mx)) <= TOL
+    g = np.random.default_rng(43)
+    f = (g.standard_normal((Mx, Mx)) + 1j * g.standard_normal((Mx, Mx))).astype(np.complex64)
+    with Plan(Mx, Mx, layout="rows", width=8, order=order) as plan:
+        plan.set_points(dev(lx2), dev(ly2))
+        plan.weights(count=False)
+        y = plan.forward(dev(f)).cpu().numpy().astype(np.complex128)
+    yref = oracle.forward_samples(lx2, ly2, f, Dref2)
+    assert rel_l2(y, yref) <= TOL
