@@ -34,6 +34,13 @@ METRIC = "NU samples/s, tFFR adjoint, 16.7M samples->4096^2 image, rel-L2<=1e-5;
 UNIT = "NU samples/s"
 WORKLOAD = "stripmap_4096"
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a stage's
+# kernel on this workload, from one ncu capture of that kernel; an entry is removed
+# when its kernel changes, and a stage without one reports null.
+DRAM_TRAFFIC = {
+    ("col_fft", "pulse_rows"): 232_713_472,     # k_adj_cols_pulse<13>
+}
+
 
 def peaks():
     try:
@@ -271,10 +278,12 @@ def run_gpu(args, world, rank, local):
     # once.  points: both coordinate arrays (16 B/sample).  weights: nothing,
     # D is evaluated inside the spread.  spread: lambda_x + value (16 B/sample)
     # in, pulse-row buffers (8 B/cell) out.  row_fft: row buffers in, the
-    # [2M][M] intermediate out.  col_fft: intermediate in, M x M image out.
+    # intermediate out ([P][M] in pulse-row order, [2M][M] in fine-row order).
+    # col_fft: intermediate in, M x M image out.
     hbm, peak_kind = peaks()
     R = int(info["row_cells"])
-    T_bytes = 8 * M * (2 * M)
+    pulse = bool(info["pulse_order"])
+    T_bytes = 8 * M * (int(info["n_rows"]) if pulse else 2 * M)
     alg = {
         "points": N * 16,
         "weights": 0,
@@ -292,7 +301,8 @@ def run_gpu(args, world, rank, local):
                 kern[name].update(gbs=b / (per * 1e-3) / 1e9, frac=b / (per * 1e-3) / 1e9 / hbm)
     hot = max(("spread", "row_fft", "col_fft"), key=lambda k: kern[k]["ms"])
     roof = {"bound": "hbm", "kernel": hot, "achieved": kern[hot]["gbs"], "peak": hbm, "unit": "GB/s",
-            "frac": kern[hot]["frac"], "peak_source": peak_kind, "traffic": None}
+            "frac": kern[hot]["frac"], "peak_source": peak_kind,
+            "traffic": DRAM_TRAFFIC.get((hot, "pulse_rows" if pulse else "fine_rows"))}
 
     # ---- forward twin, timed on its own ----
     yout = torch.empty(N, dtype=torch.complex64, device=dev)
@@ -356,6 +366,7 @@ def run_gpu(args, world, rank, local):
             "config": {"workload": WORKLOAD, "N": N, "image": "%dx%d" % (M, M), "pulses": wl.n_pulses,
                        "freqs": wl.n_freq, "sigma": 2, "width": 6, "beta": info["beta"], "values": "c64",
                        "layout": "rows" if info["layout"] == 2 else "general", "pulse_rows": info["n_rows"],
+                       "pass_order": "pulse_rows" if pulse else "fine_rows",
                        "step": "set_points+weights+adjoint", "l2": "inputs (402 MB/step) larger than L2",
                        "parallelism": "independent images per GPU" if world > 1 else "single GPU"},
             "roofline": roof,

@@ -143,8 +143,8 @@ __device__ __forceinline__ float weight_tffr(double lam_x, int cx, float fx, dou
 // checks every coordinate and takes each run's extent of fine x cells.
 // Tiles number their runs from one atomic counter (row ids follow sample
 // order inside a tile, not across tiles: nothing downstream needs more), so
-// no tile waits on another; a single-block pass then hands each tile's
-// leading samples to the row they continue and closes each tile's last row.
+// no tile waits on another; k_row_finish then hands each tile's leading
+// samples to the row they continue and closes each tile's last row.
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;                     // single-block scans below
 
@@ -310,117 +310,49 @@ k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restric
     }
 }
 
-// Single block: the leading samples of tile t belong to the last row of the
-// nearest earlier tile that starts a row; the last row of tile t ends at the
-// first start of the nearest later tile that has one (or at N).
-__global__ void __launch_bounds__(kScanThreads)
-k_scan_fixup(int ntiles, int64_t N, RowScanArgs a) {
-    __shared__ int s_warp[32];
-    __shared__ int s_carry;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    // forward: latest row id (non-negative) strictly before each tile
-    if (threadIdx.x == 0) s_carry = -1;
-    __syncthreads();
-    for (int c0 = 0; c0 < ntiles; c0 += blockDim.x) {
-        const int t = c0 + threadIdx.x;
-        const int4 ti = (t < ntiles) ? a.tile[t] : make_int4(-1, -1, -1, 0);
-        int v = (ti.x >= 0) ? ti.y : -1;               // inclusive "latest row id" scan
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o && v < 0) v = u;
-        }
-        if (lane == 31) s_warp[wid] = v;
-        __syncthreads();
-        if (wid == 0) {
-            int w = (lane < nwarps) ? s_warp[lane] : -1;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o && w < 0) w = u;
-            }
-            s_warp[lane] = w;
-        }
-        __syncthreads();
-        const int carry = s_carry;
-        int before = __shfl_up_sync(0xffffffffu, v, 1);    // exclusive within the warp
-        if (lane == 0) before = -1;
-        if (before < 0 && wid > 0) before = s_warp[wid - 1];
-        if (before < 0) before = carry;
-        if (t < ntiles) {
-            const int2 h = a.head[t];
-            if (h.x != kIntMax && before >= 0 && before < a.cap) {
-                atomicMin(&a.row_min[before], h.x);
-                atomicMax(&a.row_max[before], h.y);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int last = s_warp[nwarps - 1];
-            if (last >= 0) s_carry = last;
-        }
-        __syncthreads();
-    }
-    // backward: first row start strictly after each tile
-    if (threadIdx.x == 0) s_carry = (int)N;
-    __syncthreads();
-    for (int c1 = ntiles; c1 > 0; c1 -= blockDim.x) {
-        const int t = c1 - 1 - threadIdx.x;            // thread order runs backwards over tiles
-        const int4 ti = (t >= 0) ? a.tile[t] : make_int4(-1, -1, -1, 0);
-        int v = (ti.x >= 0) ? ti.z : -1;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o && v < 0) v = u;
-        }
-        if (lane == 31) s_warp[wid] = v;
-        __syncthreads();
-        if (wid == 0) {
-            int w = (lane < nwarps) ? s_warp[lane] : -1;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o && w < 0) w = u;
-            }
-            s_warp[lane] = w;
-        }
-        __syncthreads();
-        const int carry = s_carry;
-        int after = __shfl_up_sync(0xffffffffu, v, 1);
-        if (lane == 0) after = -1;
-        if (after < 0 && wid > 0) after = s_warp[wid - 1];
-        if (after < 0) after = carry;
-        if (t >= 0 && ti.x >= 0 && ti.y < a.cap) a.row_end[ti.y] = after;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int last = s_warp[nwarps - 1];
-            if (last >= 0) s_carry = last;
-        }
-        __syncthreads();
-    }
-}
-
 __global__ void k_fill_int(int n, int v, int* __restrict__ a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
 }
 
-// Per pulse row: x footprint from the cell extent (the row buffer's first
-// fine cell row_clo and its length row_len; a footprint of >= nx cells takes
-// the whole periodic row, row_clo = 0, row_len = nx) and the row's y cell.
-// Puts the extent arrays back to their identities for the next scan.
-// Also the row's w azimuth taps, row_wy[p][s] = phi(s - (w/2 - 1) - fy) (stride 8).
-__global__ void k_row_finish(const int* __restrict__ runs, int cap, int nx, int w, TapPoly tp,
-                             const double* __restrict__ lam_y, const int* __restrict__ row_start,
-                             int* __restrict__ row_min, int* __restrict__ row_max, int* __restrict__ row_clo,
-                             int* __restrict__ row_len, int* __restrict__ row_ly, float* __restrict__ row_fy,
-                             double* __restrict__ row_lam_y, float* __restrict__ row_wy) {
+// Per pulse row: the end of a row that is the last one started in its tile
+// (the first start of the next tile that has one, or N), folding in the
+// leading samples of the tiles up to there; the x footprint from the cell
+// extent (the row buffer's first fine cell row_clo and its length row_len; a
+// footprint of >= nx cells takes the whole periodic row, row_clo = 0,
+// row_len = nx); the row's y cell, its w azimuth taps row_wy[p][s] =
+// phi(s - (w/2 - 1) - fy) (stride 8) and the count of pulse rows reaching
+// each fine row (tap_count, zeroed).  Puts the extent arrays back to their
+// identities for the next scan.  The walk over tiles is O(tiles) in total.
+__global__ void k_row_finish(const int* __restrict__ runs, int cap, int64_t N, int ntiles,
+                             const int4* __restrict__ tile, const int2* __restrict__ head, int nx, int ny, int w,
+                             TapPoly tp, const double* __restrict__ lam_y, const int* __restrict__ row_start,
+                             int* __restrict__ row_end, int* __restrict__ row_min, int* __restrict__ row_max,
+                             int* __restrict__ row_clo, int* __restrict__ row_len, int* __restrict__ row_ly,
+                             float* __restrict__ row_fy, double* __restrict__ row_lam_y, float* __restrict__ row_wy,
+                             int* __restrict__ tap_count) {
     const int P = min(*runs, cap);
     const int h = w / 2;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-        const int mn = row_min[p], mx = row_max[p];
-        row_min[p] = 0x7fffffff;
-        row_max[p] = -0x7fffffff - 1;
+        int mn = row_min[p], mx = row_max[p];
+        row_min[p] = kIntMax;
+        row_max[p] = kIntMin;
+        const int s0 = row_start[p];
+        const int t = s0 / kRowScanTile;
+        if (tile[t].y == p) {
+            int t2 = t + 1;
+            int e = (int)N;
+            for (; t2 < ntiles; ++t2) {
+                const int2 hd = head[t2];
+                mn = min(mn, hd.x);
+                mx = max(mx, hd.y);
+                const int4 ti = tile[t2];
+                if (ti.x >= 0) {
+                    e = ti.z;
+                    break;
+                }
+            }
+            row_end[p] = e;
+        }
         const long long span = (long long)mx - (long long)mn + w;
         if (span >= nx) {
             row_clo[p] = 0;
@@ -429,23 +361,28 @@ __global__ void k_row_finish(const int* __restrict__ runs, int cap, int nx, int 
             row_clo[p] = mn - (h - 1);
             row_len[p] = (int)span;
         }
-        const double ly = lam_y[row_start[p]];
+        const double ly = lam_y[s0];
         int cy;
         float fy;
         fine_coord(ly, cy, fy);
         row_ly[p] = cy;
         row_fy[p] = fy;
         row_lam_y[p] = ly;
-        const float t = 2.0f * fy - 1.0f;
+        const float tt = 2.0f * fy - 1.0f;
 #pragma unroll
-        for (int s = 0; s < 8; ++s) row_wy[(size_t)p * 8 + s] = (s < w) ? tap_eval(tp, s, t) : 0.0f;
+        for (int s = 0; s < 8; ++s) row_wy[(size_t)p * 8 + s] = (s < w) ? tap_eval(tp, s, tt) : 0.0f;
+        for (int s = 0; s < w; ++s) atomicAdd(&tap_count[wrapmod(cy - (h - 1) + s, ny)], 1);
     }
 }
 
-// Row buffer offsets (exclusive scan of row_len, single block, any P), the
-// total cells and the longest row: out[0] = total (int64), out32[0] = max len.
-__global__ void k_row_offsets(const int* __restrict__ runs, int cap, const int* __restrict__ row_len,
-                              int64_t* __restrict__ row_off, long long* __restrict__ total, int* __restrict__ max_len) {
+// Single block, after k_row_finish: row buffer offsets (exclusive scan of
+// row_len over the P rows), their total and the longest row; then the
+// exclusive scan of the per-fine-row tap counts into tap_start[0..ny] and the
+// largest count (atomic max into *max_len and *max_count, zero before).
+__global__ void __launch_bounds__(kScanThreads)
+k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_len, int64_t* __restrict__ row_off,
+            long long* __restrict__ total, int ny, const int* __restrict__ tap_count, int* __restrict__ tap_start,
+            int* __restrict__ max_len, int* __restrict__ max_count) {
     __shared__ int s_warp[32];
     const int P = min(*runs, cap);
     long long carry = 0;
@@ -459,41 +396,27 @@ __global__ void k_row_offsets(const int* __restrict__ runs, int cap, const int* 
         if (i < P) row_off[i] = carry + ex;
         carry += tot;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(max_len, mx);
     if (threadIdx.x == 0) *total = carry;
-}
-
-// Azimuth taps of every pulse row, grouped by the fine row they reach: pulse
-// row p adds phi(t - (w/2 - 1) - fy_p) R_p to fine row ly_p - (w/2 - 1) + t.
-__global__ void k_tap_count(const int* __restrict__ runs, int cap, int ny, int w, const int* __restrict__ row_ly,
-                            int* __restrict__ count) {
-    const int P = min(*runs, cap);
-    const int h = w / 2;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-        for (int t = 0; t < w; ++t) atomicAdd(&count[wrapmod(row_ly[p] - (h - 1) + t, ny)], 1);
-}
-
-// Exclusive scan of n counts into start[0..n] (single block); *max_count =
-// the largest count.
-__global__ void k_scan_counts(int n, const int* __restrict__ count, int* __restrict__ start,
-                              int* __restrict__ max_count) {
-    __shared__ int s_warp[32];
-    int carry = 0, mx = 0;
-    for (int base = 0; base < n; base += kScanThreads) {
+    int c = 0, cmx = 0;
+    for (int base = 0; base < ny; base += kScanThreads) {
         const int i = base + threadIdx.x;
-        const int x = (i < n) ? count[i] : 0;
-        mx = max(mx, x);
+        const int x = (i < ny) ? tap_count[i] : 0;
+        cmx = max(cmx, x);
         int tot;
         const int ex = block_exclusive_scan(x, s_warp, &tot);
-        if (i < n) start[i] = carry + ex;
-        carry += tot;
+        if (i < ny) tap_start[i] = c + ex;
+        c += tot;
     }
-    if (threadIdx.x == 0) start[n] = carry;
+    if (threadIdx.x == 0) tap_start[ny] = c;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(max_count, mx);
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        cmx = max(cmx, __shfl_xor_sync(0xffffffffu, cmx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(max_len, mx);
+        atomicMax(max_count, cmx);
+    }
 }
 
 // Azimuth taps as a table of fixed width per fine row (pulse-row order of

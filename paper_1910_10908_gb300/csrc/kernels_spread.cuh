@@ -26,8 +26,10 @@ constexpr int kSpreadStageBytes = kSpreadStageElems * (int)(sizeof(double) + siz
 // k_spread_rows lists them and k_spread_deferred adds them afterwards.  The
 // FP64 closed form then stays out of the hot kernel (and its registers).
 struct DeferList {
-    int* count;                     // zero before the spread
-    int2* item;                     // [N] (sample, pulse row)
+    int* count;                     // [0] listed samples, [1] finished blocks of k_spread_deferred;
+                                    // both zero before the spread, and left zero by k_spread_deferred
+    int2* item;                     // [cap] (sample, pulse row)
+    int cap;                        // N: every sample is listed at most once per adjoint
 };
 
 // Adjoint, step 1: R_p[c] = sum_{n in row p} D_n v_n phi(c - u_n) over the W
@@ -96,7 +98,8 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
                 float G = g_fitted(cell, f, Mx, wa, exact) * gy;
                 d = (G != 0.0f) ? __frcp_rn(G) : 0.0f;
                 if (exact || !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau))) {
-                    defer.item[atomicAdd(defer.count, 1)] = make_int2((int)(s0 + t0 + i), p);
+                    const int slot = atomicAdd(defer.count, 1);
+                    if (slot < defer.cap) defer.item[slot] = make_int2((int)(s0 + t0 + i), p);
                     continue;
                 }
                 if (d < wa.tau) d = 0.0f;
@@ -157,7 +160,18 @@ k_spread_deferred(RowsView rv, int nx, int Mx, int My, const double* __restrict_
                   const void* __restrict__ values, WeightArgs wa, TapPoly tp, DeferList defer,
                   float2* __restrict__ R) {
     constexpr int H = W / 2;
-    const int count = *defer.count;
+    __shared__ int s_count;
+    if (threadIdx.x == 0) s_count = *(volatile int*)defer.count;
+    __syncthreads();
+    const int count = min(s_count, defer.cap);
+    // the last block to have read the count puts both counters back to zero
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&defer.count[1], 1) == (int)gridDim.x - 1) {
+            defer.count[0] = 0;
+            defer.count[1] = 0;
+        }
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         const int2 e = defer.item[i];
         const int n = e.x, p = e.y;

@@ -55,7 +55,8 @@ struct tffr_plan_s {
     DevBuf<float> deap_x, deap_y;
     DevBuf<int> d_small;                   // [0] error bits, [1] rows, [2] longest row, [3] row overflow,
                                            // [4] most pulse rows reaching one fine row,
-                                           // [5] samples deferred to the FP64 weight decision
+                                           // [5], [6] deferred FP64 weight decisions: listed samples and
+                                           // finished blocks (zero between adjoints)
     DevBuf<int2> defer;                    // [N] deferred (sample, pulse row)
     int* h_small = nullptr;                // pinned read-back: d_small[0..4]; [6..7] the total cells (int64)
     DevBuf<long long> d_big;               // [0] total row-buffer cells
@@ -491,23 +492,20 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     a.flags = p->d_small.ptr;
     k_scan_rows<<<(unsigned)ntiles, kRowScanWarps * 32, 0, p->stream>>>(N, p->lam_x, p->lam_y, a);
     CK_LAUNCH("k_scan_rows");
-    k_scan_fixup<<<1, kScanThreads, 0, p->stream>>>((int)ntiles, N, a);
-    CK_LAUNCH("k_scan_fixup");
     const int* runs = p->d_small.ptr + 1;
-    k_row_finish<<<prow, 256, 0, p->stream>>>(runs, cap, p->nx, w, p->taps, p->lam_y, p->row_start.ptr,
-                                              p->row_min.ptr, p->row_max.ptr, p->row_clo.ptr, p->row_len.ptr,
-                                              p->row_ly.ptr, p->row_fy.ptr, p->row_lam_y.ptr, p->row_wy.ptr);
-    CK_LAUNCH("k_row_finish");
-    k_row_offsets<<<1, kScanThreads, 0, p->stream>>>(runs, cap, p->row_len.ptr, p->row_off.ptr, p->d_big.ptr,
-                                                      p->d_small.ptr + 2);
-    CK_LAUNCH("k_row_offsets");
-    // fine rows reached by each pulse row's azimuth taps: counts (and the
-    // largest, which picks the order of the FFT passes) before the read-back
     CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
-    k_tap_count<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->cursor.ptr);
-    CK_LAUNCH("k_tap_count");
-    k_scan_counts<<<1, kScanThreads, 0, p->stream>>>(ny, p->cursor.ptr, p->tap_start.ptr, p->d_small.ptr + 4);
-    CK_LAUNCH("k_scan_counts");
+    k_row_finish<<<prow, 256, 0, p->stream>>>(runs, cap, N, (int)ntiles, p->tile_info.ptr, p->tile_head.ptr, p->nx,
+                                              ny, w, p->taps, p->lam_y, p->row_start.ptr, p->row_end.ptr,
+                                              p->row_min.ptr, p->row_max.ptr, p->row_clo.ptr, p->row_len.ptr,
+                                              p->row_ly.ptr, p->row_fy.ptr, p->row_lam_y.ptr, p->row_wy.ptr,
+                                              p->cursor.ptr);
+    CK_LAUNCH("k_row_finish");
+    // row buffer offsets, longest row (-> d_small[2]) and the per-fine-row tap
+    // counts with the largest (-> d_small[4], which picks the pass order)
+    k_row_scans<<<1, kScanThreads, 0, p->stream>>>(runs, cap, p->row_len.ptr, p->row_off.ptr, p->d_big.ptr, ny,
+                                                    p->cursor.ptr, p->tap_start.ptr, p->d_small.ptr + 2,
+                                                    p->d_small.ptr + 4);
+    CK_LAUNCH("k_row_scans");
     CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 5 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaMemcpyAsync(p->h_small + 6, p->d_big.ptr, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
@@ -593,7 +591,7 @@ FftTables tables_y(const tffr_plan_s* p) { return FftTables{p->twh_y.ptr, p->twl
 template <typename VT, int W>
 void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values) {
     const size_t smem = (size_t)kSpreadStageBytes + (size_t)p->max_len * sizeof(float2);
-    const DeferList defer{p->d_small.ptr + 5, p->defer.ptr};
+    const DeferList defer{p->d_small.ptr + 5, p->defer.ptr, (int)p->N};
     k_spread_rows<VT, W><<<p->P, kSpreadThreads, smem, p->stream>>>(rv, p->N, p->nx, p->Mx, p->My, p->lam_x, values,
                                                                      p->wargs, p->taps, defer, p->R.ptr);
     if (p->wargs.mode == TFFR_WEIGHTS_TFFR)
@@ -607,7 +605,6 @@ int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
     if (p->layout == TFFR_POINTS_ROWS) {
         const RowsView rv = rows_view(p);
         STAGE_BEGIN(TFFR_STAGE_SPREAD);
-        if (p->wargs.mode == TFFR_WEIGHTS_TFFR) CK(cudaMemsetAsync(p->d_small.ptr + 5, 0, sizeof(int), p->stream));
         switch (p->w) {
             case 2: launch_spread<VT, 2>(p, rv, values); break;
             case 4: launch_spread<VT, 4>(p, rv, values); break;
