@@ -365,6 +365,35 @@ def run_gpu(args, world, rank, local):
     d2h = int(h_img[0].numel() * 8)
     plan_b.close()
 
+    # ---- reduced-precision sample storage (4 B per sample, FP32 arithmetic) ----
+    variants = {}
+    for vt in ("f16", "bf16"):
+        if vt == "f16":
+            v_low = vals.to(torch.complex32)
+        else:
+            v_low = torch.view_as_real(vals).to(torch.bfloat16).contiguous()
+        plan_v = Plan(M, values=vt, device=dev)
+        img_v = torch.empty_like(img)
+
+        def step_v():
+            plan_v.set_points(lx, ly)
+            plan_v.weights(count=False)
+            plan_v.adjoint(v_low, out=img_v)
+
+        for _ in range(3):
+            step_v()
+        kv = max(3, args.steps // 4)
+        torch.cuda.synchronize()
+        ev0.record(plan_v.stream)
+        for _ in range(kv):
+            step_v()
+        ev1.record(plan_v.stream)
+        torch.cuda.synchronize()
+        ms_v = max_over_ranks(ev0.elapsed_time(ev1) / kv, world)
+        variants[vt] = {"value": whole_job_rate(N, world, ms_v), "unit": UNIT, "ms_per_step": ms_v,
+                        "bytes_per_sample_in": 12, "image": img_v}
+        plan_v.close()
+
     line = None
     if rank == 0:
         # sampled accuracy of the timed configuration against the FP64 oracle
@@ -375,6 +404,11 @@ def run_gpu(args, world, rank, local):
         ref = oracle.adjoint_pixels(wl.lam_x, wl.lam_y, wl.values, D, M, M, jx, jy)
         got = img.cpu().numpy()[jy, jx].astype(np.complex128)
         rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        precision = {}
+        for vt, d in variants.items():
+            got_v = d.pop("image").cpu().numpy()[jy, jx].astype(np.complex128)
+            d["rel_l2_vs_fp64_oracle"] = float(np.linalg.norm(got_v - ref) / np.linalg.norm(ref))
+            precision[vt] = d
         base = cpu_baseline(wl, D) if world == 1 else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -393,6 +427,7 @@ def run_gpu(args, world, rank, local):
                                                    for k in ("spread", "row_fft", "col_fft")) * 1e-3),
             "forward": {"value": N / (fwd_ms * 1e-3), "unit": UNIT, "ms": fwd_ms},
             "accuracy": {"rel_l2_vs_fp64_oracle": rel, "pixels": int(jx.shape[0])},
+            "precision_variants": precision,
             "e2e": {"value": whole_job_rate(N, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                     "overlap": "two plans on two streams: one step's copies overlap the other's kernels",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
