@@ -365,6 +365,33 @@ def run_gpu(args, world, rank, local):
     d2h = int(h_img[0].numel() * 8)
     plan_b.close()
 
+    # ---- a batch of 64 uneven sub-aperture patches: eager calls vs one CUDA graph ----
+    from paper_1910_10908_gb300.batched import PatchBatch
+    from synth import patch_batch
+    pb = patch_batch(64)
+    with PatchBatch([(m, m, torch.from_numpy(plx).to(dev), torch.from_numpy(ply).to(dev))
+                     for m, plx, ply, _ in pb]) as batch:
+        for k, (_, _, _, pv) in enumerate(pb):
+            batch.load(k, torch.from_numpy(pv).to(dev))
+        batch.capture()
+        kb = max(3, args.steps // 40)
+        timings = {}
+        for name, run in (("eager", batch.adjoint_eager), ("graph", batch.replay)):
+            run()
+            torch.cuda.synchronize()
+            ev0.record(batch.stream)
+            for _ in range(kb):
+                run()
+            ev1.record(batch.stream)
+            torch.cuda.synchronize()
+            timings[name] = max_over_ranks(ev0.elapsed_time(ev1) / kb, world)
+        batched = {"patches": len(pb), "samples": batch.samples,
+                   "sides": sorted({m for m, _, _, _ in pb}),
+                   "step": "the adjoint of every patch (points and weights set once)",
+                   "eager_ms": timings["eager"], "graph_ms": timings["graph"],
+                   "value": whole_job_rate(batch.samples, world, timings["graph"]), "unit": UNIT}
+    del pb
+
     # ---- reduced-precision sample storage (4 B per sample, FP32 arithmetic) ----
     variants = {}
     for vt in ("f16", "bf16"):
@@ -428,6 +455,7 @@ def run_gpu(args, world, rank, local):
             "forward": {"value": N / (fwd_ms * 1e-3), "unit": UNIT, "ms": fwd_ms},
             "accuracy": {"rel_l2_vs_fp64_oracle": rel, "pixels": int(jx.shape[0])},
             "precision_variants": precision,
+            "batched_patches": batched,
             "e2e": {"value": whole_job_rate(N, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                     "overlap": "two plans on two streams: one step's copies overlap the other's kernels",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -1,0 +1,81 @@
+"""A batch of independent tFFR reconstructions (sub-aperture patches of uneven
+sizes) replayed as one CUDA graph.
+
+Each patch has its own plan; all plans share one stream.  After set_points and
+weights (which synchronise, and may allocate) the per-step work of every patch
+is its adjoint alone, which neither allocates nor synchronises, so the adjoints
+of all patches can be captured once into a CUDA graph on fixed value and image
+buffers and replayed: one graph launch instead of a few kernel launches per
+patch.  New samples are copied into the fixed value buffers between replays.
+"""
+
+from __future__ import annotations
+
+import torch
+
+from . import Plan
+
+
+class PatchBatch:
+    """Plans, fixed value buffers and images for a list of patches.
+
+    patches: list of (Mx, My, lam_x, lam_y) with device float64 coordinates
+    (kept by reference, like Plan.set_points).
+    """
+
+    def __init__(self, patches, *, values: str = "c64", width: int = 6, device=None, **weight_opts):
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.plans, self.values, self.images = [], [], []
+        with torch.cuda.device(self.device), torch.cuda.stream(self.stream):
+            for Mx, My, lx, ly in patches:
+                p = Plan(Mx, My, values=values, width=width, device=self.device)
+                p.set_points(lx, ly)
+                p.weights(count=False, **weight_opts)
+                self.plans.append(p)
+                self.values.append(p.value_tensor())
+                self.images.append(torch.empty((My, Mx), dtype=torch.complex64, device=self.device))
+        self.graph = None
+
+    @property
+    def samples(self) -> int:
+        return sum(p.N for p in self.plans)
+
+    def load(self, k: int, values: torch.Tensor):
+        """Copy patch k's samples into its fixed buffer (ordered on the batch stream)."""
+        with torch.cuda.stream(self.stream):
+            self.values[k].copy_(values, non_blocking=True)
+
+    def adjoint_eager(self):
+        """Every patch's adjoint, one call after the other."""
+        with torch.cuda.stream(self.stream):
+            for p, v, img in zip(self.plans, self.values, self.images):
+                p.adjoint(v, out=img)
+
+    def capture(self):
+        """Record every patch's adjoint into one CUDA graph (once)."""
+        self.adjoint_eager()                       # warm: every kernel has run once
+        self.stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=self.stream):
+            for p, v, img in zip(self.plans, self.values, self.images):
+                p.adjoint(v, out=img)
+        return self
+
+    def replay(self):
+        if self.graph is None:
+            raise RuntimeError("capture() first")
+        with torch.cuda.stream(self.stream):
+            self.graph.replay()
+
+    def close(self):
+        self.graph = None
+        for p in self.plans:
+            p.close()
+        self.plans = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

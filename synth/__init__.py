@@ -12,5 +12,6 @@ from .stripmap import (  # noqa: F401
     scene_samples,
     make_workload,
     random_points,
+    patch_batch,
     WORKLOADS,
 )

@@ -201,3 +201,20 @@ def random_points(N: int, M: int, seed: int, extent: float = 0.45, dtype=np.comp
     lam_y = g.uniform(-extent * M, extent * M, N)
     v = ((g.standard_normal(N) + 1j * g.standard_normal(N)) / np.sqrt(2.0)).astype(dtype)
     return lam_x, lam_y, v
+
+
+def patch_batch(n_patches: int = 64, seed: int = 191010908 + 5, sides=(256, 512, 1024),
+                pulses=(128, 1024), freqs=(256, 2048)):
+    """Uneven sub-aperture patches: per patch n_pulses ~ U{pulses}, n_freq ~ U{freqs}
+    and an image side drawn from `sides`, Stolt coordinates and CN(0,1) samples.
+    Returns a list of (M, lam_x, lam_y, values)."""
+    g = np.random.default_rng(np.random.SeedSequence(seed))
+    out = []
+    for _ in range(n_patches):
+        P = int(g.integers(pulses[0], pulses[1] + 1))
+        F = int(g.integers(freqs[0], freqs[1] + 1))
+        M = int(sides[int(g.integers(0, len(sides)))])
+        lx, ly, _ = stolt_points(P, F, M)
+        v = ((g.standard_normal(lx.shape[0]) + 1j * g.standard_normal(lx.shape[0])) / np.sqrt(2.0)).astype(np.complex64)
+        out.append((M, lx, ly, v))
+    return out
