@@ -210,25 +210,30 @@ k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restric
     int cx[kRowScanK];
     bool bad_x = false, bad_y = false;
     int cnt = 0;
-    long long prev = (wbase > 0 && wbase <= N) ? __double_as_longlong(__ldg(&lam_y[wbase - 1])) : 0;
+    // 32-bit offsets from the warp's first sample; rem = samples left from there
+    const int64_t left = N - wbase;
+    const int rem = left <= 0 ? 0 : (left >= 32 * kRowScanK ? 32 * kRowScanK : (int)left);
+    const double* __restrict__ wy = lam_y + wbase;
+    const double* __restrict__ wx = lam_x + wbase;
+    long long prev = (wbase > 0 && rem > 0) ? __double_as_longlong(__ldg(wy - 1)) : 0;
 #pragma unroll
     for (int h = 0; h < kRowScanK; h += 8) {
         long long yb[8];
         double xv[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const int64_t n = wbase + (h + k) * 32 + lane;
-            yb[k] = (n < N) ? __double_as_longlong(__ldg(&lam_y[n])) : 0;
-            xv[k] = (n < N) ? __ldg(&lam_x[n]) : 0.0;
+            const int o = (h + k) * 32 + lane;
+            yb[k] = (o < rem) ? __double_as_longlong(__ldg(wy + o)) : 0;
+            xv[k] = (o < rem) ? __ldg(wx + o) : 0.0;
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const int64_t n = wbase + (h + k) * 32 + lane;
+            const int o = (h + k) * 32 + lane;
             long long up = __shfl_up_sync(FULL, yb[k], 1);
             if (lane == 0) up = prev;
             prev = __shfl_sync(FULL, yb[k], 31);
-            const bool in = n < N;
-            ball[h + k] = __ballot_sync(FULL, in && (n == 0 || yb[k] != up));
+            const bool in = o < rem;
+            ball[h + k] = __ballot_sync(FULL, in && ((wbase == 0 && o == 0) || yb[k] != up));
             cnt += __popc(ball[h + k]);
             int c = 0;
             if (in) {
@@ -270,19 +275,21 @@ k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restric
             over = true;
         }
     };
+    const int nbase = (int)wbase;                      // N < 2^31
 #pragma unroll
     for (int k = 0; k < kRowScanK; ++k) {
-        const int64_t n = wbase + k * 32 + lane;
+        const int o = k * 32 + lane;
+        const int n = nbase + o;
         const int local = pre + __popc(ball[k] & le) - 1;
-        if (n < N) {
+        if (o < rem) {
             if ((ball[k] >> lane) & 1u) {
                 const int p = base + local;
-                if (p < a.cap) a.row_start[p] = (int)n;
+                if (p < a.cap) a.row_start[p] = n;
                 else over = true;
                 if (local > 0) {
-                    if (p - 1 < a.cap) a.row_end[p - 1] = (int)n;
+                    if (p - 1 < a.cap) a.row_end[p - 1] = n;
                 } else {
-                    s_first = (int)n;
+                    s_first = n;
                 }
             }
             if (local != cur) {
