@@ -286,6 +286,20 @@ __device__ __forceinline__ void fft_line_epilogue_regs(float2 (&v)[Line<LOGN>::V
         for (int r = 0; r < R; ++r) epi(threadIdx.x + b * L::T + r * (L::N / R), v[b * R + r]);
 }
 
+// As fft_line_smem, with the first stage's input in registers, v[r] =
+// x[tid + r T] (the layout the first stage loads); buf is free to be
+// overwritten when this is called.  The result is in buf, natural order.
+template <int LOGN, int SGN>
+__device__ __forceinline__ void fft_line_regs(float2 (&v)[Line<LOGN>::V], float2* buf, const Twiddles& tw) {
+    using L = Line<LOGN>;
+    static_assert(L::NFULL >= 1, "needs a radix-V first stage");
+    stage_compute<LOGN, L::V, 0, SGN>(v, tw);
+    stage_store<LOGN, L::V, 0>(v, buf);
+    __syncthreads();
+    FullStages<LOGN, 1, L::NFULL, SGN>::run(buf, tw);
+    if constexpr (L::REM > 0) stage_smem<LOGN, (1 << L::REM), L::NFULL * L::LV, SGN>(buf, tw);
+}
+
 // Load the twiddle tables of an N-point line into shared memory: the two
 // levels for any exponent and the direct table of the NT-th roots.
 template <int LOGN>

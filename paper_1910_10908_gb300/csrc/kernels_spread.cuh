@@ -212,8 +212,8 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
     bool gy_exact = false;
     const double lam_y_row = rv.row_lam_y[p];
     if (apply_weights && wa.mode == 0 && wa.separable) gy = g_fitted(rv.row_ly[p], rv.row_fy[p], My, wa, gy_exact);
-    for (int64_t n = s0 + threadIdx.x; n < s1; n += blockDim.x) {
-        const double lam = lam_x[n];
+    // y_n for one sample of this row
+    auto interp = [&](int64_t n, double lam) -> float2 {
         int cell;
         float f;
         fine_coord(lam, cell, f);
@@ -242,7 +242,19 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
                     d = 0.0f;
             }
         }
-        ValueIO<VT>::store(out, n, cscale(acc, d));
+        return cscale(acc, d);
+    };
+    // two samples per thread and round: two independent chains of loads
+    const int64_t step = blockDim.x;
+    for (int64_t n = s0 + threadIdx.x; n < s1; n += 2 * step) {
+        const int64_t n1 = n + step;
+        const bool two = n1 < s1;
+        const double lam0 = lam_x[n];
+        const double lam1 = two ? lam_x[n1] : lam0;
+        const float2 y0 = interp(n, lam0);
+        const float2 y1 = interp(two ? n1 : n, lam1);
+        ValueIO<VT>::store(out, n, y0);
+        if (two) ValueIO<VT>::store(out, n1, y1);
     }
 }
 

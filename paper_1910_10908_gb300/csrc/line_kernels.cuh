@@ -589,10 +589,19 @@ k_fwd_rows_pulse(RowsView rv, const float2* __restrict__ F, FftTables tab, float
     const int p = blockIdx.x;
     const int tid = threadIdx.x;
     const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
-    for (int i = MX / 2 + tid; i < NX - MX / 2; i += L::T) S.buf[L::pad(i)] = make_float2(0.f, 0.f);
-    for (int jx = tid; jx < MX; jx += L::T) S.buf[L::pad(wrapmod(jx - MX / 2, NX))] = F[(size_t)p * MX + jx];
-    __syncthreads();
-    fft_line_smem<LOGN, -1>(S.buf, tw);
+    // line position j holds mode j (j < MX/2) or j - NX (j >= NX - MX/2), i.e.
+    // F column j + MX/2 or j - (NX - MX/2); the middle is zero.  Loaded straight
+    // into the first FFT stage's registers (position tid + u T).
+    float2 v[L::V];
+    const float2* Fp = F + (size_t)p * MX;
+#pragma unroll
+    for (int u = 0; u < L::V; ++u) {
+        const int j = tid + u * L::T;
+        v[u] = (j < MX / 2) ? __ldg(&Fp[j + MX / 2])
+             : (j >= NX - MX / 2) ? __ldg(&Fp[j - (NX - MX / 2)]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();                                   // twiddles in place
+    fft_line_regs<LOGN, -1>(v, S.buf, tw);
     const int len = rv.row_len[p], clo = rv.row_clo[p];
     float2* Rp = R + rv.row_off[p];
     for (int i = tid; i < len; i += L::T) Rp[i] = S.buf[L::pad(wrapmod(clo + i, NX))];
