@@ -393,14 +393,19 @@ k_adj_rows_pulse(RowsView rv, const float2* __restrict__ R, FftTables tab, const
     const int p = blockIdx.x;
     const int tid = threadIdx.x;
     const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
-    for (int i = tid; i < L::PADLEN; i += L::T) S.buf[i] = make_float2(0.f, 0.f);
-    __syncthreads();
+    // line cell j holds R_p[(j - clo) mod NX] when that is below len, else 0;
+    // read straight into the first FFT stage's registers (cell tid + u T)
     const int len = rv.row_len[p], clo = rv.row_clo[p];
     const float2* Rp = R + rv.row_off[p];
-    for (int i = tid; i < len; i += L::T) S.buf[L::pad(wrapmod(clo + i, NX))] = __ldg(&Rp[i]);
-    __syncthreads();
+    float2 v[L::V];
+#pragma unroll
+    for (int u = 0; u < L::V; ++u) {
+        const int o = wrapmod(tid + u * L::T - clo, NX);
+        v[u] = (o < len) ? __ldg(&Rp[o]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();                                   // twiddles in place
     RowOut<LOGN> epi{p, deap_x, F};
-    fft_line_epilogue<LOGN, +1>(S.buf, tw, epi);
+    fft_line_epilogue_regs<LOGN, +1>(v, S.buf, tw, epi);
 }
 
 constexpr int kPulseBatch = 4;                         // pulse rows whose taps are loaded together
