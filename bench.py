@@ -38,7 +38,7 @@ WORKLOAD = "stripmap_4096"
 # kernel on this workload, from one ncu capture of that kernel; an entry is removed
 # when its kernel changes, and a stage without one reports null.
 DRAM_TRAFFIC = {
-    ("col_fft", "pulse_rows"): 232_713_472,     # k_adj_cols_pulse<13>
+    ("col_fft", "pulse_rows"): 233_193_728,     # k_adj_cols_pulse<13>
 }
 
 
@@ -392,6 +392,51 @@ def run_gpu(args, world, rank, local):
                    "value": whole_job_rate(batch.samples, world, timings["graph"]), "unit": UNIT}
     del pb
 
+    # ---- normal operator E^H D E on the 2048^2 workload: Toeplitz vs forward + adjoint ----
+    wl2 = make_workload("stripmap_2048", values=False)
+    M2 = wl2.M
+    plan_n = Plan(M2, values="c64", device=dev)
+    plan_n.set_points(torch.from_numpy(wl2.lam_x).to(dev), torch.from_numpy(wl2.lam_y).to(dev))
+    plan_n.weights(count=False)
+    t0 = time.perf_counter()
+    plan_n.normal_setup()
+    setup_s = time.perf_counter() - t0
+    f_n = torch.randn((M2, M2), dtype=torch.complex64, device=dev)
+    g_n = torch.empty_like(f_n)
+    y_n = torch.empty(wl2.N, dtype=torch.complex64, device=dev)
+
+    def via_samples():
+        plan_n.forward(f_n, out=y_n, apply_weights=False)
+        plan_n.adjoint(y_n, out=g_n)
+
+    kn = max(3, args.steps // 40)
+
+    def time_normal():
+        out = {}
+        for name, run in (("toeplitz_ms", lambda: plan_n.normal(f_n, out=g_n)), ("forward_adjoint_ms", via_samples)):
+            run()
+            torch.cuda.synchronize()
+            ev0.record(plan_n.stream)
+            for _ in range(kn):
+                run()
+            ev1.record(plan_n.stream)
+            torch.cuda.synchronize()
+            out[name] = max_over_ranks(ev0.elapsed_time(ev1) / kn, world)
+        return out
+
+    normal = {"stripmap_2048": {"N": wl2.N, "image": "%dx%d" % (M2, M2), "setup_s": setup_s, **time_normal()}}
+    del wl2
+    # denser sampling: the 4096 x 4096 pulse/frequency grid on the same 2048^2 image
+    from synth import stolt_points
+    dlx, dly, _ = stolt_points(4096, 4096, M2)
+    plan_n.set_points(torch.from_numpy(dlx).to(dev), torch.from_numpy(dly).to(dev))
+    plan_n.weights(count=False)
+    y_n = torch.empty(dlx.shape[0], dtype=torch.complex64, device=dev)
+    plan_n.normal_setup()
+    normal["stolt_4096x4096_on_2048"] = {"N": int(dlx.shape[0]), "image": "%dx%d" % (M2, M2), **time_normal()}
+    plan_n.close()
+    del dlx, dly
+
     # ---- reduced-precision sample storage (4 B per sample, FP32 arithmetic) ----
     variants = {}
     for vt in ("f16", "bf16"):
@@ -456,6 +501,7 @@ def run_gpu(args, world, rank, local):
             "accuracy": {"rel_l2_vs_fp64_oracle": rel, "pixels": int(jx.shape[0])},
             "precision_variants": precision,
             "batched_patches": batched,
+            "normal_operator": normal,
             "e2e": {"value": whole_job_rate(N, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                     "overlap": "two plans on two streams: one step's copies overlap the other's kernels",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

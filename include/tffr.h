@@ -239,6 +239,31 @@ int tffr_profile_read(tffr_plan_t plan, double* ms, int64_t* count, int nstages)
 int tffr_weights_noalloc(int64_t N, const double* lam_x, const double* lam_y, int Mx, int My,
                          const tffr_weight_opts* opts, float* D_out, int64_t* n_kept, tffr_stream_t stream);
 
+/*
+ * Normal operator of the weighted least-squares image, N = E^H D E, where
+ * E[n, j] = exp(-2 pi i lam_n . x_j) and D the plan's weights: tffr_adjoint
+ * computes the one-step tFFR image E^H D y (Eq. (fstraight) with alpha_n = D_n),
+ * and iterating with N (conjugate gradients on N f = E^H D y) refines it.  N is
+ * the convolution of the image with k(m) = sum_n D_n exp(2 pi i lam_n . m / M)
+ * (Toeplitz), applied as crop(IFFT2(Khat . FFT2(zero-padded f))) on the
+ * 2 My x 2 Mx grid: three passes of line FFTs, independent of N.
+ *
+ * tffr_normal_setup builds Khat (4 Mx My complex64, owned by the plan) for
+ * the current points and weights, through a temporary plan of sides 2 Mx,
+ * 2 My (so Mx, My <= 2048); it allocates, synchronises the stream, and must
+ * be called again after tffr_set_points or tffr_weights.
+ * Errors: NOT_READY before points and weights; INVALID_ARG for Mx or My > 2048;
+ * OOM; CUDA.
+ */
+int tffr_normal_setup(tffr_plan_t plan);
+
+/*
+ * image_out = N image_in, both device complex64 [My][Mx], row-major; they may
+ * be the same array.  Ordered on the plan's stream, no synchronisation.
+ * Errors: NOT_READY before tffr_normal_setup; INVALID_ARG for NULL pointers; CUDA.
+ */
+int tffr_normal_apply(tffr_plan_t plan, const void* image_in, void* image_out);
+
 /* Query sizes and the state of a plan. */
 int tffr_plan_get_info(tffr_plan_t plan, tffr_plan_info* info);
 

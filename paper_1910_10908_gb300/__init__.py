@@ -119,6 +119,15 @@ def tffr_forward(plan, image: torch.Tensor, values: torch.Tensor, apply_weights:
            plan)
 
 
+def tffr_normal_setup(plan):
+    _check(_abi.load().tffr_normal_setup(plan), plan)
+
+
+def tffr_normal_apply(plan, image_in: torch.Tensor, image_out: torch.Tensor):
+    _check(_abi.load().tffr_normal_apply(plan, _dev(image_in, "image_in", torch.complex64),
+                                         _dev(image_out, "image_out", torch.complex64)), plan)
+
+
 def tffr_weights_noalloc(lam_x: torch.Tensor, lam_y: torch.Tensor, Mx: int, My: int, D_out: torch.Tensor, *,
                          mode: str = "tffr", separable: bool = False, a: float = 0.01, q: float = 3.0,
                          tau: float = 0.97, user_D: torch.Tensor | None = None, count: bool = True, stream=None):
@@ -224,6 +233,18 @@ class Plan:
             dt = torch.complex128 if self.values == "c128" else torch.complex64
             out = torch.empty(self.N or 0, dtype=dt, device=self.device)
         tffr_forward(self._handle(), image, out, apply_weights)
+        return out
+
+    def normal_setup(self) -> "Plan":
+        """Build the Toeplitz normal operator E^H D E for the current points and weights."""
+        tffr_normal_setup(self._handle())
+        return self
+
+    def normal(self, image: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """E^H D E image (after normal_setup)."""
+        if out is None:
+            out = torch.empty((self.My, self.Mx), dtype=torch.complex64, device=self.device)
+        tffr_normal_apply(self._handle(), image, out)
         return out
 
     def info(self) -> dict:

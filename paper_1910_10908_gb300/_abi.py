@@ -59,6 +59,8 @@ SIGNATURES = {
     "tffr_weights_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_int, ctypes.POINTER(tffr_weight_opts), ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
+    "tffr_normal_setup": (ctypes.c_int, [ctypes.c_void_p]),
+    "tffr_normal_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tffr_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tffr_plan_info)]),
     "tffr_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "tffr_error_string": (ctypes.c_char_p, [ctypes.c_int]),

@@ -32,6 +32,9 @@ cudaError_t attrs_for() {
     if (e == cudaSuccess) e = smem_attr(k_fwd_rows_pulse<LOGN>, b);
     if (e == cudaSuccess) e = smem_attr(k_adj_cols_pulse<LOGN>, line_smem_pulse_cols<LOGN>());
     if (e == cudaSuccess) e = smem_attr(k_fwd_cols_pulse<LOGN>, line_smem_pulse_cols<LOGN>());
+    if (e == cudaSuccess) e = smem_attr(k_fft_rows<LOGN, -1>, b);
+    if (e == cudaSuccess) e = smem_attr(k_fft_rows<LOGN, +1>, b);
+    if (e == cudaSuccess) e = smem_attr(k_fft_cols_conv<LOGN>, b);
     return e;
 }
 
@@ -127,6 +130,26 @@ void launch_fwd_rows_pulse(int lognx, int P, cudaStream_t s, const RowsView& rv,
                            float2* R) {
 #define L(LG) k_fwd_rows_pulse<LG><<<P, Line<LG>::T, line_smem<LG>(), s>>>(rv, F, tab, R)
     TFFR_LOGN_SWITCH(lognx, L)
+#undef L
+}
+
+void launch_fft_rows(int logn, int sgn, int rows, cudaStream_t s, const float2* in, int ld_in, int n_in,
+                     FftTables tab, float2* out, int ld_out, int n_out) {
+    if (sgn < 0) {
+#define L(LG) k_fft_rows<LG, -1><<<rows, Line<LG>::T, line_smem<LG>(), s>>>(in, ld_in, n_in, tab, out, ld_out, n_out)
+        TFFR_LOGN_SWITCH(logn, L)
+#undef L
+    } else {
+#define L(LG) k_fft_rows<LG, +1><<<rows, Line<LG>::T, line_smem<LG>(), s>>>(in, ld_in, n_in, tab, out, ld_out, n_out)
+        TFFR_LOGN_SWITCH(logn, L)
+#undef L
+    }
+}
+
+void launch_fft_cols_conv(int logn, int cols, cudaStream_t s, const float2* in, int n_in, int ld, FftTables tab,
+                          const float2* khat, float scale, float2* out, int n_out) {
+#define L(LG) k_fft_cols_conv<LG><<<cols, Line<LG>::T, line_smem<LG>(), s>>>(in, n_in, ld, tab, khat, scale, out, n_out)
+    TFFR_LOGN_SWITCH(logn, L)
 #undef L
 }
 

@@ -612,4 +612,113 @@ k_fwd_rows_pulse(RowsView rv, const float2* __restrict__ F, FftTables tab, float
     for (int i = tid; i < len; i += L::T) Rp[i] = S.buf[L::pad(wrapmod(clo + i, NX))];
 }
 
+// ---------------------------------------------------------------------------
+// Normal operator E^H D E by its Toeplitz embedding.  On the image grid
+// (E^H D E f)[j] = sum_j' k(j - j') f[j'] with k(m) = sum_n D_n exp(2 pi i
+// lam_n . m / M), m in (-M, M)^2: a convolution, computed on the 2M x 2M grid
+// as crop(IFFT2(Khat . FFT2(pad(f)))) with Khat = FFT2 of k arranged
+// circularly (built once).  Lines here are full 2M-point transforms.
+// ---------------------------------------------------------------------------
+
+// One row per CTA: in[r][0..n_in) (zero beyond) -> FFT_{SGN} -> out[r][0..n_out).
+template <int LOGN, int SGN>
+__global__ void __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_fft_rows(const float2* __restrict__ in, int ld_in, int n_in, FftTables tab, float2* __restrict__ out, int ld_out,
+           int n_out) {
+    using L = Line<LOGN>;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    const int r = blockIdx.x;
+    const int tid = threadIdx.x;
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
+    const float2* row = in + (size_t)r * ld_in;
+    float2 v[L::V];
+#pragma unroll
+    for (int u = 0; u < L::V; ++u) {
+        const int j = tid + u * L::T;
+        v[u] = (j < n_in) ? __ldg(&row[j]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();                                   // twiddles in place
+    fft_line_regs<LOGN, SGN>(v, S.buf, tw);
+    float2* o = out + (size_t)r * ld_out;
+    for (int k = tid; k < n_out; k += L::T) o[k] = S.buf[L::pad(k)];
+}
+
+// Clusters of 4 CTAs, one column each, over a row-major array with ld columns:
+// column rows [0, n_in) (zero beyond) -> FFT_-.  With khat (column-major,
+// khat[col][ky]): times khat, then FFT_+ and rows [0, n_out) out (row-major,
+// ld columns).  Without: times (-1)^(ky + col) scale (the circular arrangement
+// of k and the inverse's normalisation), stored column-major: out[col][ky].
+template <int LOGN>
+__global__ void __cluster_dims__(kColCluster, 1, 1) __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
+k_fft_cols_conv(const float2* __restrict__ in, int n_in, int ld, FftTables tab, const float2* __restrict__ khat,
+                float scale, float2* __restrict__ out, int n_out) {
+    using L = Line<LOGN>;
+    constexpr int NY = L::N;
+    extern __shared__ float2 smem[];
+    LineSmem<LOGN> S(smem);
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int jx0 = (int)blockIdx.x - rank;
+    const int col = jx0 + rank;
+    const int tid = threadIdx.x;
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
+    for (int i = n_in + tid; i < NY; i += L::T) S.buf[L::pad(i)] = make_float2(0.f, 0.f);
+    static_assert(L::T % kColCluster == 0, "line threads must be a multiple of the cluster size");
+    float2* const peer = cluster.map_shared_rank(S.buf, tid % kColCluster);
+    // scatter: this CTA reads rows [r0, r1) of the 4 columns (32-byte chunks)
+    const int RQ = (n_in + kColCluster - 1) / kColCluster;
+    const int r0 = min(n_in, rank * RQ), nel = (min(n_in, r0 + RQ) - r0) * kColCluster;
+    cluster_arrive_relaxed();                          // every CTA runs before its memory is written
+    cluster_wait();
+    for (int base = 0; base < nel; base += L::V * L::T) {
+        float2 tmp[L::V];
+#pragma unroll
+        for (int u = 0; u < L::V; ++u) {
+            const int i = base + tid + u * L::T;
+            tmp[u] = (i < nel) ? __ldg(&in[(size_t)(r0 + i / kColCluster) * ld + jx0 + i % kColCluster])
+                               : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < L::V; ++u) {
+            const int i = base + tid + u * L::T;
+            if (i < nel) peer[L::pad(r0 + i / kColCluster)] = tmp[u];
+        }
+    }
+    cluster.sync();
+    fft_line_smem<LOGN, -1>(S.buf, tw);
+    if (!khat) {
+        float2* o = out + (size_t)col * NY;
+        for (int k = tid; k < NY; k += L::T) o[k] = cscale(S.buf[L::pad(k)], ((k + col) & 1) ? -scale : scale);
+        cluster_arrive_relaxed();                      // no remote access after the scatter barrier
+        cluster_wait();
+        return;
+    }
+    {
+        const float2* kc = khat + (size_t)col * NY;
+        for (int k = tid; k < NY; k += L::T) S.buf[L::pad(k)] = cmul(S.buf[L::pad(k)], __ldg(&kc[k]));
+        __syncthreads();
+        fft_line_smem<LOGN, +1>(S.buf, tw);
+    }
+    cluster.sync();
+    // gather: this CTA stores rows [o0, o1) of the 4 columns
+    const int OQ = (n_out + kColCluster - 1) / kColCluster;
+    const int o0 = min(n_out, rank * OQ), nout = (min(n_out, o0 + OQ) - o0) * kColCluster;
+    for (int base = 0; base < nout; base += L::V * L::T) {
+        float2 tmp[L::V];
+#pragma unroll
+        for (int u = 0; u < L::V; ++u) {
+            const int i = base + tid + u * L::T;
+            tmp[u] = (i < nout) ? peer[L::pad(o0 + i / kColCluster)] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < L::V; ++u) {
+            const int i = base + tid + u * L::T;
+            if (i < nout) out[(size_t)(o0 + i / kColCluster) * ld + jx0 + i % kColCluster] = tmp[u];
+        }
+    }
+    cluster_arrive_relaxed();                          // every remote load was consumed above
+    cluster_wait();
+}
+
 }  // namespace tffr

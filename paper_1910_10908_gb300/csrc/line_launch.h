@@ -38,4 +38,10 @@ void launch_fwd_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float
 void launch_fwd_rows_pulse(int lognx, int P, cudaStream_t s, const RowsView& rv, const float2* F, FftTables tab,
                            float2* R);
 
+// Toeplitz normal operator: full line transforms (see line_kernels.cuh).
+void launch_fft_rows(int logn, int sgn, int rows, cudaStream_t s, const float2* in, int ld_in, int n_in,
+                     FftTables tab, float2* out, int ld_out, int n_out);
+void launch_fft_cols_conv(int logn, int cols, cudaStream_t s, const float2* in, int n_in, int ld, FftTables tab,
+                          const float2* khat, float scale, float2* out, int n_out);
+
 }  // namespace tffr

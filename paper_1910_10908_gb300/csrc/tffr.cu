@@ -67,6 +67,8 @@ struct tffr_plan_s {
     const double* lam_x = nullptr;
     const double* lam_y = nullptr;
     bool have_points = false, have_weights = false;
+    bool normal_ready = false;             // Khat of the Toeplitz normal operator built for these points/weights
+    DevBuf<float2> khat, nwork1, nwork2;   // Khat column-major [2Mx][2My]; two [My][2Mx] work arrays
     int layout = 0;
     int64_t n_kept = -1;
     DevBuf<float> D;                       // per-sample weights when materialised
@@ -889,6 +891,7 @@ int tffr_destroy(tffr_plan_t p) {
     release(p->T); release(p->deap_x); release(p->deap_y);
     release(p->d_small); release(p->d_kept); release(p->d_big); release(p->D);
     release(p->tile_info); release(p->tile_head); release(p->defer);
+    release(p->khat); release(p->nwork1); release(p->nwork2);
     if (p->h_small) cudaFreeHost(p->h_small);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly);
     release(p->row_min); release(p->row_max); release(p->row_end); release(p->row_wy);
@@ -957,6 +960,7 @@ int tffr_set_points(tffr_plan_t p, int64_t N, const double* lam_x, const double*
     if (N > 0 && (!lam_x || !lam_y)) return fail(p, TFFR_ERR_INVALID_ARG, "NULL coordinates");
     p->have_points = false;
     p->have_weights = false;
+    p->normal_ready = false;
     p->n_kept = -1;
     p->N = N;
     p->lam_x = lam_x;
@@ -1008,6 +1012,7 @@ int tffr_weights(tffr_plan_t p, const tffr_weight_opts* opts, float* D_out, int6
     if (o.mode == TFFR_WEIGHTS_USER && !o.user_D && p->N > 0) return fail(p, TFFR_ERR_INVALID_ARG, "user_D");
     const int64_t N = p->N;
     p->have_weights = false;
+    p->normal_ready = false;
     p->n_kept = -1;
     WeightArgs& A = p->wargs;
     std::memset(&A, 0, sizeof(A));
@@ -1093,6 +1098,126 @@ int tffr_forward(tffr_plan_t p, const void* image, void* values, int apply_weigh
         case TFFR_VALUES_C128: return forward_impl<double2>(p, img, values, apply_weights);
         default: return forward_impl<float2>(p, img, values, apply_weights);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Toeplitz normal operator
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_normal_inputs(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y,
+                                double* __restrict__ lx2, double* __restrict__ ly2, float2* __restrict__ ones) {
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        lx2[n] = 2.0 * lam_x[n];
+        ly2[n] = 2.0 * lam_y[n];
+        ones[n] = make_float2(1.0f, 0.0f);
+    }
+}
+
+// k(m) for m in [-M, M)^2 (per axis) as the image of a plan with twice the
+// sides, coordinates 2 lam, unit samples and this plan's weights D (user
+// weights there): that plan's pixel j sits at (j - M) / (2M), and 2 lam times
+// it is lam (j - M) / M, so pixel j holds k(j - M).
+int normal_kernel_image(tffr_plan_s* p, float2* g) {
+    const int64_t N = p->N;
+    DevBuf<double> lx2, ly2;
+    DevBuf<float2> ones;
+    tffr_plan_t q = nullptr;
+    int s = TFFR_OK;
+    auto cleanup = [&]() {                              // temporaries: not counted in the plan's bytes
+        if (q) tffr_destroy(q);
+        cudaStreamSynchronize(p->stream);
+        p->device_bytes -= (size_t)lx2.cap * sizeof(double) + (size_t)ly2.cap * sizeof(double) +
+                           (size_t)ones.cap * sizeof(float2);
+        release(lx2); release(ly2); release(ones);
+    };
+    cudaError_t e = grow(p, lx2, N);
+    if (e == cudaSuccess) e = grow(p, ly2, N);
+    if (e == cudaSuccess) e = grow(p, ones, N);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(p, e, "tffr_normal_setup: allocation");
+    }
+    k_normal_inputs<<<grid_for(N, 256), 256, 0, p->stream>>>(N, p->lam_x, p->lam_y, lx2.ptr, ly2.ptr, ones.ptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(p, e, "k_normal_inputs");
+    }
+    tffr_opts o;
+    tffr_default_opts(&o);
+    o.width = p->w;
+    o.beta = p->beta;
+    o.values = TFFR_VALUES_C64;
+    o.layout = p->layout_hint;
+    s = tffr_plan(&q, 2 * p->Mx, 2 * p->My, &o, p->stream);
+    if (s == TFFR_OK) s = tffr_set_points(q, N, lx2.ptr, ly2.ptr);
+    if (s == TFFR_OK) {
+        tffr_weight_opts wo;
+        tffr_default_weight_opts(&wo);
+        wo.mode = TFFR_WEIGHTS_USER;
+        wo.user_D = p->D.ptr;
+        s = tffr_weights(q, &wo, nullptr, nullptr);
+    }
+    if (s == TFFR_OK) s = tffr_adjoint(q, ones.ptr, g);
+    if (s != TFFR_OK && q) p->last_error = std::string("tffr_normal_setup: ") + tffr_last_error(q);
+    cleanup();
+    return s;
+}
+
+}  // namespace
+
+int tffr_normal_setup(tffr_plan_t p) {
+    if (!p) return TFFR_ERR_INVALID_ARG;
+    p->last_error.clear();
+    if (!p->have_points || !p->have_weights) return fail(p, TFFR_ERR_NOT_READY, "normal setup before points/weights");
+    if (4 * p->Mx > kFftNMax || 4 * p->My > kFftNMax)
+        return fail(p, TFFR_ERR_INVALID_ARG, "the Toeplitz embedding needs Mx, My <= 2048");
+    p->normal_ready = false;
+    const int64_t N = p->N;
+    const int Mx2 = 2 * p->Mx, My2 = 2 * p->My;
+    CK(grow(p, p->khat, (int64_t)Mx2 * My2));
+    CK(grow(p, p->nwork1, (int64_t)Mx2 * My2));       // Khat build: all 2My rows; apply: My rows
+    CK(grow(p, p->nwork2, (int64_t)Mx2 * p->My));
+    if (N == 0) {
+        CK(cudaMemsetAsync(p->khat.ptr, 0, (size_t)Mx2 * My2 * sizeof(float2), p->stream));
+    } else {
+        // D_n in sample order (for USER weights already in p->D)
+        CK(grow(p, p->D, N));
+        CK(cudaMemsetAsync(p->d_kept.ptr, 0, sizeof(unsigned long long), p->stream));
+        k_weights<<<grid_for(N, 256), 256, 0, p->stream>>>(N, p->lam_x, p->lam_y, p->Mx, p->My, p->wargs, p->D.ptr,
+                                                          p->d_kept.ptr);
+        CK_LAUNCH("k_weights");
+        const int s = normal_kernel_image(p, p->khat.ptr);   // k first, transformed in place below
+        if (s != TFFR_OK) return s;
+        // Khat = FFT2 of k arranged circularly ((-1)^(kx+ky) in frequency) / (4 Mx My)
+        launch_fft_rows(p->lognx, -1, My2, p->stream, p->khat.ptr, Mx2, Mx2, tables_x(p), p->nwork1.ptr, Mx2, Mx2);
+        CK_LAUNCH("k_fft_rows");
+        launch_fft_cols_conv(p->logny, Mx2, p->stream, p->nwork1.ptr, My2, Mx2, tables_y(p), nullptr,
+                             1.0f / ((float)Mx2 * (float)My2), p->khat.ptr, My2);
+        CK_LAUNCH("k_fft_cols_conv");
+    }
+    CK(cudaStreamSynchronize(p->stream));
+    p->normal_ready = true;
+    return TFFR_OK;
+}
+
+int tffr_normal_apply(tffr_plan_t p, const void* image_in, void* image_out) {
+    if (!p) return TFFR_ERR_INVALID_ARG;
+    p->last_error.clear();
+    if (!p->normal_ready) return fail(p, TFFR_ERR_NOT_READY, "tffr_normal_apply before tffr_normal_setup");
+    if (!image_in || !image_out) return fail(p, TFFR_ERR_INVALID_ARG, "NULL pointer");
+    const int Mx2 = 2 * p->Mx;
+    launch_fft_rows(p->lognx, -1, p->My, p->stream, reinterpret_cast<const float2*>(image_in), p->Mx, p->Mx,
+                    tables_x(p), p->nwork1.ptr, Mx2, Mx2);
+    CK_LAUNCH("k_fft_rows");
+    launch_fft_cols_conv(p->logny, Mx2, p->stream, p->nwork1.ptr, p->My, Mx2, tables_y(p), p->khat.ptr, 0.0f,
+                         p->nwork2.ptr, p->My);
+    CK_LAUNCH("k_fft_cols_conv");
+    launch_fft_rows(p->lognx, +1, p->My, p->stream, p->nwork2.ptr, Mx2, Mx2, tables_x(p),
+                    reinterpret_cast<float2*>(image_out), p->Mx, p->Mx);
+    CK_LAUNCH("k_fft_rows");
+    return TFFR_OK;
 }
 
 int tffr_weights_noalloc(int64_t N, const double* lam_x, const double* lam_y, int Mx, int My,

@@ -91,16 +91,24 @@ def tffr_samples(plan: Plan, image: torch.Tensor) -> torch.Tensor:
 
 
 def cg_normal(plan: Plan, values: torch.Tensor, iters: int = 20, tol: float = 0.0,
-              x0: torch.Tensor | None = None):
+              x0: torch.Tensor | None = None, toeplitz: bool = False):
     """Conjugate gradients on the weighted normal equations E^H D E f = E^H D y.
 
     The minimiser of || D^(1/2) (E f - y) ||^2 over images f.  N f = E^H D E f
-    is one forward twin without weights and one adjoint (which applies D).
-    Returns (f, residual norms ||b - N f_k|| for k = 0..iters).  FP32 kernels:
-    the residual levels off near 1e-6 of ||b||.
+    is one forward twin without weights and one adjoint (which applies D), or,
+    with toeplitz=True, the plan's Toeplitz normal operator (three line-FFT
+    passes on the 2M grid, independent of the number of samples; built here by
+    plan.normal_setup()).  Returns (f, residual norms ||b - N f_k|| for
+    k = 0..iters).  FP32 kernels: the residual levels off near 1e-6 of ||b||.
     """
-    def normal(f):
-        return plan.adjoint(plan.forward(f.contiguous(), apply_weights=False))
+    if toeplitz:
+        plan.normal_setup()
+
+        def normal(f):
+            return plan.normal(f.contiguous())
+    else:
+        def normal(f):
+            return plan.adjoint(plan.forward(f.contiguous(), apply_weights=False))
 
     b = plan.adjoint(_c64(values).contiguous())
     x = torch.zeros_like(b) if x0 is None else x0.to(torch.complex64).clone()
