@@ -508,6 +508,14 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
                                                     p->cursor.ptr, p->tap_start.ptr, p->d_small.ptr + 2,
                                                     p->d_small.ptr + 4);
     CK_LAUNCH("k_row_scans");
+    // the fine-row tap table of the pulse-row order, filled before the read-back
+    // so that nothing is left to launch after it (unused in the fine-row order)
+    CK(grow(p, p->ell, (int64_t)kEllMax * ny));
+    CK(cudaMemsetAsync(p->ell.ptr, 0, (size_t)kEllMax * ny * sizeof(int2), p->stream));
+    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
+    k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, p->cursor.ptr,
+                                            p->ell.ptr);
+    CK_LAUNCH("k_ell_fill");
     CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 5 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaMemcpyAsync(p->h_small + 6, p->d_big.ptr, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
@@ -527,13 +535,7 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     // after the read-back, ordered on the stream like everything else)
     p->pulse_order = p->order_hint == TFFR_ORDER_AUTO && p->P >= 1 && p->P <= p->My && hs[4] <= kEllMax;
     if (p->pulse_order) {
-        p->ell_k = hs[4];
-        CK(grow(p, p->ell, (int64_t)kEllMax * ny));
-        CK(cudaMemsetAsync(p->ell.ptr, 0, (size_t)p->ell_k * ny * sizeof(int2), p->stream));
-        CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
-        k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, p->cursor.ptr,
-                                                p->ell.ptr);
-        CK_LAUNCH("k_ell_fill");
+        p->ell_k = hs[4];                              // the table itself was filled before the read-back
     } else {
         CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
         k_tap_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->taps, p->row_ly.ptr, p->row_fy.ptr,
