@@ -22,18 +22,20 @@ def test_graph_replay_matches_eager_and_oracle():
     pb = patch_batch(6, seed=77, sides=(64, 128), pulses=(16, 96), freqs=(32, 256))
     dev = torch.device("cuda", 0)
     patches = [(M, M, torch.from_numpy(lx).to(dev), torch.from_numpy(ly).to(dev)) for M, lx, ly, _ in pb]
-    with PatchBatch(patches, width=8) as batch:         # white random samples: width 8 (see the parity tests)
+    with PatchBatch(patches, width=8, streams=3) as batch:   # white random samples: width 8 (see the parity tests)
         assert batch.samples == sum(lx.shape[0] for _, lx, _, _ in pb)
         for k, (_, _, _, v) in enumerate(pb):
             batch.load(k, torch.from_numpy(v).to(dev))
         batch.adjoint_eager()
         batch.stream.synchronize()
-        eager = [img.clone() for img in batch.images]
-        for img in batch.images:
-            img.zero_()
+        with torch.cuda.stream(batch.stream):
+            eager = [img.clone() for img in batch.images]
+            for img in batch.images:
+                img.zero_()
         batch.capture()
-        for img in batch.images:
-            img.zero_()
+        with torch.cuda.stream(batch.stream):
+            for img in batch.images:
+                img.zero_()
         batch.replay()
         batch.replay()                                  # replays are repeatable
         batch.stream.synchronize()
