@@ -56,10 +56,10 @@ struct tffr_plan_s {
     DevBuf<int> d_small;                   // [0] error bits, [1] rows, [2] longest row, [3] row overflow,
                                            // [4] most pulse rows reaching one fine row,
                                            // [5], [6] deferred FP64 weight decisions: listed samples and
-                                           // finished blocks (zero between adjoints)
+                                           // finished blocks (zero between adjoints),
+                                           // [8..9] total row-buffer cells (int64)
     DevBuf<int2> defer;                    // [N] deferred (sample, pulse row)
-    int* h_small = nullptr;                // pinned read-back: d_small[0..4]; [6..7] the total cells (int64)
-    DevBuf<long long> d_big;               // [0] total row-buffer cells
+    int* h_small = nullptr;                // pinned read-back of d_small[0..9]
     DevBuf<unsigned long long> d_kept;
 
     // points (the caller's coordinate arrays are used in place)
@@ -481,7 +481,6 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     CK(grow(p, p->tile_head, ntiles));
     CK(grow(p, p->tap_start, ny + 1));
     CK(grow(p, p->cursor, ny + 1));
-    CK(grow(p, p->d_big, 1));
     CK(cudaMemsetAsync(p->d_small.ptr, 0, 5 * sizeof(int), p->stream));
     RowScanArgs a;
     a.row_start = p->row_start.ptr;
@@ -504,7 +503,8 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     CK_LAUNCH("k_row_finish");
     // row buffer offsets, longest row (-> d_small[2]) and the per-fine-row tap
     // counts with the largest (-> d_small[4], which picks the pass order)
-    k_row_scans<<<1, kScanThreads, 0, p->stream>>>(runs, cap, p->row_len.ptr, p->row_off.ptr, p->d_big.ptr, ny,
+    long long* d_total = reinterpret_cast<long long*>(p->d_small.ptr + 8);
+    k_row_scans<<<1, kScanThreads, 0, p->stream>>>(runs, cap, p->row_len.ptr, p->row_off.ptr, d_total, ny,
                                                     p->cursor.ptr, p->tap_start.ptr, p->d_small.ptr + 2,
                                                     p->d_small.ptr + 4);
     CK_LAUNCH("k_row_scans");
@@ -516,13 +516,13 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, p->cursor.ptr,
                                             p->ell.ptr);
     CK_LAUNCH("k_ell_fill");
-    CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 5 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaMemcpyAsync(p->h_small + 6, p->d_big.ptr, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
+    // one read-back: d_small[0..4] and the total cells in d_small[8..9]
+    CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 10 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaStreamSynchronize(p->stream));
     int hs[5];
     long long tot;
     std::memcpy(hs, p->h_small, sizeof(hs));
-    std::memcpy(&tot, p->h_small + 6, sizeof(tot));
+    std::memcpy(&tot, p->h_small + 8, sizeof(tot));
     if (hs[0] & 1) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_y or |lam_y| >= 2^28");
     if (hs[0] & 2) return fail(p, TFFR_ERR_INVALID_ARG, "non-finite lam_x or |lam_x| >= 2^28");
     *P_out = hs[1];
@@ -872,9 +872,9 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
     if (s == TFFR_OK) s = upload_tables(p);
     if (s == TFFR_OK) {
         cudaError_t e = grow(p, p->T, (int64_t)Mx * p->ny);
-        if (e == cudaSuccess) e = grow(p, p->d_small, 8);
-        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_small.ptr, 0, 8 * sizeof(int), p->stream);
-        if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_small, 8 * sizeof(int));
+        if (e == cudaSuccess) e = grow(p, p->d_small, 16);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_small.ptr, 0, 16 * sizeof(int), p->stream);
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_small, 16 * sizeof(int));
         if (e == cudaSuccess) e = grow(p, p->d_kept, 1);
         if (e != cudaSuccess) s = cuda_fail(p, e, "tffr_plan: allocation");
     }
@@ -891,7 +891,7 @@ int tffr_destroy(tffr_plan_t p) {
     cudaStreamSynchronize(p->stream);
     release(p->twh_x); release(p->twl_x); release(p->twh_y); release(p->twl_y); release(p->tt_x); release(p->tt_y);
     release(p->T); release(p->deap_x); release(p->deap_y);
-    release(p->d_small); release(p->d_kept); release(p->d_big); release(p->D);
+    release(p->d_small); release(p->d_kept); release(p->D);
     release(p->tile_info); release(p->tile_head); release(p->defer);
     release(p->khat); release(p->nwork1); release(p->nwork2);
     if (p->h_small) cudaFreeHost(p->h_small);
