@@ -365,6 +365,23 @@ def run_gpu(args, world, rank, local):
     d2h = int(h_img[0].numel() * 8)
     plan_b.close()
 
+    # ---- comparison only: cuFFT (torch.fft) on the 2M x 2M grid a plain NUFFT transforms ----
+    # (never on the path; the two pruned passes above also apply the azimuth
+    # taps, the deapodisation and the crop)
+    grid = torch.randn((2 * M, 2 * M), dtype=torch.complex64, device=dev)
+    with torch.cuda.stream(stream):
+        torch.fft.ifft2(grid, norm="forward")
+        torch.cuda.synchronize()
+        kc = max(3, args.steps // 40)
+        ev0.record(stream)
+        for _ in range(kc):
+            torch.fft.ifft2(grid, norm="forward")
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    fft_compare = {"cufft_ifft2_%dx%d_c64_ms" % (2 * M, 2 * M): ev0.elapsed_time(ev1) / kc,
+                   "tffr_x_pass_plus_column_pass_ms": kern["row_fft"]["ms"] + kern["col_fft"]["ms"]}
+    del grid
+
     # ---- a batch of 64 uneven sub-aperture patches: eager calls vs one CUDA graph ----
     from paper_1910_10908_gb300.batched import PatchBatch
     from synth import patch_batch
@@ -502,6 +519,7 @@ def run_gpu(args, world, rank, local):
             "precision_variants": precision,
             "batched_patches": batched,
             "normal_operator": normal,
+            "fft_comparison": fft_compare,
             "e2e": {"value": whole_job_rate(N, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                     "overlap": "two plans on two streams: one step's copies overlap the other's kernels",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
