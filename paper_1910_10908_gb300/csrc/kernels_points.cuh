@@ -328,15 +328,16 @@ __global__ void k_fill_int(int n, int v, int* __restrict__ a) {
 // footprint of >= nx cells takes the whole periodic row, row_clo = 0,
 // row_len = nx); the row's y cell, its w azimuth taps row_wy[p][s] =
 // phi(s - (w/2 - 1) - fy) (stride 8) and the count of pulse rows reaching
-// each fine row (tap_count, zeroed).  Puts the extent arrays back to their
-// identities for the next scan.  The walk over tiles is O(tiles) in total.
+// each fine row (tap_count, zeroed), and how many rows have each fine y cell
+// (ly_count, zeroed).  Puts the extent arrays back to their identities for
+// the next scan.  The walk over tiles is O(tiles) in total.
 __global__ void k_row_finish(const int* __restrict__ runs, int cap, int64_t N, int ntiles,
                              const int4* __restrict__ tile, const int2* __restrict__ head, int nx, int ny, int w,
                              TapPoly tp, const double* __restrict__ lam_y, const int* __restrict__ row_start,
                              int* __restrict__ row_end, int* __restrict__ row_min, int* __restrict__ row_max,
                              int* __restrict__ row_clo, int* __restrict__ row_len, int* __restrict__ row_ly,
                              float* __restrict__ row_fy, double* __restrict__ row_lam_y, float* __restrict__ row_wy,
-                             int* __restrict__ tap_count) {
+                             int* __restrict__ tap_count, int* __restrict__ ly_count) {
     const int P = min(*runs, cap);
     const int h = w / 2;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
@@ -379,42 +380,61 @@ __global__ void k_row_finish(const int* __restrict__ runs, int cap, int64_t N, i
 #pragma unroll
         for (int s = 0; s < 8; ++s) row_wy[(size_t)p * 8 + s] = (s < w) ? tap_eval(tp, s, tt) : 0.0f;
         for (int s = 0; s < w; ++s) atomicAdd(&tap_count[wrapmod(cy - (h - 1) + s, ny)], 1);
+        atomicAdd(&ly_count[wrapmod(cy, ny)], 1);
     }
 }
 
-// Single block, after k_row_finish: row buffer offsets (exclusive scan of
-// row_len over the P rows), their total and the longest row; then the
-// exclusive scan of the per-fine-row tap counts into tap_start[0..ny] and the
-// largest count (atomic max into *max_len and *max_count, zero before).
-__global__ void __launch_bounds__(kScanThreads)
-k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_len, int64_t* __restrict__ row_off,
-            long long* __restrict__ total, int ny, const int* __restrict__ tap_count, int* __restrict__ tap_start,
-            int* __restrict__ max_len, int* __restrict__ max_count) {
-    __shared__ int s_warp[32];
-    const int P = min(*runs, cap);
-    long long carry = 0;
-    int mx = 0;
-    for (int base = 0; base < P; base += kScanThreads) {
-        const int i = base + threadIdx.x;
-        const int x = (i < P) ? row_len[i] : 0;
-        mx = max(mx, x);
+constexpr int kScanItems = 8;                          // consecutive items per thread in a block pass
+
+// Exclusive scan of in[0..n) into out[0..n) by one block, kScanItems
+// consecutive items per thread and pass; out may be in (each thread reads its
+// items before writing them).  Starts from carry and returns the carry after
+// the last item (to every thread); folds the items into mx.  The sum of one
+// pass must fit an int.
+template <typename OutT>
+__device__ long long block_scan_items(const int* in, OutT* out, int n, long long carry, int* s_warp, int& mx) {
+    for (int base = 0; base < n; base += kScanThreads * kScanItems) {
+        const int i0 = base + (int)threadIdx.x * kScanItems;
+        int x[kScanItems];
+        int sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            x[k] = (i0 + k < n) ? in[i0 + k] : 0;
+            mx = max(mx, x[k]);
+            sum += x[k];
+        }
         int tot;
-        const int ex = block_exclusive_scan(x, s_warp, &tot);
-        if (i < P) row_off[i] = carry + ex;
+        int ex = block_exclusive_scan(sum, s_warp, &tot);
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (i0 + k < n) out[i0 + k] = (OutT)(carry + ex);
+            ex += x[k];
+        }
         carry += tot;
     }
-    if (threadIdx.x == 0) *total = carry;
-    int c = 0, cmx = 0;
-    for (int base = 0; base < ny; base += kScanThreads) {
-        const int i = base + threadIdx.x;
-        const int x = (i < ny) ? tap_count[i] : 0;
-        cmx = max(cmx, x);
-        int tot;
-        const int ex = block_exclusive_scan(x, s_warp, &tot);
-        if (i < ny) tap_start[i] = c + ex;
-        c += tot;
-    }
-    if (threadIdx.x == 0) tap_start[ny] = c;
+    return carry;
+}
+
+// Single block, after k_row_finish: row buffer offsets (exclusive scan of
+// row_len over the P rows), their total and the longest row; the exclusive
+// scan of the per-fine-row tap counts into tap_start[0..ny] and the largest
+// count (atomic max into *max_len and *max_count, zero before), after which
+// tap_count is zeroed again (the cursor of k_ell_fill); and ly_count[0..ny)
+// replaced in place by its exclusive scan, the first place in fine-y order
+// of the rows of each fine y cell.
+__global__ void __launch_bounds__(kScanThreads)
+k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_len, int64_t* __restrict__ row_off,
+            long long* __restrict__ total, int ny, int* tap_count, int* __restrict__ tap_start,
+            int* __restrict__ max_len, int* __restrict__ max_count, int* ly_count) {
+    __shared__ int s_warp[32];
+    const int P = min(*runs, cap);
+    int mx = 0, cmx = 0, unused = 0;
+    const long long cells = block_scan_items(row_len, row_off, P, 0, s_warp, mx);
+    if (threadIdx.x == 0) *total = cells;
+    const long long taps = block_scan_items(tap_count, tap_start, ny, 0, s_warp, cmx);
+    if (threadIdx.x == 0) tap_start[ny] = (int)taps;
+    block_scan_items(ly_count, ly_count, ny, 0, s_warp, unused);
+    for (int i = threadIdx.x; i < ny; i += kScanThreads) tap_count[i] = 0;   // every read is behind a barrier
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -427,18 +447,28 @@ k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_l
 }
 
 // Azimuth taps as a table of fixed width per fine row (pulse-row order of
-// the FFT passes): slot k of fine row r holds (pulse row, tap weight) in
-// ell[k * ny + r]; slots past the row's count stay (0, 0).  cursor: zeroed.
+// the FFT passes).  Each pulse row p first takes its place q in fine-y order
+// (ly_first: the first place of each fine y cell, from k_row_scans; rows of
+// one cell in any order) into row_rank[p]: the x pass writes row p to row q
+// of F, so that the rows a warp's consecutive fine rows gather are
+// neighbouring words of shared memory.  Slot k of fine row r then holds
+// (q, tap weight) in ell[k * ny + r]; slots past the row's count stay (0, 0).
+// cursor: zeroed.
 __global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny, int w, const int* __restrict__ row_ly,
-                           const float* __restrict__ row_wy, int* __restrict__ cursor, int2* __restrict__ ell) {
+                           const float* __restrict__ row_wy, int* __restrict__ ly_first, int* __restrict__ row_rank,
+                           int* __restrict__ cursor, int2* __restrict__ ell) {
     const int P = min(*runs, cap);
     const int h = w / 2;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const int ly = row_ly[p];
+        const int q = atomicAdd(&ly_first[wrapmod(ly, ny)], 1);
+        row_rank[p] = q;
         for (int t = 0; t < w; ++t) {
-            const int r = wrapmod(row_ly[p] - (h - 1) + t, ny);
+            const int r = wrapmod(ly - (h - 1) + t, ny);
             const int k = atomicAdd(&cursor[r], 1);
-            if (k < kEllMax) ell[(size_t)k * ny + r] = make_int2(p, __float_as_int(row_wy[(size_t)p * 8 + t]));
+            if (k < kEllMax) ell[(size_t)k * ny + r] = make_int2(q, __float_as_int(row_wy[(size_t)p * 8 + t]));
         }
+    }
 }
 
 __global__ void k_tap_fill(const int* __restrict__ runs, int cap, int ny, int w, TapPoly tp, const int* __restrict__ row_ly,

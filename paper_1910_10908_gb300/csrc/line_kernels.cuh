@@ -404,7 +404,7 @@ k_adj_rows_pulse(RowsView rv, const float2* __restrict__ R, FftTables tab, const
         v[u] = (o < len) ? __ldg(&Rp[o]) : make_float2(0.f, 0.f);
     }
     __syncthreads();                                   // twiddles in place
-    RowOut<LOGN> epi{p, deap_x, F};
+    RowOut<LOGN> epi{rv.row_rank[p], deap_x, F};          // F rows in fine-y order
     fft_line_epilogue_regs<LOGN, +1>(v, S.buf, tw, epi);
 }
 
@@ -455,7 +455,9 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
     }
     cluster.sync();
     // azimuth taps, gathered: fine row r = sum over its table slots k < K of
-    // weight_k F[p_k] (K: the most pulse rows any fine row receives), straight
+    // weight_k F[q_k] (K: the most pulse rows any fine row receives; q_k the
+    // tap's row of F, in fine-y order so that a warp's lanes read neighbouring
+    // words of fcol), straight
     // into the registers of the first FFT stage (row tid + u T)
     float2 v[V];
 #pragma unroll

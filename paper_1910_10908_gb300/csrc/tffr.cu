@@ -90,6 +90,7 @@ struct tffr_plan_s {
     DevBuf<int64_t> row_off;
     DevBuf<float2> R;
     DevBuf<int> tap_start;                 // [ny + 1] taps of each fine row
+    DevBuf<int> row_rank;                  // [cap] place of each pulse row in fine-y order (its row of F)
     DevBuf<TapEntry> tap_list;             // [P * w]
 
     // general points
@@ -426,6 +427,7 @@ RowsView rows_view(const tffr_plan_s* p) {
     v.row_fy = p->row_fy.ptr;
     v.row_lam_y = p->row_lam_y.ptr;
     v.row_off = p->row_off.ptr;
+    v.row_rank = p->row_rank.ptr;
     v.tap_start = p->tap_start.ptr;
     v.taps = p->tap_list.ptr;
     return v;
@@ -458,6 +460,7 @@ int reserve_rows(tffr_plan_s* p, int cap) {
     CK(grow(p, p->row_fy, cap));
     CK(grow(p, p->row_lam_y, cap));
     CK(grow(p, p->row_off, cap));
+    CK(grow(p, p->row_rank, cap));
     CK(grow(p, p->row_wy, (int64_t)cap * 8));
     CK(grow(p, p->tap_list, (int64_t)cap * w));
     k_fill_int<<<grid_for(cap, 256), 256, 0, p->stream>>>(cap, kIntMax, p->row_min.ptr);
@@ -480,7 +483,10 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     CK(grow(p, p->tile_info, ntiles));
     CK(grow(p, p->tile_head, ntiles));
     CK(grow(p, p->tap_start, ny + 1));
-    CK(grow(p, p->cursor, ny + 1));
+    CK(grow(p, p->cursor, 2 * ny + 1));
+    // cursor[0..ny]: tap counts per fine row, then the table's fill cursor;
+    // cursor[ny + 1..2 ny]: pulse rows per fine y cell, then their places in fine-y order
+    int* const ly_first = p->cursor.ptr + ny + 1;
     CK(cudaMemsetAsync(p->d_small.ptr, 0, 5 * sizeof(int), p->stream));
     RowScanArgs a;
     a.row_start = p->row_start.ptr;
@@ -494,27 +500,26 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     k_scan_rows<<<(unsigned)ntiles, kRowScanWarps * 32, 0, p->stream>>>(N, p->lam_x, p->lam_y, a);
     CK_LAUNCH("k_scan_rows");
     const int* runs = p->d_small.ptr + 1;
-    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
+    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(2 * ny + 1) * sizeof(int), p->stream));
     k_row_finish<<<prow, 256, 0, p->stream>>>(runs, cap, N, (int)ntiles, p->tile_info.ptr, p->tile_head.ptr, p->nx,
                                               ny, w, p->taps, p->lam_y, p->row_start.ptr, p->row_end.ptr,
                                               p->row_min.ptr, p->row_max.ptr, p->row_clo.ptr, p->row_len.ptr,
                                               p->row_ly.ptr, p->row_fy.ptr, p->row_lam_y.ptr, p->row_wy.ptr,
-                                              p->cursor.ptr);
+                                              p->cursor.ptr, ly_first);
     CK_LAUNCH("k_row_finish");
     // row buffer offsets, longest row (-> d_small[2]) and the per-fine-row tap
     // counts with the largest (-> d_small[4], which picks the pass order)
     long long* d_total = reinterpret_cast<long long*>(p->d_small.ptr + 8);
     k_row_scans<<<1, kScanThreads, 0, p->stream>>>(runs, cap, p->row_len.ptr, p->row_off.ptr, d_total, ny,
                                                     p->cursor.ptr, p->tap_start.ptr, p->d_small.ptr + 2,
-                                                    p->d_small.ptr + 4);
+                                                    p->d_small.ptr + 4, ly_first);
     CK_LAUNCH("k_row_scans");
     // the fine-row tap table of the pulse-row order, filled before the read-back
     // so that nothing is left to launch after it (unused in the fine-row order)
     CK(grow(p, p->ell, (int64_t)kEllMax * ny));
     CK(cudaMemsetAsync(p->ell.ptr, 0, (size_t)kEllMax * ny * sizeof(int2), p->stream));
-    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(ny + 1) * sizeof(int), p->stream));
-    k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, p->cursor.ptr,
-                                            p->ell.ptr);
+    k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, ly_first,
+                                            p->row_rank.ptr, p->cursor.ptr, p->ell.ptr);
     CK_LAUNCH("k_ell_fill");
     // one read-back: d_small[0..4] and the total cells in d_small[8..9]
     CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 10 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
@@ -899,7 +904,7 @@ int tffr_destroy(tffr_plan_t p) {
     release(p->row_min); release(p->row_max); release(p->row_end); release(p->row_wy);
     release(p->ell);
     release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);
-    release(p->tap_start); release(p->tap_list);
+    release(p->tap_start); release(p->tap_list); release(p->row_rank);
     release(p->lx); release(p->ly); release(p->perm); release(p->slx); release(p->cursor);
     release(p->fx); release(p->fy); release(p->sfx); release(p->sfy); release(p->sD); release(p->acc);
     for (auto& sp : p->prof)

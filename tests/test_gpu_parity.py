@@ -330,24 +330,31 @@ def expected_rows(lx, ly, nx, w):
     return len(starts), int(np.sum(lens)), int(np.max(lens))
 
 
-@pytest.mark.parametrize("case", ["long_rows_across_tiles", "more_rows_than_first_capacity", "repeated_lam_y"])
+@pytest.mark.parametrize("case", ["long_rows_across_tiles", "more_rows_than_first_capacity", "repeated_lam_y",
+                                  "rows_at_the_y_edges"])
 def test_pulse_row_scan(case):
     """Pulse rows found by the one-pass scan: rows longer than a scan tile (4096 samples),
     more rows than the plan's first row capacity (4096, so the scan runs twice), a lam_y
-    value that comes back after another row (two separate rows), single-sample rows."""
+    value that comes back after another row (two separate rows), single-sample rows, and
+    rows whose azimuth taps wrap around the fine grid (rows of one fine y cell, in any
+    order, and the first and last cells)."""
     M, w = 64, 8
     g = np.random.default_rng({"long_rows_across_tiles": 21, "more_rows_than_first_capacity": 22,
-                               "repeated_lam_y": 23}[case])
+                               "repeated_lam_y": 23, "rows_at_the_y_edges": 24}[case])
     if case == "long_rows_across_tiles":
         lens = [1, 5000, 9000, 2, 4095, 4097, 1, 300]
     elif case == "more_rows_than_first_capacity":
         lens = list(g.integers(1, 12, 5000))
+    elif case == "rows_at_the_y_edges":
+        lens = [300, 40, 500, 7, 1, 260, 90, 120]
     else:
         lens = [700, 1, 900, 5, 4200, 33]
     ly_rows = g.uniform(-0.45 * M, 0.45 * M, len(lens))
     if case == "repeated_lam_y":
         ly_rows[2] = ly_rows[0]
         ly_rows[4] = ly_rows[0]
+    if case == "rows_at_the_y_edges":
+        ly_rows = np.array([M / 2 - 1e-9, -M / 2, 0.1, M / 2 - 0.3, -M / 2 + 0.2, 0.15, -M / 2 + 0.1, 0.1 + 2 ** -40])
     ly = np.repeat(ly_rows, lens)
     lx = np.empty(ly.shape[0])
     pos = 0
@@ -360,6 +367,7 @@ def test_pulse_row_scan(case):
     P, cells, longest = expected_rows(lx, ly, 2 * M, w)
     assert info["layout"] == 2
     assert (info["n_rows"], info["row_cells"], info["max_row_cells"]) == (P, cells, longest)
+    assert info["pulse_order"] == (P <= M)
     ref = oracle.adjoint_image(lx, ly, v, oracle.tffr_weights(lx, M), M, M)
     assert rel_l2(img, ref) <= TOL
 
