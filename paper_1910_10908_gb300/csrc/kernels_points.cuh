@@ -419,7 +419,7 @@ __device__ long long block_scan_items(const int* in, OutT* out, int n, long long
 // row_len over the P rows), their total and the longest row; the exclusive
 // scan of the per-fine-row tap counts into tap_start[0..ny] and the largest
 // count (atomic max into *max_len and *max_count, zero before), after which
-// tap_count is zeroed again (the cursor of k_ell_fill); and ly_count[0..ny)
+// tap_count is zeroed again (the per-fine-row cursor of k_ell_fill); and ly_count[0..ny)
 // replaced in place by its exclusive scan, the first place in fine-y order
 // of the rows of each fine y cell.
 __global__ void __launch_bounds__(kScanThreads)
@@ -447,25 +447,27 @@ k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_l
 }
 
 // Azimuth taps as a table of fixed width per fine row (pulse-row order of
-// the FFT passes).  Each pulse row p first takes its place q in fine-y order
-// (ly_first: the first place of each fine y cell, from k_row_scans; rows of
-// one cell in any order) into row_rank[p]: the x pass writes row p to row q
-// of F, so that the rows a warp's consecutive fine rows gather are
-// neighbouring words of shared memory.  Slot k of fine row r then holds
-// (q, tap weight) in ell[k * ny + r]; slots past the row's count stay (0, 0).
-// cursor: zeroed.
+// the FFT passes).  Each pulse row p first takes its place q in fine-y order,
+// q = ly_first[c] + (its arrival among the rows of its fine y cell c), and
+// rank_row[q] = p: the x pass puts row p at place q of F, so that the rows a
+// warp's consecutive fine rows gather are neighbouring words of shared
+// memory.  Slot k of fine row r then holds (q, tap weight) in
+// ell[k * ny + r]; slots past the row's count stay (0, 0).  cell_cursor and
+// row_cursor (arrivals per fine y cell and per fine row): zeroed.
 __global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny, int w, const int* __restrict__ row_ly,
-                           const float* __restrict__ row_wy, int* __restrict__ ly_first, int* __restrict__ row_rank,
-                           int* __restrict__ cursor, int2* __restrict__ ell) {
+                           const float* __restrict__ row_wy, const int* __restrict__ ly_first,
+                           int* __restrict__ rank_row, int* __restrict__ cell_cursor, int* __restrict__ row_cursor,
+                           int2* __restrict__ ell) {
     const int P = min(*runs, cap);
     const int h = w / 2;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
         const int ly = row_ly[p];
-        const int q = atomicAdd(&ly_first[wrapmod(ly, ny)], 1);
-        row_rank[p] = q;
+        const int c = wrapmod(ly, ny);
+        const int q = ly_first[c] + atomicAdd(&cell_cursor[c], 1);
+        rank_row[q] = p;
         for (int t = 0; t < w; ++t) {
             const int r = wrapmod(ly - (h - 1) + t, ny);
-            const int k = atomicAdd(&cursor[r], 1);
+            const int k = atomicAdd(&row_cursor[r], 1);
             if (k < kEllMax) ell[(size_t)k * ny + r] = make_int2(q, __float_as_int(row_wy[(size_t)p * 8 + t]));
         }
     }

@@ -377,10 +377,40 @@ k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int ny, in
 // ---------------------------------------------------------------------------
 
 // Column-pass shared memory: the line plus one column of F (up to N/2 pulse rows).
+// Column passes in pulse-row order: the line's shared memory, then a column
+// of F (up to N / 2 = M_y places) starting on a 128-byte boundary, so that
+// the 16 places of each 128 bytes fall in one shared-memory wavefront.
+template <int LOGN>
+constexpr int kPulseColOff = (Line<LOGN>::SMEM_ELEMS + 15) & ~15;
+
 template <int LOGN>
 __host__ __device__ constexpr size_t line_smem_pulse_cols() {
-    return line_smem_bytes<LOGN>() + (size_t)(Line<LOGN>::N / 2) * sizeof(float2);
+    return (size_t)(kPulseColOff<LOGN> + Line<LOGN>::N / 2) * sizeof(float2);
 }
+
+// F in the adjoint's pulse-row order, by blocks of four columns: entry q
+// (place in fine-y order) of column jx at F[((jx / 4) ldq + q) 4 + jx % 4],
+// ldq = P rounded up to 4.  The x pass stores the four columns of a block as
+// one 32-byte piece; the four CTAs of a column cluster read their block as
+// one contiguous run.
+__host__ __device__ __forceinline__ int pulse_ldq(int P) { return (P + 3) & ~3; }
+
+// Pass-1 epilogue of the adjoint in pulse-row order: keep the M_x = N/2
+// wanted x modes, deapodise, store them as entry q of every column of F.
+template <int LOGN>
+struct QuadOut {
+    int q, ldq;
+    const float* deap_x;
+    float2* F;
+    __device__ __forceinline__ void operator()(int o, float2 v) const {
+        constexpr int N = 1 << LOGN, MX = N / 2, HALF = MX / 2;
+        int jx;
+        if (o < HALF) jx = o + HALF;
+        else if (o >= N - HALF) jx = o - (N - HALF);
+        else return;
+        F[(((size_t)(jx >> 2) * ldq + q) << 2) + (jx & 3)] = cscale(v, __ldg(&deap_x[jx]));
+    }
+};
 
 template <int LOGN>
 __global__ void __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
@@ -390,7 +420,8 @@ k_adj_rows_pulse(RowsView rv, const float2* __restrict__ R, FftTables tab, const
     constexpr int NX = L::N;
     extern __shared__ float2 smem[];
     LineSmem<LOGN> S(smem);
-    const int p = blockIdx.x;
+    const int q = blockIdx.x;                          // place in fine-y order
+    const int p = rv.rank_row[q];
     const int tid = threadIdx.x;
     const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
     // line cell j holds R_p[(j - clo) mod NX] when that is below len, else 0;
@@ -404,7 +435,7 @@ k_adj_rows_pulse(RowsView rv, const float2* __restrict__ R, FftTables tab, const
         v[u] = (o < len) ? __ldg(&Rp[o]) : make_float2(0.f, 0.f);
     }
     __syncthreads();                                   // twiddles in place
-    RowOut<LOGN> epi{rv.row_rank[p], deap_x, F};          // F rows in fine-y order
+    QuadOut<LOGN> epi{q, pulse_ldq(rv.P), deap_x, F};
     fft_line_epilogue_regs<LOGN, +1>(v, S.buf, tw, epi);
 }
 
@@ -426,17 +457,20 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
     constexpr int NY = L::N, MY = NY / 2, V = L::V;
     extern __shared__ float2 smem[];
     LineSmem<LOGN> S(smem);
-    float2* fcol = smem + L::SMEM_ELEMS;               // this CTA's column of F, P entries
+    float2* fcol = smem + kPulseColOff<LOGN>;         // this CTA's column of F, P entries
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int jx0 = (int)blockIdx.x - rank;
     const int tid = threadIdx.x;
     const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
     static_assert(L::T % kColCluster == 0, "line threads must be a multiple of the cluster size");
-    // element i of this CTA's share (pulse row p0 + i / 4, column i % 4 = tid % 4)
+    // The cluster's block of four columns of F is one contiguous run; CTA rank
+    // reads the quarter of places [p0, p0 + PQ) and sends entry i of it
+    // (place p0 + i / 4, column i % 4 = tid % 4) to the fcol of CTA i % 4.
     float2* const peer_f = cluster.map_shared_rank(fcol, tid % kColCluster);
-    const int PQ = (P + kColCluster - 1) / kColCluster;
-    const int p0 = min(P, rank * PQ), nel = (min(P, p0 + PQ) - p0) * kColCluster;
+    const int ldq = pulse_ldq(P), PQ = ldq / kColCluster;
+    const int p0 = rank * PQ, nel = max(0, min(P, p0 + PQ) - p0) * kColCluster;
+    const float2* const Fq = F + ((size_t)(jx0 / kColCluster) * ldq + p0) * kColCluster;
     cluster_arrive_relaxed();                          // every CTA runs before its memory is written
     cluster_wait();
     for (int base = 0; base < nel; base += V * L::T) {
@@ -444,8 +478,7 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int i = base + tid + u * L::T;
-            tmp[u] = (i < nel) ? __ldg(&F[(size_t)(p0 + i / kColCluster) * Mx + jx0 + i % kColCluster])
-                               : make_float2(0.f, 0.f);
+            tmp[u] = (i < nel) ? __ldg(&Fq[i]) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int u = 0; u < V; ++u) {
@@ -455,10 +488,10 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
     }
     cluster.sync();
     // azimuth taps, gathered: fine row r = sum over its table slots k < K of
-    // weight_k F[q_k] (K: the most pulse rows any fine row receives; q_k the
-    // tap's row of F, in fine-y order so that a warp's lanes read neighbouring
-    // words of fcol), straight
-    // into the registers of the first FFT stage (row tid + u T)
+    // weight_k fcol[q_k] (K: the most pulse rows any fine row receives; q_k
+    // the tap's place in fine-y order, so that a warp's lanes read
+    // neighbouring words of fcol), straight into the registers of the first
+    // FFT stage (row tid + u T)
     float2 v[V];
 #pragma unroll
     for (int u = 0; u < V; ++u) v[u] = make_float2(0.f, 0.f);
@@ -509,7 +542,7 @@ k_fwd_cols_pulse(const float2* __restrict__ img, int Mx, FftTables tab, const fl
     constexpr int NY = L::N, MY = NY / 2, V = L::V;
     extern __shared__ float2 smem[];
     LineSmem<LOGN> S(smem);
-    float2* fcol = smem + L::SMEM_ELEMS;
+    float2* fcol = smem + kPulseColOff<LOGN>;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int jx0 = (int)blockIdx.x - rank;

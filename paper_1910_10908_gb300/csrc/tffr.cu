@@ -80,7 +80,7 @@ struct tffr_plan_s {
     int64_t R_cells = 0;
     int max_len = 0;
     int row_cap = 0;                       // capacity of the per-row arrays
-    bool pulse_order = false;              // FFT passes in pulse-row order (F [P][Mx] in T's memory)
+    bool pulse_order = false;              // FFT passes in pulse-row order (F in T's memory)
     DevBuf<float> row_wy;                  // [cap][8] azimuth taps of each pulse row
     DevBuf<int2> ell;                      // [kEllMax][ny] fine-row tap table (pulse-row order)
     int ell_k = 0;                         // slots in use: the most pulse rows a fine row receives
@@ -90,7 +90,7 @@ struct tffr_plan_s {
     DevBuf<int64_t> row_off;
     DevBuf<float2> R;
     DevBuf<int> tap_start;                 // [ny + 1] taps of each fine row
-    DevBuf<int> row_rank;                  // [cap] place of each pulse row in fine-y order (its row of F)
+    DevBuf<int> rank_row;                  // [cap] pulse row at each place in fine-y order
     DevBuf<TapEntry> tap_list;             // [P * w]
 
     // general points
@@ -427,7 +427,7 @@ RowsView rows_view(const tffr_plan_s* p) {
     v.row_fy = p->row_fy.ptr;
     v.row_lam_y = p->row_lam_y.ptr;
     v.row_off = p->row_off.ptr;
-    v.row_rank = p->row_rank.ptr;
+    v.rank_row = p->rank_row.ptr;
     v.tap_start = p->tap_start.ptr;
     v.taps = p->tap_list.ptr;
     return v;
@@ -460,7 +460,7 @@ int reserve_rows(tffr_plan_s* p, int cap) {
     CK(grow(p, p->row_fy, cap));
     CK(grow(p, p->row_lam_y, cap));
     CK(grow(p, p->row_off, cap));
-    CK(grow(p, p->row_rank, cap));
+    CK(grow(p, p->rank_row, cap));
     CK(grow(p, p->row_wy, (int64_t)cap * 8));
     CK(grow(p, p->tap_list, (int64_t)cap * w));
     k_fill_int<<<grid_for(cap, 256), 256, 0, p->stream>>>(cap, kIntMax, p->row_min.ptr);
@@ -483,9 +483,10 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     CK(grow(p, p->tile_info, ntiles));
     CK(grow(p, p->tile_head, ntiles));
     CK(grow(p, p->tap_start, ny + 1));
-    CK(grow(p, p->cursor, 2 * ny + 1));
+    CK(grow(p, p->cursor, 3 * ny + 1));
     // cursor[0..ny]: tap counts per fine row, then the table's fill cursor;
-    // cursor[ny + 1..2 ny]: pulse rows per fine y cell, then their places in fine-y order
+    // cursor[ny + 1..2 ny]: pulse rows per fine y cell, then their first places
+    // in fine-y order; cursor[2 ny + 1..3 ny]: arrivals per fine y cell
     int* const ly_first = p->cursor.ptr + ny + 1;
     CK(cudaMemsetAsync(p->d_small.ptr, 0, 5 * sizeof(int), p->stream));
     RowScanArgs a;
@@ -500,7 +501,7 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     k_scan_rows<<<(unsigned)ntiles, kRowScanWarps * 32, 0, p->stream>>>(N, p->lam_x, p->lam_y, a);
     CK_LAUNCH("k_scan_rows");
     const int* runs = p->d_small.ptr + 1;
-    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(2 * ny + 1) * sizeof(int), p->stream));
+    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(3 * ny + 1) * sizeof(int), p->stream));
     k_row_finish<<<prow, 256, 0, p->stream>>>(runs, cap, N, (int)ntiles, p->tile_info.ptr, p->tile_head.ptr, p->nx,
                                               ny, w, p->taps, p->lam_y, p->row_start.ptr, p->row_end.ptr,
                                               p->row_min.ptr, p->row_max.ptr, p->row_clo.ptr, p->row_len.ptr,
@@ -519,7 +520,7 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     CK(grow(p, p->ell, (int64_t)kEllMax * ny));
     CK(cudaMemsetAsync(p->ell.ptr, 0, (size_t)kEllMax * ny * sizeof(int2), p->stream));
     k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, ly_first,
-                                            p->row_rank.ptr, p->cursor.ptr, p->ell.ptr);
+                                            p->rank_row.ptr, ly_first + ny, p->cursor.ptr, p->ell.ptr);
     CK_LAUNCH("k_ell_fill");
     // one read-back: d_small[0..4] and the total cells in d_small[8..9]
     CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 10 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
@@ -904,7 +905,7 @@ int tffr_destroy(tffr_plan_t p) {
     release(p->row_min); release(p->row_max); release(p->row_end); release(p->row_wy);
     release(p->ell);
     release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);
-    release(p->tap_start); release(p->tap_list); release(p->row_rank);
+    release(p->tap_start); release(p->tap_list); release(p->rank_row);
     release(p->lx); release(p->ly); release(p->perm); release(p->slx); release(p->cursor);
     release(p->fx); release(p->fy); release(p->sfx); release(p->sfy); release(p->sD); release(p->acc);
     for (auto& sp : p->prof)

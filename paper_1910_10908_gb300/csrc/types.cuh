@@ -29,7 +29,7 @@ struct RowsView {
     const float* row_fy;            // [P] fine y offset in [0, 1]
     const double* row_lam_y;        // [P] lam_y of the row
     const int64_t* row_off;         // [P] offset of the row buffer in R (cells)
-    const int* row_rank;            // [P] place of the row in fine-y order: its row of F (pulse-row order)
+    const int* rank_row;            // [P] pulse row at each place in fine-y order (pulse-row order of the adjoint)
     const int* tap_start;           // [ny + 1] taps of each fine row (CSR)
     const TapEntry* taps;           // [P * w]
 };
