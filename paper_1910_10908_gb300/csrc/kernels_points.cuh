@@ -415,35 +415,35 @@ __device__ long long block_scan_items(const int* in, OutT* out, int n, long long
     return carry;
 }
 
-// Single block, after k_row_finish: row buffer offsets (exclusive scan of
-// row_len over the P rows), their total and the longest row; the exclusive
-// scan of the per-fine-row tap counts into tap_start[0..ny] and the largest
-// count (atomic max into *max_len and *max_count, zero before), after which
-// tap_count is zeroed again (the per-fine-row cursor of k_ell_fill); and ly_count[0..ny)
-// replaced in place by its exclusive scan, the first place in fine-y order
-// of the rows of each fine y cell.
+// Three blocks, after k_row_finish, one independent scan each.  Block 0: row
+// buffer offsets (exclusive scan of row_len over the P rows), their total
+// and the longest row (atomic max into *max_len, zero before).  Block 1: the
+// exclusive scan of the per-fine-row tap counts into tap_start[0..ny] and the
+// largest count (atomic max into *max_count, zero before), after which
+// tap_count is zeroed again (the per-fine-row cursor of k_ell_fill).  Block
+// 2: ly_count[0..ny) replaced in place by its exclusive scan, the first place
+// in fine-y order of the rows of each fine y cell.
 __global__ void __launch_bounds__(kScanThreads)
 k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_len, int64_t* __restrict__ row_off,
             long long* __restrict__ total, int ny, int* tap_count, int* __restrict__ tap_start,
             int* __restrict__ max_len, int* __restrict__ max_count, int* ly_count) {
     __shared__ int s_warp[32];
-    const int P = min(*runs, cap);
-    int mx = 0, cmx = 0, unused = 0;
-    const long long cells = block_scan_items(row_len, row_off, P, 0, s_warp, mx);
-    if (threadIdx.x == 0) *total = cells;
-    const long long taps = block_scan_items(tap_count, tap_start, ny, 0, s_warp, cmx);
-    if (threadIdx.x == 0) tap_start[ny] = (int)taps;
-    block_scan_items(ly_count, ly_count, ny, 0, s_warp, unused);
-    for (int i = threadIdx.x; i < ny; i += kScanThreads) tap_count[i] = 0;   // every read is behind a barrier
+    int mx = 0;
+    if (blockIdx.x == 0) {
+        const int P = min(*runs, cap);
+        const long long cells = block_scan_items(row_len, row_off, P, 0, s_warp, mx);
+        if (threadIdx.x == 0) *total = cells;
+    } else if (blockIdx.x == 1) {
+        const long long taps = block_scan_items(tap_count, tap_start, ny, 0, s_warp, mx);
+        if (threadIdx.x == 0) tap_start[ny] = (int)taps;
+        for (int i = threadIdx.x; i < ny; i += kScanThreads) tap_count[i] = 0;   // every read is behind a barrier
+    } else {
+        block_scan_items(ly_count, ly_count, ny, 0, s_warp, mx);
+        return;
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        cmx = max(cmx, __shfl_xor_sync(0xffffffffu, cmx, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicMax(max_len, mx);
-        atomicMax(max_count, cmx);
-    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(blockIdx.x == 0 ? max_len : max_count, mx);
 }
 
 // Azimuth taps as a table of fixed width per fine row (pulse-row order of

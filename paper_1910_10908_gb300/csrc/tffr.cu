@@ -511,7 +511,7 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     // row buffer offsets, longest row (-> d_small[2]) and the per-fine-row tap
     // counts with the largest (-> d_small[4], which picks the pass order)
     long long* d_total = reinterpret_cast<long long*>(p->d_small.ptr + 8);
-    k_row_scans<<<1, kScanThreads, 0, p->stream>>>(runs, cap, p->row_len.ptr, p->row_off.ptr, d_total, ny,
+    k_row_scans<<<3, kScanThreads, 0, p->stream>>>(runs, cap, p->row_len.ptr, p->row_off.ptr, d_total, ny,
                                                     p->cursor.ptr, p->tap_start.ptr, p->d_small.ptr + 2,
                                                     p->d_small.ptr + 4, ly_first);
     CK_LAUNCH("k_row_scans");
