@@ -25,9 +25,9 @@
  *    plan owns all of its internal device buffers and frees them in
  *    tffr_destroy.
  *  - Every call is ordered on the plan's stream.  tffr_adjoint and
- *    tffr_forward never synchronise; tffr_set_points synchronises the stream
- *    before it returns; tffr_weights synchronises only when n_kept is
- *    requested.
+ *    tffr_forward never synchronise; tffr_set_points waits for the stream
+ *    before it returns (see there); tffr_weights synchronises only when
+ *    n_kept is requested.
  *  - The coordinate arrays given to tffr_set_points are used in place (no
  *    copy): they must stay valid and unchanged until the next
  *    tffr_set_points or tffr_destroy on that plan.
@@ -164,7 +164,10 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
  * would keep only ~1e-3 cell).
  * N = 0 is allowed (adjoint then returns a zero image).  Invalidates the weights.
  * Errors: INVALID_ARG for N < 0, N >= 2^31, NULL pointers with N > 0, or any
- * |lam| >= 2^28 or non-finite coordinate; OOM; CUDA.  Synchronises the stream.
+ * |lam| >= 2^28 or non-finite coordinate; OOM; CUDA.  Waits until the stream
+ * has finished everything issued before the call and the pass over the
+ * coordinates; in layout ROWS the plan's fine-row tap table may still be
+ * filled on the stream after the return (that fill reads no caller memory).
  */
 int tffr_set_points(tffr_plan_t plan, int64_t N, const double* lam_x, const double* lam_y);
 

@@ -60,6 +60,7 @@ struct tffr_plan_s {
                                            // [8..9] total row-buffer cells (int64)
     DevBuf<int2> defer;                    // [N] deferred (sample, pulse row)
     int* h_small = nullptr;                // pinned read-back of d_small[0..9]
+    cudaEvent_t readback = nullptr;        // recorded after that read-back
     DevBuf<unsigned long long> d_kept;
 
     // points (the caller's coordinate arrays are used in place)
@@ -515,16 +516,18 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
                                                     p->cursor.ptr, p->tap_start.ptr, p->d_small.ptr + 2,
                                                     p->d_small.ptr + 4, ly_first);
     CK_LAUNCH("k_row_scans");
-    // the fine-row tap table of the pulse-row order, filled before the read-back
-    // so that nothing is left to launch after it (unused in the fine-row order)
+    // one read-back: d_small[0..4] and the total cells in d_small[8..9].  The
+    // fine-row tap table of the pulse-row order is filled after it on the
+    // stream while the host waits for the read-back alone (unused in the
+    // fine-row order).
+    CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 10 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaEventRecord(p->readback, p->stream));
     CK(grow(p, p->ell, (int64_t)kEllMax * ny));
     CK(cudaMemsetAsync(p->ell.ptr, 0, (size_t)kEllMax * ny * sizeof(int2), p->stream));
     k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, ly_first,
                                             p->rank_row.ptr, ly_first + ny, p->cursor.ptr, p->ell.ptr);
     CK_LAUNCH("k_ell_fill");
-    // one read-back: d_small[0..4] and the total cells in d_small[8..9]
-    CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 10 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    CK(cudaStreamSynchronize(p->stream));
+    CK(cudaEventSynchronize(p->readback));
     int hs[5];
     long long tot;
     std::memcpy(hs, p->h_small, sizeof(hs));
@@ -881,6 +884,7 @@ int tffr_plan(tffr_plan_t* out, int Mx, int My, const tffr_opts* opts, tffr_stre
         if (e == cudaSuccess) e = grow(p, p->d_small, 16);
         if (e == cudaSuccess) e = cudaMemsetAsync(p->d_small.ptr, 0, 16 * sizeof(int), p->stream);
         if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_small, 16 * sizeof(int));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->readback, cudaEventDisableTiming);
         if (e == cudaSuccess) e = grow(p, p->d_kept, 1);
         if (e != cudaSuccess) s = cuda_fail(p, e, "tffr_plan: allocation");
     }
@@ -901,6 +905,7 @@ int tffr_destroy(tffr_plan_t p) {
     release(p->tile_info); release(p->tile_head); release(p->defer);
     release(p->khat); release(p->nwork1); release(p->nwork2);
     if (p->h_small) cudaFreeHost(p->h_small);
+    if (p->readback) cudaEventDestroy(p->readback);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly);
     release(p->row_min); release(p->row_max); release(p->row_end); release(p->row_wy);
     release(p->ell);
