@@ -276,38 +276,54 @@ k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restric
         }
     };
     const int nbase = (int)wbase;                      // N < 2^31
+    unsigned starts = 0;
 #pragma unroll
-    for (int k = 0; k < kRowScanK; ++k) {
-        const int o = k * 32 + lane;
-        const int n = nbase + o;
-        const int local = pre + __popc(ball[k] & le) - 1;
-        if (o < rem) {
-            if ((ball[k] >> lane) & 1u) {
-                const int p = base + local;
-                if (p < a.cap) a.row_start[p] = n;
-                else over = true;
-                if (local > 0) {
-                    if (p - 1 < a.cap) a.row_end[p - 1] = n;
-                } else {
-                    s_first = n;
-                }
-            }
-            if (local != cur) {
-                if (cur != kNone) flush(cur, mn, mx);
-                cur = local;
-                mn = mx = cx[k];
-            } else {
+    for (int k = 0; k < kRowScanK; ++k) starts |= ball[k];
+    if (starts == 0) {
+        // no run starts among the warp's samples (the common case): all of
+        // them continue run woff - 1, whose extent takes the warp's min / max
+#pragma unroll
+        for (int k = 0; k < kRowScanK; ++k)
+            if (k * 32 + lane < rem) {
                 mn = min(mn, cx[k]);
                 mx = max(mx, cx[k]);
             }
-        }
-        pre += __popc(ball[k]);
-    }
-    if (__all_sync(FULL, cur == __shfl_sync(FULL, cur, 0))) {
         const int m0 = __reduce_min_sync(FULL, mn), m1 = __reduce_max_sync(FULL, mx);
-        if (lane == 0 && cur != kNone) flush(cur, m0, m1);
-    } else if (cur != kNone) {
-        flush(cur, mn, mx);
+        if (lane == 0 && rem > 0) flush(woff - 1, m0, m1);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRowScanK; ++k) {
+            const int o = k * 32 + lane;
+            const int n = nbase + o;
+            const int local = pre + __popc(ball[k] & le) - 1;
+            if (o < rem) {
+                if ((ball[k] >> lane) & 1u) {
+                    const int p = base + local;
+                    if (p < a.cap) a.row_start[p] = n;
+                    else over = true;
+                    if (local > 0) {
+                        if (p - 1 < a.cap) a.row_end[p - 1] = n;
+                    } else {
+                        s_first = n;
+                    }
+                }
+                if (local != cur) {
+                    if (cur != kNone) flush(cur, mn, mx);
+                    cur = local;
+                    mn = mx = cx[k];
+                } else {
+                    mn = min(mn, cx[k]);
+                    mx = max(mx, cx[k]);
+                }
+            }
+            pre += __popc(ball[k]);
+        }
+        if (__all_sync(FULL, cur == __shfl_sync(FULL, cur, 0))) {
+            const int m0 = __reduce_min_sync(FULL, mn), m1 = __reduce_max_sync(FULL, mx);
+            if (lane == 0 && cur != kNone) flush(cur, m0, m1);
+        } else if (cur != kNone) {
+            flush(cur, mn, mx);
+        }
     }
     if (over) atomicOr(&a.flags[3], 1);
     __syncthreads();
@@ -465,11 +481,15 @@ __global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny, int w,
         const int c = wrapmod(ly, ny);
         const int q = ly_first[c] + atomicAdd(&cell_cursor[c], 1);
         rank_row[q] = p;
-        for (int t = 0; t < w; ++t) {
-            const int r = wrapmod(ly - (h - 1) + t, ny);
-            const int k = atomicAdd(&row_cursor[r], 1);
-            if (k < kEllMax) ell[(size_t)k * ny + r] = make_int2(q, __float_as_int(row_wy[(size_t)p * 8 + t]));
-        }
+        int k[8];                                      // w <= 8: the slot claims overlap
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (t < w) k[t] = atomicAdd(&row_cursor[wrapmod(ly - (h - 1) + t, ny)], 1);
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            if (t < w && k[t] < kEllMax)
+                ell[(size_t)k[t] * ny + wrapmod(ly - (h - 1) + t, ny)] =
+                    make_int2(q, __float_as_int(row_wy[(size_t)p * 8 + t]));
     }
 }
 
