@@ -467,13 +467,14 @@ k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_l
 // q = ly_first[c] + (its arrival among the rows of its fine y cell c), and
 // rank_row[q] = p: the x pass puts row p at place q of F, so that the rows a
 // warp's consecutive fine rows gather are neighbouring words of shared
-// memory.  Slot k of fine row r then holds (q, tap weight) in
+// memory; the row's y cell and taps are copied to place q (q_ly, q_wy) for
+// the forward twin.  Slot k of fine row r then holds (q, tap weight) in
 // ell[k * ny + r]; slots past the row's count stay (0, 0).  cell_cursor and
 // row_cursor (arrivals per fine y cell and per fine row): zeroed.
 __global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny, int w, const int* __restrict__ row_ly,
                            const float* __restrict__ row_wy, const int* __restrict__ ly_first,
-                           int* __restrict__ rank_row, int* __restrict__ cell_cursor, int* __restrict__ row_cursor,
-                           int2* __restrict__ ell) {
+                           int* __restrict__ rank_row, int* __restrict__ q_ly, float4* __restrict__ q_wy,
+                           int* __restrict__ cell_cursor, int* __restrict__ row_cursor, int2* __restrict__ ell) {
     const int P = min(*runs, cap);
     const int h = w / 2;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
@@ -481,6 +482,9 @@ __global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny, int w,
         const int c = wrapmod(ly, ny);
         const int q = ly_first[c] + atomicAdd(&cell_cursor[c], 1);
         rank_row[q] = p;
+        q_ly[q] = ly;
+        q_wy[2 * q] = reinterpret_cast<const float4*>(row_wy)[2 * p];
+        q_wy[2 * q + 1] = reinterpret_cast<const float4*>(row_wy)[2 * p + 1];
         int k[8];                                      // w <= 8: the slot claims overlap
 #pragma unroll
         for (int t = 0; t < 8; ++t)

@@ -118,10 +118,10 @@ void launch_adj_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float
 }
 
 void launch_fwd_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float2* img, FftTables tab,
-                           const float* deap_y, const float* deap_x, const int* row_ly, const float* row_wy, int w,
+                           const float* deap_y, const float* deap_x, const int* q_ly, const float* q_wy, int w,
                            float2* F) {
 #define L(LG) k_fwd_cols_pulse<LG><<<Mx, Line<LG>::T, line_smem_pulse_cols<LG>(), s>>>(img, Mx, tab, deap_y, deap_x, \
-                                                                                      row_ly, row_wy, w, P, F)
+                                                                                      q_ly, q_wy, w, P, F)
     TFFR_LOGN_SWITCH(logny, L)
 #undef L
 }

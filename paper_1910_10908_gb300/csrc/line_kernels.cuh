@@ -439,7 +439,7 @@ k_adj_rows_pulse(RowsView rv, const float2* __restrict__ R, FftTables tab, const
     fft_line_epilogue_regs<LOGN, +1>(v, S.buf, tw, epi);
 }
 
-constexpr int kPulseBatch = 4;                         // pulse rows whose taps are loaded together
+constexpr int kPulseBatch = 8;                         // pulse rows whose taps are loaded together
 
 // The w azimuth taps of pulse row p, two 16-byte loads.
 __device__ __forceinline__ void load_row_taps(const float* __restrict__ row_wy, int p, float (&wy)[8]) {
@@ -536,7 +536,7 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
 template <int LOGN>
 __global__ void __cluster_dims__(kColCluster, 1, 1) __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
 k_fwd_cols_pulse(const float2* __restrict__ img, int Mx, FftTables tab, const float* __restrict__ deap_y,
-                 const float* __restrict__ deap_x, const int* __restrict__ row_ly, const float* __restrict__ row_wy,
+                 const float* __restrict__ deap_x, const int* __restrict__ q_ly, const float* __restrict__ q_wy,
                  int w, int P, float2* __restrict__ F) {
     using L = Line<LOGN>;
     constexpr int NY = L::N, MY = NY / 2, V = L::V;
@@ -571,16 +571,18 @@ k_fwd_cols_pulse(const float2* __restrict__ img, int Mx, FftTables tab, const fl
     }
     cluster.sync();
     fft_line_smem<LOGN, -1>(S.buf, tw);
-    // transposed azimuth taps: F_p = sum_s phi_y(s - (w/2 - 1) - fy_p) line[ly_p - (w/2 - 1) + s]
+    // transposed azimuth taps, per place q in fine-y order (a warp's lanes
+    // read neighbouring cells of the line):
+    // F_q = sum_s phi_y(s - (w/2 - 1) - fy_q) line[ly_q - (w/2 - 1) + s]
     const int h = w / 2;
     for (int base = 0; base < P; base += kPulseBatch * L::T) {
         int c0[kPulseBatch];
         float wy[kPulseBatch][8];
 #pragma unroll
         for (int b = 0; b < kPulseBatch; ++b) {
-            const int p = min(base + tid + b * L::T, P - 1);
-            c0[b] = __ldg(&row_ly[p]) - (h - 1);
-            load_row_taps(row_wy, p, wy[b]);
+            const int q = min(base + tid + b * L::T, P - 1);
+            c0[b] = __ldg(&q_ly[q]) - (h - 1);
+            load_row_taps(q_wy, q, wy[b]);
         }
 #pragma unroll
         for (int b = 0; b < kPulseBatch; ++b) {
@@ -626,14 +628,15 @@ k_fwd_rows_pulse(RowsView rv, const float2* __restrict__ F, FftTables tab, float
     constexpr int NX = L::N, MX = NX / 2;
     extern __shared__ float2 smem[];
     LineSmem<LOGN> S(smem);
-    const int p = blockIdx.x;
+    const int q = blockIdx.x;                          // place in fine-y order: row q of F
+    const int p = rv.rank_row[q];
     const int tid = threadIdx.x;
     const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
     // line position j holds mode j (j < MX/2) or j - NX (j >= NX - MX/2), i.e.
     // F column j + MX/2 or j - (NX - MX/2); the middle is zero.  Loaded straight
     // into the first FFT stage's registers (position tid + u T).
     float2 v[L::V];
-    const float2* Fp = F + (size_t)p * MX;
+    const float2* Fp = F + (size_t)q * MX;
 #pragma unroll
     for (int u = 0; u < L::V; ++u) {
         const int j = tid + u * L::T;

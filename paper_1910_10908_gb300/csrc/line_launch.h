@@ -25,18 +25,19 @@ void launch_fwd_cols(int logny, int Mx, cudaStream_t s, const float2* img, FftTa
 void launch_fwd_rows(int lognx, int ny, bool rows, cudaStream_t s, const RowsView& rv, const GeneralView& gv,
                      const float2* T, int w, const TapPoly& tp, FftTables tab, float2* R, float2* acc);
 
-// Pulse-row order (rows layout, P <= M_y): F replaces T.  The adjoint keeps
-// F by blocks of four columns, [Mx / 4][ldq][4] with ldq = P rounded up to 4:
-// the x pass, launched in fine-y order (block q takes pulse row
-// rv.rank_row[q]), writes entry q of every column.  The forward twin keeps F by rows, [P][Mx], row p for pulse
-// row p.  row_wy: [P][8] azimuth taps of each pulse row.
+// Pulse-row order (rows layout, P <= M_y): F replaces T, indexed by place q
+// in fine-y order (pulse row rv.rank_row[q]).  The adjoint keeps F by blocks
+// of four columns, [Mx / 4][ldq][4] with ldq = P rounded up to 4: its x pass,
+// block q, writes entry q of every column.  The forward twin keeps F by rows,
+// [P][Mx]: its column pass writes row q from the taps of place q (q_ly: y
+// cell, q_wy: [P][8] azimuth taps), its x pass reads it.
 void launch_adj_rows_pulse(int lognx, int P, cudaStream_t s, const RowsView& rv, const float2* R, FftTables tab,
                            const float* deap_x, float2* F);
 // ell: [K][2 My] azimuth-tap table of the fine rows (place q in F's columns, weight).
 void launch_adj_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float2* F, FftTables tab,
                            const int2* ell, int K, const float* deap_y, float2* img);
 void launch_fwd_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float2* img, FftTables tab,
-                           const float* deap_y, const float* deap_x, const int* row_ly, const float* row_wy, int w,
+                           const float* deap_y, const float* deap_x, const int* q_ly, const float* q_wy, int w,
                            float2* F);
 void launch_fwd_rows_pulse(int lognx, int P, cudaStream_t s, const RowsView& rv, const float2* F, FftTables tab,
                            float2* R);

@@ -92,6 +92,8 @@ struct tffr_plan_s {
     DevBuf<float2> R;
     DevBuf<int> tap_start;                 // [ny + 1] taps of each fine row
     DevBuf<int> rank_row;                  // [cap] pulse row at each place in fine-y order
+    DevBuf<int> q_ly;                      // [cap] y cell of the pulse row at each place
+    DevBuf<float> q_wy;                    // [cap][8] its azimuth taps
     DevBuf<TapEntry> tap_list;             // [P * w]
 
     // general points
@@ -462,6 +464,8 @@ int reserve_rows(tffr_plan_s* p, int cap) {
     CK(grow(p, p->row_lam_y, cap));
     CK(grow(p, p->row_off, cap));
     CK(grow(p, p->rank_row, cap));
+    CK(grow(p, p->q_ly, cap));
+    CK(grow(p, p->q_wy, (int64_t)cap * 8));
     CK(grow(p, p->row_wy, (int64_t)cap * 8));
     CK(grow(p, p->tap_list, (int64_t)cap * w));
     k_fill_int<<<grid_for(cap, 256), 256, 0, p->stream>>>(cap, kIntMax, p->row_min.ptr);
@@ -525,7 +529,8 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     CK(grow(p, p->ell, (int64_t)kEllMax * ny));
     CK(cudaMemsetAsync(p->ell.ptr, 0, (size_t)kEllMax * ny * sizeof(int2), p->stream));
     k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, ly_first,
-                                            p->rank_row.ptr, ly_first + ny, p->cursor.ptr, p->ell.ptr);
+                                            p->rank_row.ptr, p->q_ly.ptr, reinterpret_cast<float4*>(p->q_wy.ptr),
+                                            ly_first + ny, p->cursor.ptr, p->ell.ptr);
     CK_LAUNCH("k_ell_fill");
     CK(cudaEventSynchronize(p->readback));
     int hs[5];
@@ -674,7 +679,7 @@ int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_we
     STAGE_BEGIN(TFFR_STAGE_FWD_COL_FFT);
     if (pulse) {
         launch_fwd_cols_pulse(p->logny, p->Mx, p->P, p->stream, image, tables_y(p), p->deap_y.ptr, p->deap_x.ptr,
-                              p->row_ly.ptr, p->row_wy.ptr, p->w, p->T.ptr);
+                              p->q_ly.ptr, p->q_wy.ptr, p->w, p->T.ptr);
         CK_LAUNCH("k_fwd_cols_pulse");
     } else {
         launch_fwd_cols(p->logny, p->Mx, p->stream, image, tables_y(p), p->deap_y.ptr, p->deap_x.ptr, p->T.ptr);
@@ -910,7 +915,7 @@ int tffr_destroy(tffr_plan_t p) {
     release(p->row_min); release(p->row_max); release(p->row_end); release(p->row_wy);
     release(p->ell);
     release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);
-    release(p->tap_start); release(p->tap_list); release(p->rank_row);
+    release(p->tap_start); release(p->tap_list); release(p->rank_row); release(p->q_ly); release(p->q_wy);
     release(p->lx); release(p->ly); release(p->perm); release(p->slx); release(p->cursor);
     release(p->fx); release(p->fy); release(p->sfx); release(p->sfy); release(p->sD); release(p->acc);
     for (auto& sp : p->prof)
