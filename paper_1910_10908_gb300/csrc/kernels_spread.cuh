@@ -197,7 +197,7 @@ k_spread_deferred(RowsView rv, int nx, int Mx, int My, const double* __restrict_
 
 // Forward, last step: y_n = D_n sum_s phi(c_s - u_n) R_p[c_s] (or without D_n).
 template <typename VT, int W>
-__global__ void __launch_bounds__(kSpreadThreads)
+__global__ void __launch_bounds__(kSpreadThreads, 4)
 k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __restrict__ lam_x,
               const float2* __restrict__ R, WeightArgs wa, TapPoly tp, int apply_weights, void* __restrict__ out) {
     constexpr int H = W / 2;
@@ -244,17 +244,24 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
         }
         return cscale(acc, d);
     };
-    // two samples per thread and round: two independent chains of loads
+    // two samples per thread and round (two independent chains of loads);
+    // the next round's coordinates are loaded before this round's work
     const int64_t step = blockDim.x;
-    for (int64_t n = s0 + threadIdx.x; n < s1; n += 2 * step) {
+    int64_t n = s0 + threadIdx.x;
+    double lam0 = (n < s1) ? lam_x[n] : 0.0;
+    double lam1 = (n + step < s1) ? lam_x[n + step] : 0.0;
+    for (; n < s1; n += 2 * step) {
         const int64_t n1 = n + step;
         const bool two = n1 < s1;
-        const double lam0 = lam_x[n];
-        const double lam1 = two ? lam_x[n1] : lam0;
+        const int64_t m = n + 2 * step;
+        const double next0 = (m < s1) ? lam_x[m] : 0.0;
+        const double next1 = (m + step < s1) ? lam_x[m + step] : 0.0;
         const float2 y0 = interp(n, lam0);
-        const float2 y1 = interp(two ? n1 : n, lam1);
+        const float2 y1 = interp(two ? n1 : n, two ? lam1 : lam0);
         ValueIO<VT>::store(out, n, y0);
         if (two) ValueIO<VT>::store(out, n1, y1);
+        lam0 = next0;
+        lam1 = next1;
     }
 }
 
