@@ -153,6 +153,25 @@ def test_stripmap_4096_sampled_pixels_bench_configuration():
     assert rel_l2(img[jy, jx], ref) <= TOL
 
 
+def test_stripmap_4096_forward_twin_sampled_bench_configuration():
+    """The forward twin at the bench size (pulse-row order), at sampled samples: the first
+    and last sample of the data, and random ones.  D_n depends on lam_x_n alone (range-only
+    weights), so the oracle's D is taken at those samples only."""
+    from paper_1910_10908_gb300 import Plan
+    wl = make_workload("stripmap_4096")
+    g = np.random.default_rng(24)
+    f = (g.standard_normal((wl.M, wl.M)) + 1j * g.standard_normal((wl.M, wl.M))).astype(np.complex64)
+    with Plan(wl.M) as plan:
+        plan.set_points(dev(wl.lam_x), dev(wl.lam_y))
+        plan.weights(count=False)
+        assert plan.info()["pulse_order"] == 1
+        y = plan.forward(dev(f)).cpu().numpy()
+    idx = np.concatenate([[0, wl.N - 1], g.integers(0, wl.N, 78)])
+    Dn = oracle.tffr_weights(wl.lam_x[idx], wl.M)
+    ref = Dn * oracle.forward_samples(wl.lam_x, wl.lam_y, f, None, idx=idx)
+    assert rel_l2(y[idx], ref) <= TOL
+
+
 @pytest.mark.parametrize("apply_weights", [True, False])
 def test_forward_twin_vs_oracle(apply_weights):
     from paper_1910_10908_gb300 import Plan
