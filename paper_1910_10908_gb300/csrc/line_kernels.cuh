@@ -621,6 +621,18 @@ k_fwd_cols_pulse(const float2* __restrict__ img, int Mx, FftTables tab, const fl
     cluster_wait();
 }
 
+// Forward x-pass epilogue: line cell o goes to the row buffer at
+// (o - clo) mod N when that is below len.
+template <int LOGN>
+struct RowCells {
+    int clo, len;
+    float2* Rp;
+    __device__ __forceinline__ void operator()(int o, float2 v) const {
+        const int i = wrapmod(o - clo, 1 << LOGN);
+        if (i < len) Rp[i] = v;
+    }
+};
+
 template <int LOGN>
 __global__ void __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
 k_fwd_rows_pulse(RowsView rv, const float2* __restrict__ F, FftTables tab, float2* __restrict__ R) {
@@ -644,10 +656,10 @@ k_fwd_rows_pulse(RowsView rv, const float2* __restrict__ F, FftTables tab, float
              : (j >= NX - MX / 2) ? __ldg(&Fp[j - (NX - MX / 2)]) : make_float2(0.f, 0.f);
     }
     __syncthreads();                                   // twiddles in place
-    fft_line_regs<LOGN, -1>(v, S.buf, tw);
-    const int len = rv.row_len[p], clo = rv.row_clo[p];
-    float2* Rp = R + rv.row_off[p];
-    for (int i = tid; i < len; i += L::T) Rp[i] = S.buf[L::pad(wrapmod(clo + i, NX))];
+    // the last stage hands each line cell to the epilogue, which stores the
+    // cells of the row buffer (cell clo + i at R_p[i], i < len) and drops the rest
+    RowCells<LOGN> epi{rv.row_clo[p], rv.row_len[p], R + rv.row_off[p]};
+    fft_line_epilogue_regs<LOGN, -1>(v, S.buf, tw, epi);
 }
 
 // ---------------------------------------------------------------------------
