@@ -244,8 +244,8 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
         }
         return cscale(acc, d);
     };
-    // two samples per thread and round (two independent chains of loads);
-    // the next round's coordinates are loaded before this round's work
+    // two samples per thread and iteration (two independent chains of loads);
+    // the next iteration's coordinates are loaded before this iteration's work
     const int64_t step = blockDim.x;
     int64_t n = s0 + threadIdx.x;
     double lam0 = (n < s1) ? lam_x[n] : 0.0;
