@@ -123,6 +123,58 @@ def test_diagonal_from_dense_matrices_built_by_quadrature():
         assert np.allclose(ow.tffr_weights(lam, M, tau=tau), D_ref_t, atol=1e-11)
 
 
+def _quad2_nodes(n=48):
+    """2-D Gauss-Legendre nodes and weights on [-1/2, 1/2]^2, split at t = 0 on each axis
+    (the window exp(-a|t|) has a kink there): n points per half-axis."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    t = np.concatenate([-0.25 + 0.25 * x, 0.25 + 0.25 * x])     # [-1/2, 0] and [0, 1/2]
+    wt = np.concatenate([0.25 * w, 0.25 * w])
+    TX, TY = np.meshgrid(t, t, indexing="ij")
+    return TX, TY, np.outer(wt, wt)
+
+
+def test_separable_weights_from_dense_2d_matrices_built_by_quadrature():
+    """The separable variant on a tensor-product frame: the 2-D window is w(tx) w(ty), and
+    Psi[p, m] = <e^{2 pi i lam_p . t}, e^{2 pi i l_m . t} / w2(t)>, W[m, p] = w2_hat(l_m - lam_p)
+    are built by 2-D quadrature over [-1/2, 1/2]^2 on an Mx x My grid with Mx != My, banded by
+    |lam_x - l_x| < q and |lam_y - l_y| < q (both grid edges truncate).  diag(Psi W),
+    R_tau(pinv) with the threshold on the product, match the oracle's separable branch; a
+    mistake that uses lam_x or Mx for both factors, or thresholds each factor, would not."""
+    Mx, My, q = 8, 4, 3.0
+    lam_x = np.array([-3.6, 0.5, 2.25, 3.9, 0.0])
+    lam_y = np.array([0.3, -1.5, 1.7, -0.02, 0.5])
+    lx_grid = np.arange(-Mx // 2, Mx // 2, dtype=float)
+    ly_grid = np.arange(-My // 2, My // 2, dtype=float)
+    TX, TY, WQ = _quad2_nodes()
+    w2 = np.exp(-A * np.abs(TX)) * np.exp(-A * np.abs(TY))
+    G = np.zeros(lam_x.shape[0], complex)
+    for p in range(lam_x.shape[0]):
+        for lx_m in lx_grid:
+            for ly_m in ly_grid:
+                if not (abs(lam_x[p] - lx_m) < q and abs(lam_y[p] - ly_m) < q):
+                    continue
+                ph = 2j * np.pi * ((lam_x[p] - lx_m) * TX + (lam_y[p] - ly_m) * TY)
+                psi = np.sum(WQ * np.exp(ph) / w2)          # <e^{2 pi i lam.t}, e^{2 pi i l.t}/w2>
+                wh = np.sum(WQ * w2 * np.exp(ph))           # w2_hat(l - lam) = int w2 e^{-2 pi i (l - lam).t}
+                G[p] += psi * wh
+    assert np.max(np.abs(G.imag)) < 1e-12
+    Gx = ow.diag_psi_w(lam_x, Mx, q, A)
+    Gy = ow.diag_psi_w(lam_y, My, q, A)
+    assert np.allclose(Gx * Gy, G.real, rtol=0, atol=1e-11)
+    D_ref = np.diag(np.linalg.pinv(np.diag(G.real)))
+    decided_differently = False
+    for tau in (0.97, 1.02, 1.1):
+        D_sep = ow.tffr_weights(lam_x, Mx, tau=tau, q=q, lam_y=lam_y, My=My, separable=True)
+        assert np.allclose(D_sep, np.where(D_ref >= tau, D_ref, 0.0), atol=1e-11)
+        per_factor = np.where((1 / Gx >= tau) & (1 / Gy >= tau), D_ref, 0.0)
+        decided_differently |= not np.allclose(D_sep, per_factor)
+    assert decided_differently                     # the product decision is what is tested
+    # the y edge matters: the same samples on a wide y grid give other weights
+    assert not np.allclose(Gy, ow.diag_psi_w(lam_y, 64, q, A), rtol=0, atol=1e-6)
+    assert not np.allclose(Gx * Gy, Gx * ow.diag_psi_w(lam_y, Mx, q, A), rtol=0, atol=1e-6)
+    assert not np.allclose(Gx * Gy, Gx * ow.diag_psi_w(lam_x, My, q, A), rtol=0, atol=1e-6)
+
+
 def test_weight_range_for_paper_parameters():
     """With a = 0.01, q = 3: G in [0.933, 1.0000022], so D in [1, 1.072] (tau = 0.97 keeps all)."""
     d = np.linspace(-0.5, 0.5, 2001) + 3.0
