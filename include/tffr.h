@@ -56,8 +56,8 @@ typedef enum {
     TFFR_ERR_NOT_READY = 2,   /* adjoint/forward before set_points and weights */
     TFFR_ERR_CUDA = 3,        /* a CUDA call failed; see tffr_last_error */
     TFFR_ERR_OOM = 4,         /* device allocation failed */
-    TFFR_ERR_TIMEOUT = 5      /* a bounded device wait gave up (reserved: no kernel of this
-                                 version waits on another CTA or on the host) */
+    TFFR_ERR_TIMEOUT = 5      /* a bounded device wait gave up (the batch's column items wait
+                                 for their patch's rows; see tffr_batch_wait) */
 } tffr_status;
 
 /* Storage type of the sample values read by tffr_adjoint (and written by
@@ -204,6 +204,120 @@ int tffr_adjoint(tffr_plan_t plan, const void* values, void* image);
 int tffr_forward(tffr_plan_t plan, const void* image, void* values, int apply_weights);
 
 /*
+ * The unweighted adjoint f = E^H y (Eq. (fstraight) with alpha_n = 1), the
+ * Hermitian transpose of tffr_forward with apply_weights = 0; it serves as that
+ * map's backward pass.  Arguments, ordering and errors as tffr_adjoint.
+ */
+int tffr_adjoint_unweighted(tffr_plan_t plan, const void* values, void* image);
+
+/*
+ * Gradient of a real loss L with respect to real frame weights D (the
+ * backward of tffr_adjoint in the D argument): for f = E^H D y and
+ * grad_image = dL/d conj(f),
+ *     grad_D[n] = Re( conj((E grad_image)_n) * y_n ),
+ * the unweighted forward twin of grad_image times the samples, fused into the
+ * forward's last pass.  grad_image: device complex64 [My][Mx]; values: device,
+ * N samples y_n in the plan's value type; grad_D: device float[N], fully
+ * overwritten.  Ordered on the plan's stream, no synchronisation.
+ * Errors: as tffr_forward.
+ */
+int tffr_weight_grad(tffr_plan_t plan, const void* grad_image, const void* values, float* grad_D);
+
+/*
+ * Conjugate gradients on the weighted normal equations E^H D E f = E^H D y,
+ * started from f = 0: the least-squares image refining the one-step tFFR
+ * image E^H D y (which is the first CG direction).  E^H D E is applied by the
+ * Toeplitz operator when use_toeplitz != 0 (after tffr_normal_setup), else as
+ * the unweighted forward twin followed by the weighted adjoint.  Exactly
+ * iters iterations run; every vector update and reduction is a kernel on the
+ * plan's stream (step sizes are device scalars), so nothing synchronises
+ * unless residuals is given.  values: device, N samples in the plan's value
+ * type.  image: device complex64 [My][Mx], receives f.  residuals (nullable,
+ * host double[iters + 1]): ||b - E^H D E f_k|| by the CG recurrence, k =
+ * 0..iters; asking for them synchronises the stream.  The plan keeps three
+ * My x Mx work images (and N samples without the Toeplitz operator),
+ * allocated on first use.
+ * Errors: NOT_READY before points and weights, or use_toeplitz before
+ * tffr_normal_setup; INVALID_ARG for NULL pointers or iters outside
+ * [0, 100000]; OOM; CUDA.
+ */
+int tffr_cg(tffr_plan_t plan, const void* values, void* image, int iters, int use_toeplitz, double* residuals);
+
+/*
+ * Batches of independent reconstructions (sub-aperture patches of uneven
+ * size; the per-slice structure of Algorithm 1 repeated over patches).  A
+ * batch takes plans that each have points and weights set (pulse-row layout,
+ * complex64 values, square images of side 256, 512 or 1024, spreading width 6
+ * or 8) and fixed device buffers for each plan's samples and image.  Its
+ * adjoint runs every patch with one persistent launch per image side: blocks
+ * claim work items from a device counter, first one item per pulse row of
+ * every patch (range spread; in the pulse-row order of the passes fused with
+ * the x FFT, the row kept in shared memory), then, for patches in the
+ * fine-row order (more pulse rows than image rows), one item per fine row
+ * (azimuth taps and x FFT), then one item per image column (azimuth taps or
+ * the fine rows' column, y FFT, deapodisation, image store).  An item waits for
+ * the items of its patch it reads; the wait is bounded (1 s of device time by
+ * default) and a wait that runs out makes every later wait give up, so the
+ * launch always ends; tffr_batch_wait then returns TFFR_ERR_TIMEOUT.
+ */
+typedef struct tffr_batch_s* tffr_batch_t;
+
+#define TFFR_BATCH_MAX_CLASSES 8
+typedef struct {
+    int n_patches;
+    int n_classes;                              /* launches per adjoint: one per (image side, width) */
+    int64_t samples;                            /* samples of all patches */
+    int tuned;                                  /* 1 after tffr_batch_tune */
+    int class_side[TFFR_BATCH_MAX_CLASSES];     /* image side of each class */
+    int class_width[TFFR_BATCH_MAX_CLASSES];    /* spreading width */
+    int class_patches[TFFR_BATCH_MAX_CLASSES];  /* patches in the class */
+    int class_blocks[TFFR_BATCH_MAX_CLASSES];   /* blocks of the class's persistent launch */
+    int class_run[TFFR_BATCH_MAX_CLASSES];      /* spread samples per thread and tile */
+    float class_ms[TFFR_BATCH_MAX_CLASSES];     /* the tuner's best time of the class's launch alone (0 untuned) */
+} tffr_batch_info;
+
+/*
+ * Create a batch of n plans.  values[i] (device complex64, plan i's N samples)
+ * and images[i] (device complex64 [M][M]) stay the batch's buffers: load new
+ * samples into them between adjoints.  The batch keeps pointers into the plans:
+ * recreate it after tffr_set_points or tffr_weights on any of them.  stream:
+ * the stream tffr_batch_adjoint is ordered on (the batch forks its classes to
+ * streams of its own and joins them back).  Allocates and synchronises.
+ * Errors: INVALID_ARG (NULL pointers, n < 1, a plan outside the supported
+ * layout, value type, sides or width, or two plans of one class with different
+ * weight options or kernel shape); NOT_READY (a plan without points or
+ * weights); OOM; CUDA.
+ */
+int tffr_batch_create(const tffr_plan_t* plans, int n, const void* const* values, void* const* images,
+                      tffr_stream_t stream, tffr_batch_t* out);
+
+/* Every patch's adjoint (its plan's weights, Eq. (fstraight) with alpha_n = D_n)
+ * into its image.  Ordered on the batch's stream; allocates nothing and does
+ * not synchronise, so it can be captured into a CUDA graph.  Errors: CUDA. */
+int tffr_batch_adjoint(tffr_batch_t batch);
+
+/* Synchronise the batch's stream and report (and clear) a timed-out wait of an
+ * earlier adjoint: TFFR_ERR_TIMEOUT, else TFFR_OK.  Errors: CUDA. */
+int tffr_batch_wait(tffr_batch_t batch);
+
+/* Autotuner: for each class, time reps launches of every candidate (spread
+ * samples per thread and tile 4, 8, 16; blocks per SM 1, 2, 4, ... up to what
+ * fits) and keep the fastest; tffr_batch_get_info reports the choice.
+ * Synchronises.  Errors: INVALID_ARG (reps outside [1, 1000]); CUDA; TIMEOUT. */
+int tffr_batch_tune(tffr_batch_t batch, int reps);
+
+/* Limit of one wait of a column item for its patch's rows, in seconds of device
+ * time (0 < wait_s <= 60; default 1).  hold_rows != 0 makes row items skip
+ * publishing their completion, so that every wait runs out: a test of the
+ * timeout path that faults and hangs nothing.  Errors: INVALID_ARG. */
+int tffr_batch_set_wait(tffr_batch_t batch, double wait_s, int hold_rows);
+
+int tffr_batch_get_info(tffr_batch_t batch, tffr_batch_info* info);
+
+/* Free the batch (after synchronising its streams); the plans stay. NULL is a no-op. */
+int tffr_batch_destroy(tffr_batch_t batch);
+
+/*
  * Per-stage timing with CUDA events recorded on the plan's stream around each
  * stage's kernels.  enable != 0 starts (and resets) recording, 0 stops it.
  * Recording costs two event records per stage launch.
@@ -237,7 +351,13 @@ int tffr_profile_read(tffr_plan_t plan, double* ms, int64_t* count, int nstages)
  * before any stream capture.  Every call shares the array, so calls that
  * overlap on the GPU (several streams, several host threads) race: serialise
  * them.
- * Errors: INVALID_ARG for bad sizes, options or NULL pointers; CUDA.
+ * In USER mode D_out must not overlap user_D: the kernel reads one while it
+ * writes the other, so an overlap returns INVALID_ARG (copy the weights first).
+ * n_kept reads the count back with a pageable copy and a stream
+ * synchronisation, neither of which may run while the stream is captured:
+ * pass n_kept = NULL there.
+ * Errors: INVALID_ARG for bad sizes, options, NULL pointers or D_out
+ * overlapping user_D; CUDA.
  */
 int tffr_weights_noalloc(int64_t N, const double* lam_x, const double* lam_y, int Mx, int My,
                          const tffr_weight_opts* opts, float* D_out, int64_t* n_kept, tffr_stream_t stream);

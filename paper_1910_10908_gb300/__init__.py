@@ -21,7 +21,9 @@ from ._abi import VALUES, LAYOUTS, ORDERS, WEIGHT_MODES
 
 __all__ = ["TffrError", "Plan", "tffr_plan", "tffr_set_points", "tffr_weights", "tffr_adjoint",
            "tffr_forward", "tffr_destroy", "tffr_plan_get_info", "tffr_profile", "tffr_profile_read",
-           "tffr_weights_noalloc",
+           "tffr_weights_noalloc", "tffr_adjoint_unweighted", "tffr_weight_grad", "tffr_cg",
+           "tffr_batch_create", "tffr_batch_adjoint", "tffr_batch_wait", "tffr_batch_tune",
+           "tffr_batch_set_wait", "tffr_batch_get_info", "tffr_batch_destroy",
            "load_library"]
 
 
@@ -119,6 +121,74 @@ def tffr_forward(plan, image: torch.Tensor, values: torch.Tensor, apply_weights:
            plan)
 
 
+def tffr_adjoint_unweighted(plan, values: torch.Tensor, image: torch.Tensor):
+    pv = _dev(values, "values") if values.numel() else None
+    _check(_abi.load().tffr_adjoint_unweighted(plan, pv, _dev(image, "image", torch.complex64)), plan)
+
+
+def tffr_weight_grad(plan, grad_image: torch.Tensor, values: torch.Tensor, grad_D: torch.Tensor):
+    n = values.shape[0]
+    pv = _dev(values, "values") if n else None
+    pg = _dev(grad_D, "grad_D", torch.float32) if n else None
+    _check(_abi.load().tffr_weight_grad(plan, _dev(grad_image, "grad_image", torch.complex64), pv, pg), plan)
+
+
+def tffr_cg(plan, values: torch.Tensor, image: torch.Tensor, iters: int, use_toeplitz: bool = False,
+            residuals: bool = True):
+    pv = _dev(values, "values") if values.numel() else None
+    hist = (ctypes.c_double * (int(iters) + 1))() if residuals else None
+    _check(_abi.load().tffr_cg(plan, pv, _dev(image, "image", torch.complex64), int(iters),
+                               1 if use_toeplitz else 0, hist), plan)
+    return [float(v) for v in hist] if residuals else None
+
+
+def tffr_batch_create(plans, values, images, stream=None) -> ctypes.c_void_p:
+    """A batch of plans (their handles) with fixed value and image tensors, one per plan."""
+    n = len(plans)
+    if not (len(values) == len(images) == n) or n == 0:
+        raise ValueError("one value tensor and one image per plan")
+    hp = (ctypes.c_void_p * n)(*[ctypes.c_void_p(h.value) for h in plans])
+    hv = (ctypes.c_void_p * n)(*[_dev(v, "values", torch.complex64) for v in values])
+    hi = (ctypes.c_void_p * n)(*[_dev(im, "image", torch.complex64) for im in images])
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = ctypes.c_void_p()
+    _check(_abi.load().tffr_batch_create(hp, n, hv, hi, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(out)))
+    return out
+
+
+def tffr_batch_adjoint(batch):
+    _check(_abi.load().tffr_batch_adjoint(batch))
+
+
+def tffr_batch_wait(batch):
+    """Synchronise; raises TffrError (status TIMEOUT) when a wait of an earlier adjoint ran out."""
+    _check(_abi.load().tffr_batch_wait(batch))
+
+
+def tffr_batch_tune(batch, reps: int = 5):
+    _check(_abi.load().tffr_batch_tune(batch, int(reps)))
+
+
+def tffr_batch_set_wait(batch, wait_s: float = 1.0, hold_rows: bool = False):
+    _check(_abi.load().tffr_batch_set_wait(batch, float(wait_s), 1 if hold_rows else 0))
+
+
+def tffr_batch_get_info(batch) -> dict:
+    info = _abi.tffr_batch_info()
+    _check(_abi.load().tffr_batch_get_info(batch, ctypes.byref(info)))
+    k = info.n_classes
+    out = {"n_patches": info.n_patches, "n_classes": k, "samples": info.samples, "tuned": bool(info.tuned)}
+    out["classes"] = [{"side": info.class_side[i], "width": info.class_width[i], "patches": info.class_patches[i],
+                       "blocks": info.class_blocks[i], "run": info.class_run[i], "ms": info.class_ms[i]}
+                      for i in range(min(k, 8))]
+    return out
+
+
+def tffr_batch_destroy(batch):
+    _check(_abi.load().tffr_batch_destroy(batch))
+
+
 def tffr_normal_setup(plan):
     _check(_abi.load().tffr_normal_setup(plan), plan)
 
@@ -131,7 +201,35 @@ def tffr_normal_apply(plan, image_in: torch.Tensor, image_out: torch.Tensor):
 def tffr_weights_noalloc(lam_x: torch.Tensor, lam_y: torch.Tensor, Mx: int, My: int, D_out: torch.Tensor, *,
                          mode: str = "tffr", separable: bool = False, a: float = 0.01, q: float = 3.0,
                          tau: float = 0.97, user_D: torch.Tensor | None = None, count: bool = True, stream=None):
-    """Weights without a plan and without device allocation (see include/tffr.h)."""
+    """Weights without a plan and without device allocation, for callers that cannot
+    allocate when they need them (see include/tffr.h).
+
+    N is D_out's length.  lam_x (tFFR mode), lam_y (separable mode) and user_D (user
+    mode) must hold at least N elements, and every tensor must sit on the current CUDA
+    device: the kernel indexes them up to N on that device.  count=True reads the kept
+    count back (a pageable copy and a stream synchronisation); under stream capture
+    pass count=False.
+    """
+    if D_out.dim() != 1:
+        raise ValueError("D_out must be 1-D")
+    N = int(D_out.shape[0])
+    needed = []
+    if mode == "tffr":
+        needed.append(("lam_x", lam_x))
+        if separable:
+            needed.append(("lam_y", lam_y))
+    if mode == "user":
+        if user_D is None:
+            raise ValueError("user mode needs user_D")
+        needed.append(("user_D", user_D))
+    for name, t in needed:
+        if t is None or t.dim() != 1 or int(t.shape[0]) < N:
+            raise ValueError("%s must be 1-D with at least %d elements" % (name, N))
+    if N:
+        here = torch.cuda.current_device()
+        for name, t in [("D_out", D_out), ("lam_x", lam_x), ("lam_y", lam_y), ("user_D", user_D)]:
+            if t is not None and (not t.is_cuda or t.device.index != here):
+                raise ValueError("%s must be on the current CUDA device (cuda:%d)" % (name, here))
     lib = _abi.load()
     o = _abi.tffr_weight_opts()
     lib.tffr_default_weight_opts(ctypes.byref(o))
@@ -140,7 +238,6 @@ def tffr_weights_noalloc(lam_x: torch.Tensor, lam_y: torch.Tensor, Mx: int, My: 
     o.a, o.q, o.tau = float(a), float(q), float(tau)
     if user_D is not None:
         o.user_D = _dev(user_D, "user_D", torch.float32).value
-    N = int(D_out.shape[0])
     px = _dev(lam_x, "lam_x", torch.float64) if N else None
     py = _dev(lam_y, "lam_y", torch.float64) if N else None
     pd = _dev(D_out, "D_out", torch.float32) if N else None
@@ -216,10 +313,7 @@ class Plan:
         return torch.empty(n, dtype=_VALUE_DTYPES[self.values][0], device=self.device)
 
     def adjoint(self, values: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
-        if values.dtype not in _VALUE_DTYPES[self.values]:
-            raise TypeError("values dtype %s does not match the plan's %s" % (values.dtype, self.values))
-        if self.N is not None and values.shape[0] != self.N:
-            raise ValueError("expected %d samples, got %d" % (self.N, values.shape[0]))
+        self._check_values(values)
         if out is None:
             out = torch.empty((self.My, self.Mx), dtype=torch.complex64, device=self.device)
         tffr_adjoint(self._handle(), values, out)
@@ -234,6 +328,41 @@ class Plan:
             out = torch.empty(self.N or 0, dtype=dt, device=self.device)
         tffr_forward(self._handle(), image, out, apply_weights)
         return out
+
+    def _check_values(self, values: torch.Tensor):
+        if values.dtype not in _VALUE_DTYPES[self.values]:
+            raise TypeError("values dtype %s does not match the plan's %s" % (values.dtype, self.values))
+        if self.N is not None and values.shape[0] != self.N:
+            raise ValueError("expected %d samples, got %d" % (self.N, values.shape[0]))
+
+    def adjoint_unweighted(self, values: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """E^H y, the Hermitian transpose of forward(apply_weights=False)."""
+        self._check_values(values)
+        if out is None:
+            out = torch.empty((self.My, self.Mx), dtype=torch.complex64, device=self.device)
+        tffr_adjoint_unweighted(self._handle(), values, out)
+        return out
+
+    def weight_grad(self, grad_image: torch.Tensor, values: torch.Tensor,
+                    out: torch.Tensor | None = None) -> torch.Tensor:
+        """Re(conj(E grad_image) * values): the gradient of a real loss with respect to real weights."""
+        self._check_values(values)
+        if tuple(grad_image.shape) != (self.My, self.Mx):
+            raise ValueError("grad_image must be [My, Mx] = [%d, %d]" % (self.My, self.Mx))
+        if out is None:
+            out = torch.empty(values.shape[0], dtype=torch.float32, device=self.device)
+        tffr_weight_grad(self._handle(), grad_image, values, out)
+        return out
+
+    def cg(self, values: torch.Tensor, iters: int = 20, toeplitz: bool = False, out: torch.Tensor | None = None,
+           residuals: bool = True):
+        """Conjugate gradients on E^H D E f = E^H D y from f = 0 (every step in the library's kernels).
+        Returns (f, residual norms for k = 0..iters, or None)."""
+        self._check_values(values)
+        if out is None:
+            out = torch.empty((self.My, self.Mx), dtype=torch.complex64, device=self.device)
+        hist = tffr_cg(self._handle(), values, out, iters, toeplitz, residuals)
+        return out, hist
 
     def normal_setup(self) -> "Plan":
         """Build the Toeplitz normal operator E^H D E for the current points and weights."""

@@ -39,6 +39,13 @@ class tffr_plan_info(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("pulse_order", ctypes.c_int)]
 
 
+class tffr_batch_info(ctypes.Structure):
+    _fields_ = [("n_patches", ctypes.c_int), ("n_classes", ctypes.c_int), ("samples", ctypes.c_int64),
+                ("tuned", ctypes.c_int), ("class_side", ctypes.c_int * 8), ("class_width", ctypes.c_int * 8),
+                ("class_patches", ctypes.c_int * 8), ("class_blocks", ctypes.c_int * 8),
+                ("class_run", ctypes.c_int * 8), ("class_ms", ctypes.c_float * 8)]
+
+
 STAGES = ["points", "weights", "spread", "row_fft", "col_fft", "fwd_col_fft", "fwd_row_fft", "interp"]
 
 
@@ -53,12 +60,25 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_int64)]),
     "tffr_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tffr_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "tffr_adjoint_unweighted": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tffr_weight_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tffr_cg": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_double)]),
     "tffr_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "tffr_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int]),
     "tffr_weights_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_int, ctypes.POINTER(tffr_weight_opts), ctypes.c_void_p,
                                             ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p]),
+    "tffr_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                         ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "tffr_batch_adjoint": (ctypes.c_int, [ctypes.c_void_p]),
+    "tffr_batch_wait": (ctypes.c_int, [ctypes.c_void_p]),
+    "tffr_batch_tune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "tffr_batch_set_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]),
+    "tffr_batch_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tffr_batch_info)]),
+    "tffr_batch_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "tffr_normal_setup": (ctypes.c_int, [ctypes.c_void_p]),
     "tffr_normal_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tffr_plan_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tffr_plan_info)]),

@@ -1,33 +1,39 @@
 """A batch of independent tFFR reconstructions (sub-aperture patches of uneven
-sizes) replayed as one CUDA graph.
+sizes).
 
-Each patch has its own plan; the plans are spread over a few streams so that
-small patches, which cannot fill the GPU on their own, run side by side.  After
-set_points and weights (which synchronise, and may allocate) the per-step work
-of every patch is its adjoint alone, which neither allocates nor synchronises,
-so the adjoints of all patches can be captured once into a CUDA graph on fixed
-value and image buffers (the side streams fork from and join back to the
-capturing stream) and replayed: one graph launch instead of a few kernel
-launches per patch.  New samples are copied into the fixed value buffers
-between replays.
+Each patch has its own plan (points and weights set once, fixed value and
+image buffers).  The batch's adjoint is one persistent launch per image side
+(tffr_batch_adjoint): blocks claim work items from a device counter, a fused
+range spread + x FFT per pulse row of every patch, then the column pass of
+every patch, so that small patches, which cannot fill the GPU on their own,
+share it without a launch of their own.  The launch neither allocates nor
+synchronises, so it is captured once into a CUDA graph and replayed; new
+samples are copied into the fixed value buffers between replays.
+
+For comparison the per-plan path stays: every patch's own tffr_adjoint, the
+plans spread over a few streams (adjoint_eager), or one after the other on one
+stream (streams=1).
 """
 
 from __future__ import annotations
 
 import torch
 
-from . import Plan
+from . import (Plan, tffr_batch_adjoint, tffr_batch_create, tffr_batch_destroy, tffr_batch_get_info,
+               tffr_batch_set_wait, tffr_batch_tune, tffr_batch_wait)
 
 
 class PatchBatch:
     """Plans, fixed value buffers and images for a list of patches.
 
     patches: list of (Mx, My, lam_x, lam_y) with device float64 coordinates
-    (kept by reference, like Plan.set_points).
+    (kept by reference, like Plan.set_points).  persistent=True builds the
+    persistent batch (square patches of side 256, 512 or 1024 with complex64
+    samples and width 6 or 8); persistent=False keeps only the per-plan path.
     """
 
     def __init__(self, patches, *, values: str = "c64", width: int = 6, device=None, streams: int = 8,
-                 **weight_opts):
+                 persistent: bool = True, **weight_opts):
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self.stream = torch.cuda.Stream(device=self.device)             # the batch's own (capturing) stream
         self.side = [torch.cuda.Stream(device=self.device) for _ in range(max(1, streams))]
@@ -41,6 +47,11 @@ class PatchBatch:
                     self.plans.append(p)
                     self.values.append(p.value_tensor())
                     self.images.append(torch.empty((My, Mx), dtype=torch.complex64, device=self.device))
+            torch.cuda.synchronize(self.device)
+            self._b = None
+            if persistent:
+                self._b = tffr_batch_create([p._handle() for p in self.plans], self.values, self.images,
+                                            stream=self.stream)
         self.graph = None
 
     @property
@@ -52,7 +63,31 @@ class PatchBatch:
         with torch.cuda.stream(self.stream):
             self.values[k].copy_(values, non_blocking=True)
 
-    def _adjoints(self):
+    def _persistent(self):
+        if self._b is None:
+            raise RuntimeError("built without the persistent batch")
+        return self._b
+
+    def adjoint(self):
+        """Every patch's adjoint by the persistent launches, ordered on the batch stream."""
+        tffr_batch_adjoint(self._persistent())
+
+    def wait(self):
+        """Synchronise; raises TffrError (TIMEOUT) if a launch's wait ran out."""
+        tffr_batch_wait(self._persistent())
+
+    def tune(self, reps: int = 5) -> dict:
+        """Autotune the persistent launches (blocks per SM, spread run length); returns info()."""
+        tffr_batch_tune(self._persistent(), reps)
+        return self.info()
+
+    def set_wait(self, wait_s: float = 1.0, hold_rows: bool = False):
+        tffr_batch_set_wait(self._persistent(), wait_s, hold_rows)
+
+    def info(self) -> dict:
+        return tffr_batch_get_info(self._persistent())
+
+    def _adjoints_per_plan(self):
         # fork: every side stream waits for the batch stream, runs its patches,
         # and the batch stream waits for all of them
         for st in self.side:
@@ -63,17 +98,22 @@ class PatchBatch:
             self.stream.wait_stream(st)
 
     def adjoint_eager(self):
-        """Every patch's adjoint, ordered after the batch stream's prior work and
-        before its later work."""
-        self._adjoints()
+        """Every patch's own tffr_adjoint on the side streams, ordered after the batch
+        stream's prior work and before its later work."""
+        self._adjoints_per_plan()
 
-    def capture(self):
-        """Record every patch's adjoint into one CUDA graph (once)."""
-        self.adjoint_eager()                       # warm: every kernel has run once
+    def capture(self, persistent: bool | None = None):
+        """Record every patch's adjoint into one CUDA graph (once): the persistent launches,
+        or (persistent=False) the per-plan calls."""
+        if persistent is None:
+            persistent = self._b is not None
+        run = self.adjoint if persistent else self._adjoints_per_plan
+        with torch.cuda.stream(self.stream):
+            run()                                  # warm: every kernel has run once
         self.stream.synchronize()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph, stream=self.stream):
-            self._adjoints()
+            run()
         return self
 
     def replay(self):
@@ -84,6 +124,9 @@ class PatchBatch:
 
     def close(self):
         self.graph = None
+        if self._b is not None:
+            tffr_batch_destroy(self._b)
+            self._b = None
         for p in self.plans:
             p.close()
         self.plans = []

@@ -1,7 +1,8 @@
 """Build the tFFR CUDA library (csrc/*.cu -> _tffr.so) for sm_103a, in-tree.
 
-Two translation units (the C ABI with the point/spread kernels, and the FFT
-line kernels) compiled in parallel, one -gencode, static CUDA runtime.
+Three translation units (the C ABI with the point/spread kernels, the FFT
+line kernels, the persistent batch kernels) compiled in parallel, one
+-gencode, static CUDA runtime.
 """
 
 from __future__ import annotations
@@ -15,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "_tffr.so")
-SOURCES = [os.path.join(CSRC, "tffr.cu"), os.path.join(CSRC, "line_kernels.cu")]
+SOURCES = [os.path.join(CSRC, "tffr.cu"), os.path.join(CSRC, "line_kernels.cu"), os.path.join(CSRC, "batch.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(ROOT, "include", "tffr.h"), os.path.abspath(__file__)]
 

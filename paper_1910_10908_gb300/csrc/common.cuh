@@ -112,8 +112,13 @@ static __device__ __noinline__ FineCoord fine_coord_general(double v) {
 // Spreading-kernel taps as polynomials in t = 2f - 1 (f the fine-cell offset
 // in [0, 1]): tap s (fine cell floor(u) - (w/2 - 1) + s) has weight
 // P_s(t) = sum_k c[s][k] t^k, fitted at plan time in FP64 to the ES kernel
-// phi(s - (w/2 - 1) - f).  phi is even, so P_{w-1-s}(t) = P_s(-t).
-constexpr int kTapCoefs = 11;                   // degree 10
+// phi(s - (w/2 - 1) - f).  phi is even, so P_{w-1-s}(t) = P_s(-t).  The fit
+// stops at the kernel's own floor, the jump e^{-beta} at the edge of its
+// support (1e-6 at w = 6): degree 7 for w <= 6 reaches it (1.6e-6 against
+// 1.5e-6 at degree 10), w = 8 needs degree 8 (1.6e-8).  Coefficients past the
+// fitted degree are zero.
+constexpr int kTapCoefs = 11;                   // storage (degree <= 10)
+__host__ __device__ constexpr int tap_coefs(int w) { return w <= 6 ? 8 : 9; }
 struct TapPoly {
     float c[8][kTapCoefs];
 };
@@ -128,16 +133,18 @@ __device__ __forceinline__ float tap_eval(const TapPoly& P, int s, float t) {
 // All W taps; mirrored pairs share the even and odd parts in t^2.
 template <int W>
 __device__ __forceinline__ void taps_all(const TapPoly& P, float f, float (&wt)[W]) {
+    constexpr int NC = tap_coefs(W);
+    constexpr int TOP_E = (NC - 1) & ~1, TOP_O = ((NC - 2) | 1);        // highest even / odd power
     const float t = 2.0f * f - 1.0f;
     const float t2 = t * t;
 #pragma unroll
     for (int s = 0; s < W / 2; ++s) {
-        float e = P.c[s][kTapCoefs - 1];        // degree 10: even part has c0, c2, ..., c10
+        float e = P.c[s][TOP_E];
 #pragma unroll
-        for (int k = kTapCoefs - 3; k >= 0; k -= 2) e = fmaf(e, t2, P.c[s][k]);
-        float o = P.c[s][kTapCoefs - 2];        // odd part: c1, c3, ..., c9
+        for (int k = TOP_E - 2; k >= 0; k -= 2) e = fmaf(e, t2, P.c[s][k]);
+        float o = P.c[s][TOP_O];
 #pragma unroll
-        for (int k = kTapCoefs - 4; k >= 1; k -= 2) o = fmaf(o, t2, P.c[s][k]);
+        for (int k = TOP_O - 2; k >= 1; k -= 2) o = fmaf(o, t2, P.c[s][k]);
         wt[s] = fmaf(t, o, e);
         wt[W - 1 - s] = fmaf(-t, o, e);
     }
@@ -194,9 +201,11 @@ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
+// p points into shared memory: two reductions (no value returned).
 __device__ __forceinline__ void atomic_add_f2_shared(float2* p, float2 v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v.x) : "memory");
+    asm volatile("red.shared.add.f32 [%0+4], %1;" ::"r"(a), "f"(v.y) : "memory");
 }
 
 }  // namespace tffr

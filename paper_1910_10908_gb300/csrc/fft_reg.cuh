@@ -46,6 +46,11 @@ __device__ __forceinline__ float2 rot32(float2 z) {
 
 template <int R> struct Dft;
 
+template <> struct Dft<1> {
+    template <int SGN>
+    static __device__ __forceinline__ void run(float2*) {}
+};
+
 template <> struct Dft<2> {
     template <int SGN>
     static __device__ __forceinline__ void run(float2* v) {
@@ -111,6 +116,41 @@ template <> struct Dft<32> {
 };
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
+// z * exp(SGN * 2 pi i m / 32), m known once the caller's loops are unrolled.
+template <int SGN>
+__device__ __forceinline__ float2 rot32_folded(float2 z, int m) {
+    m &= 31;
+    if (m == 0) return z;
+    if (m == 8) return SGN > 0 ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+    if (m == 16) return make_float2(-z.x, -z.y);
+    if (m == 24) return SGN > 0 ? make_float2(z.y, -z.x) : make_float2(-z.y, z.x);
+    const float c = w32c(m), s = (SGN > 0) ? w32s(m) : -w32s(m);
+    return make_float2(z.x * c - z.y * s, z.x * s + z.y * c);
+}
+
+// The first radix-V stage (which has no twiddles) of a line whose points
+// x[tid + u T] are zero for u >= U: the V-point DFT of (x_0, .., x_{U-1}, 0, ..)
+// splits by output residue b = k mod (V / U) into U-point DFTs,
+//     X[(V/U) q + b] = sum_{u<U} (x_u W_V^{u b}) W_U^{u q},
+// with constant twiddles W_V^{u b}.  v[u] holds x_u on entry (u < U) and
+// X[k] in v[k] on return, as the full radix-V stage leaves it.
+template <int V, int U, int SGN>
+__device__ __forceinline__ void dft_first_sparse(float2 (&v)[V]) {
+    constexpr int G = V / U;
+    float2 x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) x[u] = v[u];
+#pragma unroll
+    for (int b = 0; b < G; ++b) {
+        float2 y[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) y[u] = rot32_folded<SGN>(x[u], (32 / V) * u * b);
+        Dft<U>::template run<SGN>(y);
+#pragma unroll
+        for (int q = 0; q < U; ++q) v[G * q + b] = y[q];
+    }
+}
 
 // Values per thread for an N-point line.
 __host__ __device__ constexpr int line_v(int n) {
@@ -261,12 +301,43 @@ __device__ __forceinline__ void fft_line_epilogue(float2* buf, const Twiddles& t
         for (int r = 0; r < R; ++r) epi(threadIdx.x + b * L::T + r * (L::N / R), v[b * R + r]);
 }
 
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// As fft_line_epilogue_regs (below) for a first-stage input with x[tid + u T]
+// = 0 for u >= U (U a power of two below V): the first stage takes the sparse
+// form.
+template <int LOGN, int U, int SGN, typename Epi>
+__device__ __forceinline__ void fft_line_epilogue_regs_sparse(float2 (&v)[Line<LOGN>::V], float2* buf,
+                                                              const Twiddles& tw, Epi& epi) {
+    using L = Line<LOGN>;
+    constexpr int NSMEM = L::REM ? L::NFULL : L::NFULL - 1;
+    constexpr int R = L::REM ? (1 << L::REM) : L::V;
+    constexpr int LOGNS = NSMEM * L::LV;
+    static_assert(NSMEM >= 1, "the first stage must not be the last");
+    static_assert(U < L::V, "sparse first stage");
+    dft_first_sparse<L::V, U, SGN>(v);
+    stage_store<LOGN, L::V, 0>(v, buf);
+    __syncthreads();
+    FullStages<LOGN, 1, NSMEM, SGN>::run(buf, tw);
+    stage_load<LOGN, R>(v, buf);
+    __syncthreads();
+    stage_compute<LOGN, R, LOGNS, SGN>(v, tw);
+    constexpr int B = L::V / R;
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+        for (int r = 0; r < R; ++r) epi(threadIdx.x + b * L::T + r * (L::N / R), v[b * R + r]);
+}
+
 // As fft_line_epilogue, but the first stage's input arrives in registers,
 // v[r] = x[tid + r T] (the layout the first stage loads); buf is free to be
-// overwritten when this is called.
-template <int LOGN, int SGN, typename Epi>
+// overwritten when this is called.  pre() runs after the last stage's
+// arithmetic, before the first epilogue call.
+template <int LOGN, int SGN, typename Epi, typename Pre = NoHook>
 __device__ __forceinline__ void fft_line_epilogue_regs(float2 (&v)[Line<LOGN>::V], float2* buf, const Twiddles& tw,
-                                                       Epi& epi) {
+                                                       Epi& epi, const Pre& pre = Pre()) {
     using L = Line<LOGN>;
     constexpr int NSMEM = L::REM ? L::NFULL : L::NFULL - 1;
     constexpr int R = L::REM ? (1 << L::REM) : L::V;
@@ -279,6 +350,7 @@ __device__ __forceinline__ void fft_line_epilogue_regs(float2 (&v)[Line<LOGN>::V
     stage_load<LOGN, R>(v, buf);
     __syncthreads();
     stage_compute<LOGN, R, LOGNS, SGN>(v, tw);
+    pre();
     constexpr int B = L::V / R;
 #pragma unroll
     for (int b = 0; b < B; ++b)

@@ -26,6 +26,7 @@ namespace tffr {
 // ---------------------------------------------------------------------------
 constexpr int kGCoefs = 16;
 constexpr int kG0Coefs = 12;       // piece 0 (the whole range for integer q): fixed length
+constexpr int kD0Coefs = 10;       // 1/G on piece 0, fitted directly (1.5e-8 at a = 0.01, q = 3)
 
 struct WeightArgs {
     int mode;              // 0 tFFR, 1 unit, 2 user (per-sample array)
@@ -37,6 +38,7 @@ struct WeightArgs {
     float vb, inv_vb;
     int n0, n1;
     float c0[kGCoefs], c1[kGCoefs];
+    float d0[kD0Coefs];    // 1/G on piece 0, same variable s (the spread's fast path)
     // closed-form parameters
     double a, q, e_minus, e_plus;
     int reach;             // ceil(q) + 1
@@ -112,7 +114,26 @@ __device__ __forceinline__ float g_fitted(int cell, float f, int M, const Weight
     return horner(A.c1, A.n1, (2.0f * v - A.vb - 0.5f) / (0.5f - A.vb));
 }
 
-__device__ __noinline__ float weight_exact_args(double lam_x, double lam_y, int Mx, int My, double a, double q,
+// 1/G (before the threshold) from the fine cell and offset: the direct fit
+// of 1/G on piece 0, else 1/G from the fitted G of piece 1; sets exact = true
+// on a truncation breakpoint (the grid edges are the caller's to check).
+__device__ __forceinline__ float d_fitted(int cell, float f, const WeightArgs& A, bool& exact) {
+    const float delta = 0.5f * ((float)(cell & 1) + f);          // lam - floor(lam)
+    const float v = fabsf(delta - 0.5f);
+    exact |= (v == A.vb) | (v == 0.5f);
+    if (v < A.vb) {
+        const float r = v * A.inv_vb;
+        const float s = fmaf(2.0f * r, r, -1.0f);
+        float d = A.d0[kD0Coefs - 1];
+#pragma unroll
+        for (int k = kD0Coefs - 2; k >= 0; --k) d = fmaf(d, s, A.d0[k]);
+        return d;
+    }
+    const float G = horner(A.c1, A.n1, (2.0f * v - A.vb - 0.5f) / (0.5f - A.vb));
+    return (G != 0.0f) ? __frcp_rn(G) : 0.0f;
+}
+
+static __device__ __noinline__ float weight_exact_args(double lam_x, double lam_y, int Mx, int My, double a, double q,
                                                 double e_minus, double e_plus, int reach, double tau, int separable) {
     double G = diag_psi_w(lam_x, Mx, a, q, e_minus, e_plus, reach);
     if (separable) G *= diag_psi_w(lam_y, My, a, q, e_minus, e_plus, reach);
@@ -193,7 +214,7 @@ struct RowScanArgs {
 
 // Error bits: 1 bad lam_y, 2 bad lam_x.  Local run index -1 marks the samples
 // of a tile that continue a row started in an earlier tile.
-__global__ void __launch_bounds__(kRowScanWarps * 32, 4)
+static __global__ void __launch_bounds__(kRowScanWarps * 32, 4)
 k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y, RowScanArgs a) {
     __shared__ int s_cnt[kRowScanWarps];
     __shared__ int s_base, s_first, s_hmin, s_hmax;
@@ -333,7 +354,7 @@ k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restric
     }
 }
 
-__global__ void k_fill_int(int n, int v, int* __restrict__ a) {
+static __global__ void k_fill_int(int n, int v, int* __restrict__ a) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = v;
 }
 
@@ -347,7 +368,7 @@ __global__ void k_fill_int(int n, int v, int* __restrict__ a) {
 // each fine row (tap_count, zeroed), and how many rows have each fine y cell
 // (ly_count, zeroed).  Puts the extent arrays back to their identities for
 // the next scan.  The walk over tiles is O(tiles) in total.
-__global__ void k_row_finish(const int* __restrict__ runs, int cap, int64_t N, int ntiles,
+static __global__ void k_row_finish(const int* __restrict__ runs, int cap, int64_t N, int ntiles,
                              const int4* __restrict__ tile, const int2* __restrict__ head, int nx, int ny, int w,
                              TapPoly tp, const double* __restrict__ lam_y, const int* __restrict__ row_start,
                              int* __restrict__ row_end, int* __restrict__ row_min, int* __restrict__ row_max,
@@ -439,7 +460,7 @@ __device__ long long block_scan_items(const int* in, OutT* out, int n, long long
 // tap_count is zeroed again (the per-fine-row cursor of k_ell_fill).  Block
 // 2: ly_count[0..ny) replaced in place by its exclusive scan, the first place
 // in fine-y order of the rows of each fine y cell.
-__global__ void __launch_bounds__(kScanThreads)
+static __global__ void __launch_bounds__(kScanThreads)
 k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_len, int64_t* __restrict__ row_off,
             long long* __restrict__ total, int ny, int* tap_count, int* __restrict__ tap_start,
             int* __restrict__ max_len, int* __restrict__ max_count, int* ly_count) {
@@ -471,7 +492,7 @@ k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_l
 // the forward twin.  Slot k of fine row r then holds (q, tap weight) in
 // ell[k * ny + r]; slots past the row's count stay (0, 0).  cell_cursor and
 // row_cursor (arrivals per fine y cell and per fine row): zeroed.
-__global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny, int w, const int* __restrict__ row_ly,
+static __global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny, int w, const int* __restrict__ row_ly,
                            const float* __restrict__ row_wy, const int* __restrict__ ly_first,
                            int* __restrict__ rank_row, int* __restrict__ q_ly, float4* __restrict__ q_wy,
                            int* __restrict__ cell_cursor, int* __restrict__ row_cursor, int2* __restrict__ ell) {
@@ -497,7 +518,7 @@ __global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny, int w,
     }
 }
 
-__global__ void k_tap_fill(const int* __restrict__ runs, int cap, int ny, int w, TapPoly tp, const int* __restrict__ row_ly,
+static __global__ void k_tap_fill(const int* __restrict__ runs, int cap, int ny, int w, TapPoly tp, const int* __restrict__ row_ly,
                            const float* __restrict__ row_fy, const int* __restrict__ row_clo,
                            const int* __restrict__ row_len, const int64_t* __restrict__ row_off,
                            const int* __restrict__ start, int* __restrict__ cursor, TapEntry* __restrict__ taps) {
@@ -522,7 +543,7 @@ __global__ void k_tap_fill(const int* __restrict__ runs, int cap, int ny, int w,
 // General points: fine cells of both axes (err bit 1 on a bad coordinate),
 // then bucketing by fine row (histogram, scatter) and a sorted copy.
 // ---------------------------------------------------------------------------
-__global__ void k_prep_general(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y,
+static __global__ void k_prep_general(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y,
                                int* __restrict__ lx, float* __restrict__ fx, int* __restrict__ ly,
                                float* __restrict__ fy, int* __restrict__ err) {
     bool bad = false;
@@ -539,7 +560,7 @@ __global__ void k_prep_general(int64_t N, const double* __restrict__ lam_x, cons
     if (bad) atomicOr(err, 1);
 }
 
-__global__ void k_bucket_hist(int64_t N, int ny, const int* __restrict__ ly, int* __restrict__ hist) {
+static __global__ void k_bucket_hist(int64_t N, int ny, const int* __restrict__ ly, int* __restrict__ hist) {
     extern __shared__ int s_hist[];
     for (int i = threadIdx.x; i < ny; i += blockDim.x) s_hist[i] = 0;
     __syncthreads();
@@ -550,7 +571,7 @@ __global__ void k_bucket_hist(int64_t N, int ny, const int* __restrict__ ly, int
         if (s_hist[i]) atomicAdd(&hist[i], s_hist[i]);
 }
 
-__global__ void k_bucket_scatter(int64_t N, int ny, const int* __restrict__ ly, const int* __restrict__ bucket_start,
+static __global__ void k_bucket_scatter(int64_t N, int ny, const int* __restrict__ ly, const int* __restrict__ bucket_start,
                                  int* __restrict__ cursor, int* __restrict__ perm) {
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
         const int b = wrapmod(ly[n], ny);
@@ -559,7 +580,7 @@ __global__ void k_bucket_scatter(int64_t N, int ny, const int* __restrict__ ly, 
     }
 }
 
-__global__ void k_gather_sorted(int64_t N, const int* __restrict__ perm, const int* __restrict__ lx,
+static __global__ void k_gather_sorted(int64_t N, const int* __restrict__ perm, const int* __restrict__ lx,
                                 const float* __restrict__ fx, const float* __restrict__ fy, int* __restrict__ slx,
                                 float* __restrict__ sfx, float* __restrict__ sfy) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
@@ -573,7 +594,7 @@ __global__ void k_gather_sorted(int64_t N, const int* __restrict__ perm, const i
 // ---------------------------------------------------------------------------
 // D_n for every sample in the caller's order (D_out, n_kept, general points).
 // ---------------------------------------------------------------------------
-__global__ void k_weights(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y, int Mx,
+static __global__ void k_weights(int64_t N, const double* __restrict__ lam_x, const double* __restrict__ lam_y, int Mx,
                           int My, WeightArgs A, float* __restrict__ D, unsigned long long* __restrict__ kept) {
     int c = 0;
     for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
@@ -599,7 +620,7 @@ __global__ void k_weights(int64_t N, const double* __restrict__ lam_x, const dou
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(kept, (unsigned long long)c);
 }
 
-__global__ void k_gather_weights(int64_t N, const int* __restrict__ perm, const float* __restrict__ D,
+static __global__ void k_gather_weights(int64_t N, const int* __restrict__ perm, const float* __restrict__ D,
                                  float* __restrict__ sD) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
         sD[q] = D[perm[q]];

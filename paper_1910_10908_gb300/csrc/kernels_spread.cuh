@@ -15,11 +15,8 @@ namespace tffr {
 
 
 constexpr int kSpreadThreads = 256;
-constexpr int kSpreadPerThread = 8;                      // samples per thread per staged tile
-constexpr int kSpreadTile = kSpreadThreads * kSpreadPerThread;
-// staged lam_x and values of one tile, one pad slot per 64 samples
-constexpr int kSpreadStageElems = kSpreadTile + kSpreadTile / 64 + 1;
-constexpr int kSpreadStageBytes = kSpreadStageElems * (int)(sizeof(double) + sizeof(float2));
+constexpr int kSpreadRun = 8;                            // consecutive samples per thread per tile
+constexpr int kSpreadTile = kSpreadThreads * kSpreadRun;
 
 // Samples whose weight needs the FP64 decision (1/G within the guard band of
 // tau, a grid edge or a truncation breakpoint; rare) are not spread inline:
@@ -32,120 +29,200 @@ struct DeferList {
     int cap;                        // N: every sample is listed at most once per adjoint
 };
 
+// One thread's run of up to kSpreadRun consecutive samples of a pulse row
+// (samples move slowly along x: a run usually spans under two fine cells).
+// The run accumulates into W + 1 register cells from its first sample's first
+// tap cell `base`: a sample whose first tap cell is base + dlt, dlt in {0, 1},
+// adds tap s into cell s + dlt (a select, no branch); a sample further right
+// flushes the window into the shared row and starts a new one (rare).  D_n:
+// MODE 0 the tFFR weight (the direct FP32 fit of 1/G times the row's azimuth
+// factor, deferred to the FP64 kernel near tau, on a truncation breakpoint or,
+// for rows not inside the grid's interior, near a grid edge), 1 unit, 2 the
+// caller's array.
+// INLINE: samples that need the FP64 decision take it here (weight_exact with
+// the row's lam_y and the grid sizes Mx, My) instead of being deferred.
+// Sample i of the run comes from src.lam(i), src.val(i) (the caller's arrays
+// or a staged copy in shared memory); n0 + i is its index in the caller's order.
+template <typename VT, int W, int MODE, bool INLINE = false, typename Src>
+__device__ __forceinline__ void spread_run(int64_t n0, int i0, int i1, int p, int nx, int clo, int len, bool periodic,
+                                           int Mx, bool edges, float dy, bool dy_exact, const Src& src,
+                                           const WeightArgs& wa, const TapPoly& tp, const DeferList& defer,
+                                           float2* s_row, const float* __restrict__ user_D,
+                                           double lam_y_row = 0.0, int My = 0) {
+    constexpr int H = W / 2;
+    constexpr int kNoBase = -(1 << 30);                // below every cell (|cell| < 2^29), no overflow
+    float2 acc[W + 1];
+#pragma unroll
+    for (int s = 0; s <= W; ++s) acc[s] = make_float2(0.f, 0.f);
+    int base = kNoBase;
+    // cells base .. base + W - 1 lie inside the row buffer (every sample's taps
+    // do); cell base + W only when some sample used it, so it is checked
+    auto flush = [&]() {
+#pragma unroll
+        for (int s = 0; s <= W; ++s) {
+            const int c = base + s;
+            const int idx = periodic ? wrapmod(c, nx) : (c - clo);
+            if (s < W || idx < len) atomic_add_f2_shared(&s_row[idx], acc[s]);
+            acc[s] = make_float2(0.f, 0.f);
+        }
+    };
+    for (int i = i0; i < i1; ++i) {
+        const int64_t n = n0 + i;
+        const double lam = src.lam(i);
+        const float2 v0 = src.val(i);
+        int cell;
+        float f;
+        fine_coord(lam, cell, f);
+        float d;
+        if constexpr (MODE == 1) {
+            d = 1.0f;
+        } else if constexpr (MODE == 2) {
+            d = __ldg(&user_D[n]);
+        } else {
+            bool exact = dy_exact;
+            if (edges) {
+                const int j0 = cell >> 1;
+                exact |= (j0 - wa.reach < -(Mx / 2)) | (j0 + wa.reach >= Mx - Mx / 2);
+            }
+            d = d_fitted(cell, f, wa, exact) * dy;
+            if (exact | !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau))) {
+                if constexpr (INLINE) {
+                    d = weight_exact(lam, lam_y_row, Mx, My, wa);
+                } else {
+                    const int slot = atomicAdd(defer.count, 1);
+                    if (slot < defer.cap) defer.item[slot] = make_int2((int)n, p);
+                    d = 0.0f;
+                }
+            }
+            d = (d >= wa.tau) ? d : 0.0f;
+        }
+        const float2 v = cscale(v0, d);
+        float wt[W];
+        taps_all<W>(tp, f, wt);
+        const int c0 = cell - (H - 1);
+        int dlt = c0 - base;
+        if (dlt < 0 || dlt > 1) {                      // first sample of the run, or a jump: new window
+            if (base != kNoBase) flush();
+            base = c0;
+            dlt = 0;
+        }
+        const bool one = dlt != 0;
+        acc[0].x = fmaf(one ? 0.0f : wt[0], v.x, acc[0].x);
+        acc[0].y = fmaf(one ? 0.0f : wt[0], v.y, acc[0].y);
+#pragma unroll
+        for (int s = 1; s < W; ++s) {
+            const float w_s = one ? wt[s - 1] : wt[s];
+            acc[s].x = fmaf(w_s, v.x, acc[s].x);
+            acc[s].y = fmaf(w_s, v.y, acc[s].y);
+        }
+        acc[W].x = fmaf(one ? wt[W - 1] : 0.0f, v.x, acc[W].x);
+        acc[W].y = fmaf(one ? wt[W - 1] : 0.0f, v.y, acc[W].y);
+    }
+    if (base != kNoBase) flush();
+}
+
+// Samples read straight from the caller's arrays (index relative to n0).
+template <typename VT>
+struct GlobalSamples {
+    const double* lam_x;
+    const void* values;
+    int64_t n0;
+    __device__ __forceinline__ double lam(int i) const { return __ldg(&lam_x[n0 + i]); }
+    __device__ __forceinline__ float2 val(int i) const { return ValueIO<VT>::load(values, n0 + i); }
+};
+
+// A staged value (the caller's bytes in shared memory) as FP32 complex.
+__device__ __forceinline__ float2 to_f2(const float2& v) { return v; }
+__device__ __forceinline__ float2 to_f2(const double2& v) { return make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ float2 to_f2(const __half2& v) { return __half22float2(v); }
+__device__ __forceinline__ float2 to_f2(const __nv_bfloat162& v) { return __bfloat1622float2(v); }
+
+// A tile of samples staged in shared memory, element i at i + i / kSpreadPadEvery
+// (the runs a warp's lanes read at once then fall on different banks).
+constexpr int kSpreadPadEvery = 8 * kSpreadRun;
+__host__ __device__ constexpr int spread_pad(int i) { return i + i / kSpreadPadEvery; }
+constexpr int kSpreadStageElems = (spread_pad(kSpreadTile - 1) + 2) & ~1;   // even: the values start 16-byte aligned
+
+template <typename VT>
+struct StagedSamples {
+    const double* s_lam;
+    const VT* s_val;
+    int t0;                                            // the tile's first sample (run indices are row-relative)
+    __device__ __forceinline__ double lam(int i) const { return s_lam[spread_pad(i - t0)]; }
+    __device__ __forceinline__ float2 val(int i) const { return to_f2(s_val[spread_pad(i - t0)]); }
+};
+
+// cp.async of one element (4, 8 or 16 bytes) from global into shared memory.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Adjoint, step 1: R_p[c] = sum_{n in row p} D_n v_n phi(c - u_n) over the W
-// taps of each sample.  Samples are staged tile by tile with coalesced loads;
-// each thread then walks a contiguous run of samples (which move slowly along
-// x) and keeps the W cells under its current footprint in registers, flushing
-// a cell into the shared row (atomic add) only when the footprint moves past
-// it.  D_n is evaluated inline from lam_x (tFFR mode) or read (user mode).
+// taps of each sample.  Each tile of kSpreadTile samples is staged in shared
+// memory by asynchronous copies (coalesced, every load in flight at once);
+// thread (warp wid, lane) then walks run wid + 8 lane of the tile: the lanes of
+// a warp are 8 runs apart, so their footprints (and the shared adds of their
+// flushes) rarely overlap.
 template <typename VT, int W>
 __global__ void __launch_bounds__(kSpreadThreads, 4)
 k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __restrict__ lam_x,
               const void* __restrict__ values, WeightArgs wa, TapPoly tp, DeferList defer, float2* __restrict__ R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* s_lam = reinterpret_cast<double*>(smem_raw);
-    float2* s_val = reinterpret_cast<float2*>(s_lam + kSpreadStageElems);
-    float2* s_row = s_val + kSpreadStageElems;
+    VT* s_val = reinterpret_cast<VT*>(s_lam + kSpreadStageElems);
+    float2* s_row = reinterpret_cast<float2*>(s_val + kSpreadStageElems);
     constexpr int H = W / 2;
     const int p = blockIdx.x;
     const int len = rv.row_len[p];
     const int clo = rv.row_clo[p];
     const bool periodic = (len == nx) && (clo == 0);
     const int64_t s0 = rv.row_start[p];
-    const int64_t s1 = rv.row_end[p];
-    const int L = (int)(s1 - s0);
+    const int L = (int)(rv.row_end[p] - s0);
     const int tid = threadIdx.x;
     for (int i = tid; i < len; i += kSpreadThreads) s_row[i] = make_float2(0.f, 0.f);
-
-    // azimuth factor of the separable weight variant: one value per row
-    float gy = 1.0f;
-    bool gy_exact = false;
-    if (wa.mode == 0 && wa.separable) gy = g_fitted(rv.row_ly[p], rv.row_fy[p], My, wa, gy_exact);
-
-    // Thread (warp wid, lane) walks run number wid + 8 * lane of the tile: the
-    // lanes of a warp are 8 runs apart, so their footprints (and the shared
-    // adds of their flushes) rarely overlap.
+    // row-wide weight facts: the azimuth factor of the separable variant, and
+    // whether every sample of the row is at least q + 1 image cells inside the
+    // grid's edges (then no sample needs the per-sample edge test)
+    float dy = 1.0f;
+    bool dy_exact = false;
+    bool edges = true;
+    if (wa.mode == 0) {
+        if (wa.separable) {
+            const float gy = g_fitted(rv.row_ly[p], rv.row_fy[p], My, wa, dy_exact);
+            dy = (gy != 0.0f) ? __frcp_rn(gy) : 0.0f;
+        }
+        const int mn = clo + (H - 1), mx = clo + len - H - 1;    // fine cells of the row's samples
+        edges = periodic || (mn >> 1) - wa.reach < -(Mx / 2) || (mx >> 1) + wa.reach >= Mx - Mx / 2;
+    }
+    __syncthreads();
     const int run = (tid >> 5) + (kSpreadThreads / 32) * (tid & 31);
+    const double* __restrict__ g_lam = lam_x + s0;
+    const VT* __restrict__ g_val = reinterpret_cast<const VT*>(values) + s0;
     for (int t0 = 0; t0 < L; t0 += kSpreadTile) {
         const int cnt = min(kSpreadTile, L - t0);
-        const int chunk = (cnt + kSpreadThreads - 1) / kSpreadThreads;
-        __syncthreads();                                   // previous tile fully consumed
-        for (int i = tid; i < cnt; i += kSpreadThreads) {
-            const int k = i + (i >> 6);                    // pad: strided reads below stay off one bank
-            s_lam[k] = lam_x[s0 + t0 + i];
-            s_val[k] = ValueIO<VT>::load(values, s0 + t0 + i);
+        __syncthreads();                                   // the previous tile is consumed
+        for (int e = tid; e < cnt; e += kSpreadThreads) {
+            cp_async_elem<8>(&s_lam[spread_pad(e)], &g_lam[t0 + e]);
+            cp_async_elem<(int)sizeof(VT)>(&s_val[spread_pad(e)], &g_val[t0 + e]);
         }
+        cp_async_wait_all();
         __syncthreads();
-        const int i0 = run * chunk;
-        const int i1 = min(cnt, i0 + chunk);
-        float2 acc[W];
-#pragma unroll
-        for (int s = 0; s < W; ++s) acc[s] = make_float2(0.f, 0.f);
-        int wbase = INT_MIN;                               // first fine cell held in acc
-        for (int i = i0; i < i1; ++i) {
-            const int k = i + (i >> 6);
-            const double lam = s_lam[k];
-            int cell;
-            float f;
-            fine_coord(lam, cell, f);
-            float d;
-            if (wa.mode == 1) {
-                d = 1.0f;
-            } else if (wa.mode == 2) {
-                d = wa.user_D[s0 + t0 + i];
-            } else {
-                bool exact = gy_exact;
-                float G = g_fitted(cell, f, Mx, wa, exact) * gy;
-                d = (G != 0.0f) ? __frcp_rn(G) : 0.0f;
-                if (exact || !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau))) {
-                    const int slot = atomicAdd(defer.count, 1);
-                    if (slot < defer.cap) defer.item[slot] = make_int2((int)(s0 + t0 + i), p);
-                    continue;
-                }
-                if (d < wa.tau) d = 0.0f;
-            }
-            if (d == 0.0f) continue;
-            const float2 v = cscale(s_val[k], d);
-            float wt[W];
-            taps_all<W>(tp, f, wt);
-            const int c0 = cell - (H - 1);
-            if (c0 != wbase) {
-                if (wbase != INT_MIN && c0 > wbase && c0 - wbase < W) {
-                    // slide the footprint right, flushing the cells it leaves
-                    do {
-                        const int idx = periodic ? wrapmod(wbase, nx) : (wbase - clo);
-                        atomic_add_f2_shared(&s_row[idx], acc[0]);
-#pragma unroll
-                        for (int s = 0; s < W - 1; ++s) acc[s] = acc[s + 1];
-                        acc[W - 1] = make_float2(0.f, 0.f);
-                        ++wbase;
-                    } while (wbase < c0);
-                } else {
-                    if (wbase != INT_MIN) {
-#pragma unroll
-                        for (int s = 0; s < W; ++s) {
-                            const int idx = periodic ? wrapmod(wbase + s, nx) : (wbase + s - clo);
-                            atomic_add_f2_shared(&s_row[idx], acc[s]);
-                        }
-                    }
-#pragma unroll
-                    for (int s = 0; s < W; ++s) acc[s] = make_float2(0.f, 0.f);
-                    wbase = c0;
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < W; ++s) {
-                acc[s].x = fmaf(wt[s], v.x, acc[s].x);
-                acc[s].y = fmaf(wt[s], v.y, acc[s].y);
-            }
-        }
-        if (wbase != INT_MIN) {
-#pragma unroll
-            for (int s = 0; s < W; ++s) {
-                const int idx = periodic ? wrapmod(wbase + s, nx) : (wbase + s - clo);
-                atomic_add_f2_shared(&s_row[idx], acc[s]);
-            }
-        }
+        const int i0 = t0 + run * kSpreadRun;
+        const int i1 = min(t0 + cnt, i0 + kSpreadRun);
+        if (i0 >= i1) continue;
+        const StagedSamples<VT> src{s_lam, s_val, t0};
+        if (wa.mode == 0)
+            spread_run<VT, W, 0>(s0, i0, i1, p, nx, clo, len, periodic, Mx, edges, dy, dy_exact, src, wa, tp, defer,
+                                 s_row, wa.user_D);
+        else if (wa.mode == 1)
+            spread_run<VT, W, 1>(s0, i0, i1, p, nx, clo, len, periodic, Mx, edges, dy, dy_exact, src, wa, tp, defer,
+                                 s_row, wa.user_D);
+        else
+            spread_run<VT, W, 2>(s0, i0, i1, p, nx, clo, len, periodic, Mx, edges, dy, dy_exact, src, wa, tp, defer,
+                                 s_row, wa.user_D);
     }
     __syncthreads();
     float2* out = R + rv.row_off[p];
@@ -196,10 +273,14 @@ k_spread_deferred(RowsView rv, int nx, int Mx, int My, const double* __restrict_
 }
 
 // Forward, last step: y_n = D_n sum_s phi(c_s - u_n) R_p[c_s] (or without D_n).
-template <typename VT, int W>
+// GRAD: the gradient of a real loss with respect to real weights D instead,
+// grad[n] = Re(conj(a_n) y_n) with a_n the unweighted sum and y_n read from y_in
+// (in the value type VT).
+template <typename VT, int W, bool GRAD = false>
 __global__ void __launch_bounds__(kSpreadThreads, 4)
 k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __restrict__ lam_x,
-              const float2* __restrict__ R, WeightArgs wa, TapPoly tp, int apply_weights, void* __restrict__ out) {
+              const float2* __restrict__ R, WeightArgs wa, TapPoly tp, int apply_weights, void* __restrict__ out,
+              const void* __restrict__ y_in = nullptr) {
     constexpr int H = W / 2;
     const int p = blockIdx.x;
     const int len = rv.row_len[p];
@@ -229,7 +310,7 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
             acc.y = fmaf(wt[s], r.y, acc.y);
         }
         float d = 1.0f;
-        if (apply_weights) {
+        if (!GRAD && apply_weights) {
             if (wa.mode == 2) {
                 d = wa.user_D[n];
             } else if (wa.mode == 0) {
@@ -258,19 +339,29 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
         const double next1 = (m + step < s1) ? lam_x[m + step] : 0.0;
         const float2 y0 = interp(n, lam0);
         const float2 y1 = interp(two ? n1 : n, two ? lam1 : lam0);
-        ValueIO<VT>::store(out, n, y0);
-        if (two) ValueIO<VT>::store(out, n1, y1);
+        if constexpr (GRAD) {
+            float* g = reinterpret_cast<float*>(out);
+            const float2 v0 = ValueIO<VT>::load(y_in, n);
+            g[n] = fmaf(y0.x, v0.x, y0.y * v0.y);
+            if (two) {
+                const float2 v1 = ValueIO<VT>::load(y_in, n1);
+                g[n1] = fmaf(y1.x, v1.x, y1.y * v1.y);
+            }
+        } else {
+            ValueIO<VT>::store(out, n, y0);
+            if (two) ValueIO<VT>::store(out, n1, y1);
+        }
         lam0 = next0;
         lam1 = next1;
     }
 }
 
-// General points: values in bucket order, weighted and converted to FP32.
+// General points: values in bucket order, weighted (sD; NULL: unweighted) and converted to FP32.
 template <typename VT>
 __global__ void k_gather_values(int64_t N, const int* __restrict__ perm, const void* __restrict__ values,
                                 const float* __restrict__ sD, float2* __restrict__ sval) {
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
-        sval[q] = cscale(ValueIO<VT>::load(values, perm[q]), sD[q]);
+        sval[q] = cscale(ValueIO<VT>::load(values, perm[q]), sD ? sD[q] : 1.0f);
 }
 
 // Forward, general points: y_{perm[q]} = D * acc[q].
@@ -280,6 +371,18 @@ __global__ void k_unpermute_output(int64_t N, const int* __restrict__ perm, cons
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
         const float d = apply_weights ? sD[q] : 1.0f;
         ValueIO<VT>::store(out, perm[q], cscale(acc[q], d));
+    }
+}
+
+// Gradient with respect to the weights, general points: grad[perm[q]] =
+// Re(conj(acc[q]) y_{perm[q]}), acc the unweighted forward sum in bucket order.
+template <typename VT>
+__global__ void k_unpermute_grad(int64_t N, const int* __restrict__ perm, const float2* __restrict__ acc,
+                                 const void* __restrict__ y_in, float* __restrict__ grad) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+        const int n = perm[q];
+        const float2 a = acc[q], y = ValueIO<VT>::load(y_in, n);
+        grad[n] = fmaf(a.x, y.x, a.y * y.y);
     }
 }
 

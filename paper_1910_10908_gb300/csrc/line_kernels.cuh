@@ -37,6 +37,11 @@ constexpr int kTapChunk = 64;                          // tap entries staged per
 __device__ __forceinline__ void cluster_arrive_relaxed() {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 }
+// Arrive with release semantics: this thread's earlier shared-memory accesses
+// are ordered before the peers' accesses that follow their wait.
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void cluster_wait() {
     asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
 }
@@ -376,16 +381,19 @@ k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int ny, in
 // row_wy holds the w azimuth taps of each pulse row (stride 8 floats).
 // ---------------------------------------------------------------------------
 
-// Column-pass shared memory: the line plus one column of F (up to N/2 pulse rows).
 // Column passes in pulse-row order: the line's shared memory, then a column
 // of F (up to N / 2 = M_y places) starting on a 128-byte boundary, so that
-// the 16 places of each 128 bytes fall in one shared-memory wavefront.
+// the 16 places of each 128 bytes fall in one shared-memory wavefront.  In the
+// adjoint the same area later receives the cluster's output rows: 4 columns
+// of N / 8 rows, each column padded by kRecvPad entries so that a column
+// starts half a bank cycle (64 bytes) after the previous one.
 template <int LOGN>
 constexpr int kPulseColOff = (Line<LOGN>::SMEM_ELEMS + 15) & ~15;
+constexpr int kRecvPad = 8;
 
 template <int LOGN>
 __host__ __device__ constexpr size_t line_smem_pulse_cols() {
-    return (size_t)(kPulseColOff<LOGN> + Line<LOGN>::N / 2) * sizeof(float2);
+    return (size_t)(kPulseColOff<LOGN> + Line<LOGN>::N / 2 + 4 * kRecvPad) * sizeof(float2);
 }
 
 // F in the adjoint's pulse-row order, by blocks of four columns: entry q
@@ -396,18 +404,21 @@ __host__ __device__ constexpr size_t line_smem_pulse_cols() {
 __host__ __device__ __forceinline__ int pulse_ldq(int P) { return (P + 3) & ~3; }
 
 // Pass-1 epilogue of the adjoint in pulse-row order: keep the M_x = N/2
-// wanted x modes, deapodise, store them as entry q of every column of F.
-template <int LOGN>
+// wanted x modes, deapodise (and, for a shifted line, undo the shift with the
+// thread's phase factor), store them as entry q of every column of F.
+template <int LOGN, bool RAMP = false>
 struct QuadOut {
     int q, ldq;
     const float* deap_x;
     float2* F;
+    float2 ramp;
     __device__ __forceinline__ void operator()(int o, float2 v) const {
         constexpr int N = 1 << LOGN, MX = N / 2, HALF = MX / 2;
         int jx;
         if (o < HALF) jx = o + HALF;
         else if (o >= N - HALF) jx = o - (N - HALF);
         else return;
+        if constexpr (RAMP) v = cmul(v, ramp);
         F[(((size_t)(jx >> 2) * ldq + q) << 2) + (jx & 3)] = cscale(v, __ldg(&deap_x[jx]));
     }
 };
@@ -424,10 +435,10 @@ k_adj_rows_pulse(RowsView rv, const float2* __restrict__ R, FftTables tab, const
     const int p = rv.rank_row[q];
     const int tid = threadIdx.x;
     const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
-    // line cell j holds R_p[(j - clo) mod NX] when that is below len, else 0;
-    // read straight into the first FFT stage's registers (cell tid + u T)
     const int len = rv.row_len[p], clo = rv.row_clo[p];
     const float2* Rp = R + rv.row_off[p];
+    // line cell j holds R_p[(j - clo) mod NX] when that is below len, else 0;
+    // read straight into the first FFT stage's registers (cell tid + u T)
     float2 v[L::V];
 #pragma unroll
     for (int u = 0; u < L::V; ++u) {
@@ -435,7 +446,7 @@ k_adj_rows_pulse(RowsView rv, const float2* __restrict__ R, FftTables tab, const
         v[u] = (o < len) ? __ldg(&Rp[o]) : make_float2(0.f, 0.f);
     }
     __syncthreads();                                   // twiddles in place
-    QuadOut<LOGN> epi{q, pulse_ldq(rv.P), deap_x, F};
+    QuadOut<LOGN> epi{q, pulse_ldq(rv.P), deap_x, F, make_float2(1.f, 0.f)};
     fft_line_epilogue_regs<LOGN, +1>(v, S.buf, tw, epi);
 }
 
@@ -449,21 +460,57 @@ __device__ __forceinline__ void load_row_taps(const float* __restrict__ row_wy, 
     wy[4] = b.x; wy[5] = b.y; wy[6] = b.z; wy[7] = b.w;
 }
 
+// Pass-2 epilogue of the adjoint in pulse-row order: keep the M_y = N/2 wanted
+// y modes, deapodise, and store each into the receive area of the cluster CTA
+// that writes its image row (row jy goes to CTA jy / (N/8), column slot =
+// this CTA's rank).
+template <int LOGN>
+struct ColPush {
+    const float* deap_y;
+    float2* dst0;
+    float2* dst1;
+    float2* dst2;
+    float2* dst3;
+    int rank;
+    __device__ __forceinline__ void operator()(int o, float2 v) const {
+        constexpr int N = 1 << LOGN, HALF = N / 4, OROWS = N / 8;
+        int jy;
+        if (o < HALF) jy = o + HALF;
+        else if (o >= N - HALF) jy = o - (N - HALF);
+        else return;
+        const int c = jy / OROWS;
+        float2* d = c == 0 ? dst0 : c == 1 ? dst1 : c == 2 ? dst2 : dst3;
+        d[rank * (OROWS + kRecvPad) + (jy % OROWS)] = cscale(v, __ldg(&deap_y[jy]));
+    }
+};
+
+// Waits at a cluster barrier whose arrive came earlier (see k_adj_cols_pulse).
+struct ClusterWait {
+    __device__ __forceinline__ void operator()() const { cluster_wait(); }
+};
+
 template <int LOGN>
 __global__ void __cluster_dims__(kColCluster, 1, 1) __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
 k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, const int2* __restrict__ ell, int K,
                  const float* __restrict__ deap_y, float2* __restrict__ img) {
     using L = Line<LOGN>;
     constexpr int NY = L::N, MY = NY / 2, V = L::V;
+    constexpr int OROWS = MY / kColCluster;            // image rows each CTA of the cluster writes
     extern __shared__ float2 smem[];
     LineSmem<LOGN> S(smem);
-    float2* fcol = smem + kPulseColOff<LOGN>;         // this CTA's column of F, P entries
+    float2* fcol = smem + kPulseColOff<LOGN>;         // this CTA's column of F, then its receive area
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int jx0 = (int)blockIdx.x - rank;
     const int tid = threadIdx.x;
-    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
     static_assert(L::T % kColCluster == 0, "line threads must be a multiple of the cluster size");
+    // Barrier phases: (A) every CTA runs before its memory is written; (B) the F
+    // columns are complete; (C) every CTA has read its F column (its area may
+    // receive output rows); (D) every output row has arrived.  C's arrive comes
+    // right after the gather and its wait just before the last FFT stage's
+    // stores, so the FFT hides it.
+    cluster_arrive_relaxed();                          // (A)
+    const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
     // The cluster's block of four columns of F is one contiguous run; CTA rank
     // reads the quarter of places [p0, p0 + PQ) and sends entry i of it
     // (place p0 + i / 4, column i % 4 = tid % 4) to the fcol of CTA i % 4.
@@ -471,8 +518,6 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
     const int ldq = pulse_ldq(P), PQ = ldq / kColCluster;
     const int p0 = rank * PQ, nel = max(0, min(P, p0 + PQ) - p0) * kColCluster;
     const float2* const Fq = F + ((size_t)(jx0 / kColCluster) * ldq + p0) * kColCluster;
-    cluster_arrive_relaxed();                          // every CTA runs before its memory is written
-    cluster_wait();
     for (int base = 0; base < nel; base += V * L::T) {
         float2 tmp[V];
 #pragma unroll
@@ -480,13 +525,16 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
             const int i = base + tid + u * L::T;
             tmp[u] = (i < nel) ? __ldg(&Fq[i]) : make_float2(0.f, 0.f);
         }
+        if (base == 0) cluster_wait();                 // (A), behind the first loads
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int i = base + tid + u * L::T;
             if (i < nel) peer_f[p0 + i / kColCluster] = tmp[u];
         }
     }
-    cluster.sync();
+    if (nel == 0) cluster_wait();                      // (A)
+    cluster_arrive_release();                          // (B)
+    cluster_wait();
     // azimuth taps, gathered: fine row r = sum over its table slots k < K of
     // weight_k fcol[q_k] (K: the most pulse rows any fine row receives; q_k
     // the tap's place in fine-y order, so that a warp's lanes read
@@ -511,26 +559,21 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
             }
         }
     }
-    ColPark<LOGN> epi{deap_y, S.buf};
-    fft_line_epilogue_regs<LOGN, +1>(v, S.buf, tw, epi);
-    cluster.sync();
-    float2* const peer = cluster.map_shared_rank(S.buf, tid % kColCluster);
-    constexpr int OROWS = MY / kColCluster;
-    {
-        float2 tmp[V / 2];
-#pragma unroll
-        for (int u = 0; u < V / 2; ++u) {
-            const int i = tid + u * L::T;
-            tmp[u] = peer[L::pad(rank * OROWS + i / kColCluster)];
-        }
-#pragma unroll
-        for (int u = 0; u < V / 2; ++u) {
-            const int i = tid + u * L::T;
-            img[(size_t)(rank * OROWS + i / kColCluster) * Mx + jx0 + i % kColCluster] = tmp[u];
-        }
-    }
-    cluster_arrive_relaxed();                          // every remote load was consumed above
+    cluster_arrive_release();                          // (C): this CTA's fcol reads are done
+    ColPush<LOGN> epi{deap_y,
+                      cluster.map_shared_rank(fcol, 0), cluster.map_shared_rank(fcol, 1),
+                      cluster.map_shared_rank(fcol, 2), cluster.map_shared_rank(fcol, 3), rank};
+    fft_line_epilogue_regs<LOGN, +1>(v, S.buf, tw, epi, ClusterWait{});   // (C) waited before the stores
+    cluster_arrive_release();                          // (D)
     cluster_wait();
+    // this CTA's image rows [rank OROWS, (rank + 1) OROWS) of the 4 columns, from
+    // its receive area (column c at c (OROWS + kRecvPad)), as 32-byte row chunks
+#pragma unroll
+    for (int u = 0; u < V / 2; ++u) {
+        const int i = tid + u * L::T;
+        const int r = i / kColCluster, c = i % kColCluster;
+        img[(size_t)(rank * OROWS + r) * Mx + jx0 + c] = fcol[c * (OROWS + kRecvPad) + r];
+    }
 }
 
 template <int LOGN>

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/tffr.h"
+#include "batch_launch.h"
 #include "common.cuh"
 #include "line_launch.h"
 #include "kernels_points.cuh"
@@ -70,6 +71,9 @@ struct tffr_plan_s {
     bool have_points = false, have_weights = false;
     bool normal_ready = false;             // Khat of the Toeplitz normal operator built for these points/weights
     DevBuf<float2> khat, nwork1, nwork2;   // Khat column-major [2Mx][2My]; two [My][2Mx] work arrays
+    DevBuf<float2> cg_r, cg_p, cg_Ap;      // conjugate gradients: residual, direction, N direction ([My][Mx])
+    DevBuf<float2> cg_y;                   // [N] samples E p (CG without the Toeplitz operator)
+    DevBuf<double> cg_s;                   // [2 iters + 1] |r_k|^2 (k = 0..iters), then Re <p_k, N p_k>
     int layout = 0;
     int64_t n_kept = -1;
     DevBuf<float> D;                       // per-sample weights when materialised
@@ -291,10 +295,11 @@ double power_fit_error(const std::vector<double>& a, F f) {
 void fit_taps(tffr_plan_s* p) {
     std::memset(&p->taps, 0, sizeof(p->taps));
     const int w = p->w, h = w / 2;
+    const int nc = tap_coefs(w);
     for (int s = 0; s < h; ++s) {
         auto f = [&](double t) { return es_phi((double)(s - (h - 1)) - 0.5 * (t + 1.0), w, p->beta); };
-        const std::vector<double> a = cheb_fit_power(f, kTapCoefs);
-        for (int k = 0; k < kTapCoefs; ++k) {
+        const std::vector<double> a = cheb_fit_power(f, nc);
+        for (int k = 0; k < nc; ++k) {
             p->taps.c[s][k] = (float)a[k];
             p->taps.c[w - 1 - s][k] = (float)((k & 1) ? -a[k] : a[k]);
         }
@@ -316,6 +321,13 @@ void fit_weights(WeightArgs& A) {
         std::vector<double> a = cheb_fit_power(f0, kG0Coefs);
         A.n0 = kG0Coefs;
         for (int k = 0; k < kG0Coefs; ++k) A.c0[k] = (float)a[k];
+        // and 1/G itself on the same piece (G >= 0.93 there for the paper's a, q)
+        auto r0 = [&](double s) {
+            const double g = f0(s);
+            return g != 0.0 ? 1.0 / g : 0.0;
+        };
+        std::vector<double> b = cheb_fit_power(r0, kD0Coefs);
+        for (int k = 0; k < kD0Coefs; ++k) A.d0[k] = (float)b[k];
     }
     if (vb < 0.5) {
         auto f1 = [&](double s) { return G(vb + (0.5 - vb) * 0.5 * (s + 1.0)); };
@@ -336,6 +348,7 @@ void copy_fit(WeightArgs& dst, const WeightArgs& src) {
     dst.n1 = src.n1;
     std::memcpy(dst.c0, src.c0, sizeof(dst.c0));
     std::memcpy(dst.c1, src.c1, sizeof(dst.c1));
+    std::memcpy(dst.d0, src.d0, sizeof(dst.d0));
 }
 
 int upload_tables(tffr_plan_s* p) {
@@ -384,7 +397,9 @@ int upload_tables(tffr_plan_s* p) {
     return TFFR_OK;
 }
 
-constexpr int kSpreadSmemMax = kSpreadStageBytes + kFftNMax * (int)sizeof(float2);
+// staged tile (lam_x and the widest value type) and the longest (periodic) row
+constexpr int kSpreadSmemMax = kSpreadStageElems * (int)(sizeof(double) + sizeof(double2)) +
+                               kFftNMax * (int)sizeof(float2);
 
 template <typename K>
 cudaError_t smem_attr(K kernel, size_t bytes) {
@@ -406,6 +421,7 @@ int set_kernel_attributes(tffr_plan_s* p) {
     static bool done[64] = {false};
     if (dev < 64 && done[dev]) return TFFR_OK;
     CK(line_set_attributes());
+    CK(batch_set_attributes());
     CK(spread_attrs<float2>());
     CK(spread_attrs<double2>());
     CK(spread_attrs<__half2>());
@@ -606,28 +622,38 @@ int build_general(tffr_plan_s* p) {
 FftTables tables_x(const tffr_plan_s* p) { return FftTables{p->twh_x.ptr, p->twl_x.ptr, p->tt_x.ptr}; }
 FftTables tables_y(const tffr_plan_s* p) { return FftTables{p->twh_y.ptr, p->twl_y.ptr, p->tt_y.ptr}; }
 
+// The plan's weights, or unit weights (the unweighted adjoint E^H y).
+WeightArgs spread_weights(const tffr_plan_s* p, bool weighted) {
+    if (weighted) return p->wargs;
+    WeightArgs u;
+    std::memset(&u, 0, sizeof(u));
+    u.mode = TFFR_WEIGHTS_UNIT;
+    return u;
+}
+
 template <typename VT, int W>
-void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values) {
-    const size_t smem = (size_t)kSpreadStageBytes + (size_t)p->max_len * sizeof(float2);
+void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values, bool weighted) {
+    const size_t smem = (size_t)kSpreadStageElems * (sizeof(double) + sizeof(VT)) + (size_t)p->max_len * sizeof(float2);
     const DeferList defer{p->d_small.ptr + 5, p->defer.ptr, (int)p->N};
+    const WeightArgs wa = spread_weights(p, weighted);
     k_spread_rows<VT, W><<<p->P, kSpreadThreads, smem, p->stream>>>(rv, p->N, p->nx, p->Mx, p->My, p->lam_x, values,
-                                                                     p->wargs, p->taps, defer, p->R.ptr);
-    if (p->wargs.mode == TFFR_WEIGHTS_TFFR)
-        k_spread_deferred<VT, W><<<152 * 2, 256, 0, p->stream>>>(rv, p->nx, p->Mx, p->My, p->lam_x, values, p->wargs,
+                                                                     wa, p->taps, defer, p->R.ptr);
+    if (wa.mode == TFFR_WEIGHTS_TFFR)
+        k_spread_deferred<VT, W><<<152 * 2, 256, 0, p->stream>>>(rv, p->nx, p->Mx, p->My, p->lam_x, values, wa,
                                                                   p->taps, defer, p->R.ptr);
 }
 
 template <typename VT>
-int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
+int adjoint_impl(tffr_plan_s* p, const void* values, float2* image, bool weighted = true) {
     const int ny = p->ny;
     if (p->layout == TFFR_POINTS_ROWS) {
         const RowsView rv = rows_view(p);
         STAGE_BEGIN(TFFR_STAGE_SPREAD);
         switch (p->w) {
-            case 2: launch_spread<VT, 2>(p, rv, values); break;
-            case 4: launch_spread<VT, 4>(p, rv, values); break;
-            case 6: launch_spread<VT, 6>(p, rv, values); break;
-            default: launch_spread<VT, 8>(p, rv, values); break;
+            case 2: launch_spread<VT, 2>(p, rv, values, weighted); break;
+            case 4: launch_spread<VT, 4>(p, rv, values, weighted); break;
+            case 6: launch_spread<VT, 6>(p, rv, values, weighted); break;
+            default: launch_spread<VT, 8>(p, rv, values, weighted); break;
         }
         CK_LAUNCH("k_spread_rows");
         STAGE_END(TFFR_STAGE_SPREAD);
@@ -648,8 +674,8 @@ int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
         STAGE_END(TFFR_STAGE_ROW_FFT);
     } else {
         STAGE_BEGIN(TFFR_STAGE_ROW_FFT);
-        k_gather_values<VT><<<grid_for(p->N, 256), 256, 0, p->stream>>>(p->N, p->perm.ptr, values, p->sD.ptr,
-                                                                         p->acc.ptr);
+        k_gather_values<VT><<<grid_for(p->N, 256), 256, 0, p->stream>>>(p->N, p->perm.ptr, values,
+                                                                         weighted ? p->sD.ptr : nullptr, p->acc.ptr);
         CK_LAUNCH("k_gather_values");
         const GeneralView gv = general_view(p);
         launch_adj_rows_general(p->lognx, ny, p->stream, gv, p->acc.ptr, p->w, p->taps, tables_x(p), p->deap_x.ptr,
@@ -665,13 +691,21 @@ int adjoint_impl(tffr_plan_s* p, const void* values, float2* image) {
 }
 
 template <typename VT, int W>
-void launch_interp(tffr_plan_s* p, const RowsView& rv, void* values, int apply_weights) {
-    k_interp_rows<VT, W><<<p->P, kSpreadThreads, 0, p->stream>>>(rv, p->N, p->nx, p->Mx, p->My, p->lam_x, p->R.ptr,
-                                                                  p->wargs, p->taps, apply_weights, values);
+void launch_interp(tffr_plan_s* p, const RowsView& rv, void* values, int apply_weights, const void* y_in) {
+    if (y_in)
+        k_interp_rows<VT, W, true><<<p->P, kSpreadThreads, 0, p->stream>>>(
+            rv, p->N, p->nx, p->Mx, p->My, p->lam_x, p->R.ptr, p->wargs, p->taps, 0, values, y_in);
+    else
+        k_interp_rows<VT, W><<<p->P, kSpreadThreads, 0, p->stream>>>(rv, p->N, p->nx, p->Mx, p->My, p->lam_x,
+                                                                      p->R.ptr, p->wargs, p->taps, apply_weights,
+                                                                      values);
 }
 
+// values = (D) E image; with y_in, values (float[N]) = Re(conj(E image) y) instead:
+// the gradient of a real loss with respect to real weights, for grad_image = its
+// gradient with respect to the image (y_in in the value type VT).
 template <typename VT>
-int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_weights) {
+int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_weights, const void* y_in = nullptr) {
     const int ny = p->ny;
     const bool pulse = p->layout == TFFR_POINTS_ROWS && p->pulse_order;
     const RowsView rv = rows_view(p);
@@ -700,10 +734,10 @@ int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_we
         STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
         STAGE_BEGIN(TFFR_STAGE_INTERP);
         switch (p->w) {
-            case 2: launch_interp<VT, 2>(p, rv, values, apply_weights); break;
-            case 4: launch_interp<VT, 4>(p, rv, values, apply_weights); break;
-            case 6: launch_interp<VT, 6>(p, rv, values, apply_weights); break;
-            default: launch_interp<VT, 8>(p, rv, values, apply_weights); break;
+            case 2: launch_interp<VT, 2>(p, rv, values, apply_weights, y_in); break;
+            case 4: launch_interp<VT, 4>(p, rv, values, apply_weights, y_in); break;
+            case 6: launch_interp<VT, 6>(p, rv, values, apply_weights, y_in); break;
+            default: launch_interp<VT, 8>(p, rv, values, apply_weights, y_in); break;
         }
         CK_LAUNCH("k_interp_rows");
         STAGE_END(TFFR_STAGE_INTERP);
@@ -714,9 +748,15 @@ int forward_impl(tffr_plan_s* p, const float2* image, void* values, int apply_we
         CK_LAUNCH("k_fwd_rows");
         STAGE_END(TFFR_STAGE_FWD_ROW_FFT);
         STAGE_BEGIN(TFFR_STAGE_INTERP);
-        k_unpermute_output<VT><<<grid_for(p->N, 256), 256, 0, p->stream>>>(p->N, p->perm.ptr, p->acc.ptr, p->sD.ptr,
-                                                                            apply_weights, values);
-        CK_LAUNCH("k_unpermute_output");
+        if (y_in) {
+            k_unpermute_grad<VT><<<grid_for(p->N, 256), 256, 0, p->stream>>>(p->N, p->perm.ptr, p->acc.ptr, y_in,
+                                                                              reinterpret_cast<float*>(values));
+            CK_LAUNCH("k_unpermute_grad");
+        } else {
+            k_unpermute_output<VT><<<grid_for(p->N, 256), 256, 0, p->stream>>>(p->N, p->perm.ptr, p->acc.ptr,
+                                                                                p->sD.ptr, apply_weights, values);
+            CK_LAUNCH("k_unpermute_output");
+        }
         STAGE_END(TFFR_STAGE_INTERP);
     }
     return TFFR_OK;
@@ -909,6 +949,7 @@ int tffr_destroy(tffr_plan_t p) {
     release(p->d_small); release(p->d_kept); release(p->D);
     release(p->tile_info); release(p->tile_head); release(p->defer);
     release(p->khat); release(p->nwork1); release(p->nwork2);
+    release(p->cg_r); release(p->cg_p); release(p->cg_Ap); release(p->cg_y); release(p->cg_s);
     if (p->h_small) cudaFreeHost(p->h_small);
     if (p->readback) cudaEventDestroy(p->readback);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly);
@@ -1185,6 +1226,101 @@ int normal_kernel_image(tffr_plan_s* p, float2* g) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Conjugate gradients on the weighted normal equations E^H D E f = E^H D y
+// (the least-squares refinement of the one-step tFFR image).  Every vector
+// operation and every reduction runs on the device; the step sizes are read
+// from device scalars, so an iteration needs no host synchronisation.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kCgThreads = 256;
+
+// Block sum of one double per thread, added to *out by one atomic per block.
+__device__ __forceinline__ void block_add(double v, double* out) {
+    __shared__ double s_part[kCgThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kCgThreads / 32; ++i) t += s_part[i];
+        atomicAdd(out, t);
+    }
+}
+
+// x = 0, p = r (r holds b = E^H D y), rr0 += |r|^2.
+__global__ void __launch_bounds__(kCgThreads)
+k_cg_start(int64_t n, const float2* __restrict__ r, float2* __restrict__ pv, float2* __restrict__ x,
+           double* __restrict__ rr0) {
+    float acc = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = r[i];
+        pv[i] = v;
+        x[i] = make_float2(0.f, 0.f);
+        acc = fmaf(v.x, v.x, fmaf(v.y, v.y, acc));
+    }
+    block_add((double)acc, rr0);
+}
+
+// *out += Re sum conj(p) Ap.
+__global__ void __launch_bounds__(kCgThreads)
+k_cg_dot(int64_t n, const float2* __restrict__ pv, const float2* __restrict__ Ap, double* __restrict__ out) {
+    float acc = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 a = pv[i], b = Ap[i];
+        acc = fmaf(a.x, b.x, fmaf(a.y, b.y, acc));
+    }
+    block_add((double)acc, out);
+}
+
+// alpha = rr_k / pAp_k (0 when pAp_k <= 0); x += alpha p, r -= alpha Ap, rr_next += |r|^2.
+__global__ void __launch_bounds__(kCgThreads)
+k_cg_step(int64_t n, const double* __restrict__ rr_k, const double* __restrict__ pap_k, float2* __restrict__ x,
+          float2* __restrict__ r, const float2* __restrict__ pv, const float2* __restrict__ Ap,
+          double* __restrict__ rr_next) {
+    const double pap = *pap_k;
+    const float alpha = pap > 0.0 ? (float)(*rr_k / pap) : 0.0f;
+    float acc = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 pi = pv[i], api = Ap[i];
+        float2 xi = x[i], ri = r[i];
+        xi.x = fmaf(alpha, pi.x, xi.x);
+        xi.y = fmaf(alpha, pi.y, xi.y);
+        ri.x = fmaf(-alpha, api.x, ri.x);
+        ri.y = fmaf(-alpha, api.y, ri.y);
+        x[i] = xi;
+        r[i] = ri;
+        acc = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, acc));
+    }
+    block_add((double)acc, rr_next);
+}
+
+// beta = rr_next / rr_k (0 when rr_k <= 0); p = r + beta p.
+__global__ void __launch_bounds__(kCgThreads)
+k_cg_dir(int64_t n, const double* __restrict__ rr_k, const double* __restrict__ rr_next,
+         const float2* __restrict__ r, float2* __restrict__ pv) {
+    const double rk = *rr_k;
+    const float beta = rk > 0.0 ? (float)(*rr_next / rk) : 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 ri = r[i], pi = pv[i];
+        pv[i] = make_float2(fmaf(beta, pi.x, ri.x), fmaf(beta, pi.y, ri.y));
+    }
+}
+
+// The adjoint in the plan's value type (values: caller's samples).
+int adjoint_dispatch(tffr_plan_s* p, const void* values, float2* img, bool weighted) {
+    switch (p->values) {
+        case TFFR_VALUES_C64: return adjoint_impl<float2>(p, values, img, weighted);
+        case TFFR_VALUES_C128: return adjoint_impl<double2>(p, values, img, weighted);
+        case TFFR_VALUES_F16: return adjoint_impl<__half2>(p, values, img, weighted);
+        default: return adjoint_impl<__nv_bfloat162>(p, values, img, weighted);
+    }
+}
+
+}  // namespace
+
 int tffr_normal_setup(tffr_plan_t p) {
     if (!p) return TFFR_ERR_INVALID_ARG;
     p->last_error.clear();
@@ -1238,6 +1374,395 @@ int tffr_normal_apply(tffr_plan_t p, const void* image_in, void* image_out) {
     return TFFR_OK;
 }
 
+int tffr_adjoint_unweighted(tffr_plan_t p, const void* values, void* image) {
+    if (!p) return TFFR_ERR_INVALID_ARG;
+    p->last_error.clear();
+    if (!p->have_points || !p->have_weights) return fail(p, TFFR_ERR_NOT_READY, "adjoint before points/weights");
+    if (!image || (p->N > 0 && !values)) return fail(p, TFFR_ERR_INVALID_ARG, "NULL pointer");
+    float2* img = reinterpret_cast<float2*>(image);
+    if (p->N == 0) {
+        CK(cudaMemsetAsync(img, 0, (size_t)p->Mx * p->My * sizeof(float2), p->stream));
+        return TFFR_OK;
+    }
+    return adjoint_dispatch(p, values, img, false);
+}
+
+int tffr_weight_grad(tffr_plan_t p, const void* grad_image, const void* values, float* grad_D) {
+    if (!p) return TFFR_ERR_INVALID_ARG;
+    p->last_error.clear();
+    if (!p->have_points || !p->have_weights) return fail(p, TFFR_ERR_NOT_READY, "weight_grad before points/weights");
+    if (!grad_image || (p->N > 0 && (!values || !grad_D))) return fail(p, TFFR_ERR_INVALID_ARG, "NULL pointer");
+    if (p->N == 0) return TFFR_OK;
+    const float2* g = reinterpret_cast<const float2*>(grad_image);
+    switch (p->values) {
+        case TFFR_VALUES_C64: return forward_impl<float2>(p, g, grad_D, 0, values);
+        case TFFR_VALUES_C128: return forward_impl<double2>(p, g, grad_D, 0, values);
+        case TFFR_VALUES_F16: return forward_impl<__half2>(p, g, grad_D, 0, values);
+        default: return forward_impl<__nv_bfloat162>(p, g, grad_D, 0, values);
+    }
+}
+
+int tffr_cg(tffr_plan_t p, const void* values, void* image, int iters, int use_toeplitz, double* residuals) {
+    if (!p) return TFFR_ERR_INVALID_ARG;
+    p->last_error.clear();
+    if (!p->have_points || !p->have_weights) return fail(p, TFFR_ERR_NOT_READY, "tffr_cg before points/weights");
+    if (use_toeplitz && !p->normal_ready) return fail(p, TFFR_ERR_NOT_READY, "tffr_cg: tffr_normal_setup first");
+    if (iters < 0 || iters > 100000) return fail(p, TFFR_ERR_INVALID_ARG, "iters out of range");
+    if (!image || (p->N > 0 && !values)) return fail(p, TFFR_ERR_INVALID_ARG, "NULL pointer");
+    const int64_t n = (int64_t)p->Mx * p->My;
+    float2* x = reinterpret_cast<float2*>(image);
+    CK(grow(p, p->cg_r, n));
+    CK(grow(p, p->cg_p, n));
+    CK(grow(p, p->cg_Ap, n));
+    CK(grow(p, p->cg_s, 2 * (int64_t)iters + 1));
+    if (!use_toeplitz && p->N > 0) CK(grow(p, p->cg_y, p->N));
+    double* rr = p->cg_s.ptr;                          // |r_k|^2, k = 0..iters
+    double* pap = p->cg_s.ptr + iters + 1;             // Re <p_k, N p_k>, k < iters
+    CK(cudaMemsetAsync(rr, 0, (size_t)(2 * iters + 1) * sizeof(double), p->stream));
+    if (p->N == 0) {
+        CK(cudaMemsetAsync(p->cg_r.ptr, 0, (size_t)n * sizeof(float2), p->stream));
+    } else {
+        const int s = adjoint_dispatch(p, values, p->cg_r.ptr, true);       // b = E^H D y
+        if (s != TFFR_OK) return s;
+    }
+    const int blocks = grid_for(n, kCgThreads);
+    k_cg_start<<<blocks, kCgThreads, 0, p->stream>>>(n, p->cg_r.ptr, p->cg_p.ptr, x, rr);
+    CK_LAUNCH("k_cg_start");
+    for (int k = 0; k < iters; ++k) {
+        if (use_toeplitz) {
+            const int s = tffr_normal_apply(p, p->cg_p.ptr, p->cg_Ap.ptr);
+            if (s != TFFR_OK) return s;
+        } else if (p->N > 0) {
+            int s = forward_impl<float2>(p, p->cg_p.ptr, p->cg_y.ptr, 0);     // E p
+            if (s == TFFR_OK) s = adjoint_impl<float2>(p, p->cg_y.ptr, p->cg_Ap.ptr, true);   // E^H D E p
+            if (s != TFFR_OK) return s;
+        } else {
+            CK(cudaMemsetAsync(p->cg_Ap.ptr, 0, (size_t)n * sizeof(float2), p->stream));
+        }
+        k_cg_dot<<<blocks, kCgThreads, 0, p->stream>>>(n, p->cg_p.ptr, p->cg_Ap.ptr, pap + k);
+        CK_LAUNCH("k_cg_dot");
+        k_cg_step<<<blocks, kCgThreads, 0, p->stream>>>(n, rr + k, pap + k, x, p->cg_r.ptr, p->cg_p.ptr,
+                                                         p->cg_Ap.ptr, rr + k + 1);
+        CK_LAUNCH("k_cg_step");
+        k_cg_dir<<<blocks, kCgThreads, 0, p->stream>>>(n, rr + k, rr + k + 1, p->cg_r.ptr, p->cg_p.ptr);
+        CK_LAUNCH("k_cg_dir");
+    }
+    if (residuals) {
+        std::vector<double> h(iters + 1);
+        CK(cudaMemcpyAsync(h.data(), rr, (size_t)(iters + 1) * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        CK(cudaStreamSynchronize(p->stream));
+        for (int k = 0; k <= iters; ++k) residuals[k] = std::sqrt(std::max(0.0, h[k]));
+    }
+    return TFFR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of pulse-row patches: one persistent launch per image-size class
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+struct BatchClass {
+    int logn = 0, w = 0;
+    std::vector<int> members;                          // indices into the batch's plans
+    BatchPatch* d_patches = nullptr;
+    int* d_first = nullptr;                            // row_first[n + 1], fine_first[n + 1], col_first[n + 1]
+    int* d_counts = nullptr;                           // next item, done[n], fine_done[n]
+    int rows_total = 0, fine_total = 0, cols_total = 0;
+    int grid = 0, run = 8, max_blocks = 1;
+    float tuned_ms = 0.0f;                             // the tuner's best time per launch
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    WeightArgs wa;
+    TapPoly tp;
+    FftTables tab;
+};
+
+}  // namespace
+
+struct tffr_batch_s {
+    cudaStream_t stream = nullptr;
+    std::vector<BatchClass> cls;
+    int* d_err = nullptr;                              // [0] error bits, [1] abort flag
+    cudaEvent_t fork = nullptr;
+    int n = 0;
+    int64_t samples = 0;
+    unsigned long long wait_ns = 1000000000ull;
+    int hold = 0, tuned = 0, sms = 0;
+};
+
+namespace {
+
+void batch_free(tffr_batch_s* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    for (BatchClass& c : b->cls) {
+        if (c.st) cudaStreamSynchronize(c.st);
+        if (c.d_patches) cudaFree(c.d_patches);
+        if (c.d_first) cudaFree(c.d_first);
+        if (c.d_counts) cudaFree(c.d_counts);
+        if (c.ev) cudaEventDestroy(c.ev);
+        if (c.st) cudaStreamDestroy(c.st);
+    }
+    if (b->d_err) cudaFree(b->d_err);
+    if (b->fork) cudaEventDestroy(b->fork);
+    delete b;
+}
+
+BatchClassArgs class_args(const tffr_batch_s* b, const BatchClass& c) {
+    BatchClassArgs a;
+    const int n = (int)c.members.size();
+    a.patches = c.d_patches;
+    a.row_first = c.d_first;
+    a.fine_first = c.d_first + (n + 1);
+    a.col_first = c.d_first + 2 * (n + 1);
+    a.npatch = n;
+    a.rows_total = c.rows_total;
+    a.fine_total = c.fine_total;
+    a.total = c.rows_total + c.fine_total + c.cols_total;
+    a.next = c.d_counts;
+    a.done = c.d_counts + 1;
+    a.fine_done = c.d_counts + 1 + n;
+    a.err = b->d_err;
+    a.wait_ns = b->wait_ns;
+    a.run = c.run;
+    a.hold = b->hold;
+    a.wa = c.wa;
+    a.tp = c.tp;
+    a.tab = c.tab;
+    return a;
+}
+
+cudaError_t launch_class(const tffr_batch_s* b, const BatchClass& c) {
+    cudaError_t e = cudaMemsetAsync(c.d_counts, 0, (2 * c.members.size() + 1) * sizeof(int), c.st);
+    if (e != cudaSuccess) return e;
+    launch_batch_class(c.logn, c.w, c.grid, c.st, class_args(b, c));
+    return cudaGetLastError();
+}
+
+bool same_weights(const WeightArgs& x, const WeightArgs& y) {
+    return x.mode == y.mode && x.separable == y.separable && x.tau_d == y.tau_d && x.a == y.a && x.q == y.q;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tffr_batch_create(const tffr_plan_t* plans, int n, const void* const* values, void* const* images,
+                      tffr_stream_t stream, tffr_batch_t* out) {
+    if (!out) return TFFR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!plans || !values || !images || n < 1) return TFFR_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        const tffr_plan_s* p = plans[i];
+        if (!p || !values[i] || !images[i]) return TFFR_ERR_INVALID_ARG;
+        if (!p->have_points || !p->have_weights) return TFFR_ERR_NOT_READY;
+        if (p->layout != TFFR_POINTS_ROWS || p->values != TFFR_VALUES_C64 || p->Mx != p->My || p->P < 1 ||
+            !batch_class_supported(p->lognx, p->w))
+            return TFFR_ERR_INVALID_ARG;
+    }
+    tffr_batch_s* b = new (std::nothrow) tffr_batch_s();
+    if (!b) return TFFR_ERR_OOM;
+    b->stream = (cudaStream_t)stream;
+    b->n = n;
+    auto bail = [&](cudaError_t e) {
+        batch_free(b);
+        return e == cudaErrorMemoryAllocation ? TFFR_ERR_OOM : TFFR_ERR_CUDA;
+    };
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return bail(e);
+    // classes: patches of one line length and spreading width share a launch
+    for (int i = 0; i < n; ++i) {
+        const tffr_plan_s* p = plans[i];
+        b->samples += p->N;
+        BatchClass* c = nullptr;
+        for (BatchClass& x : b->cls)
+            if (x.logn == p->lognx && x.w == p->w) c = &x;
+        if (!c) {
+            b->cls.emplace_back();
+            c = &b->cls.back();
+            c->logn = p->lognx;
+            c->w = p->w;
+            c->wa = p->wargs;
+            c->tp = p->taps;
+            c->tab = tables_x(p);
+        } else if (!same_weights(c->wa, p->wargs) || plans[c->members[0]]->beta != p->beta) {
+            batch_free(b);
+            return TFFR_ERR_INVALID_ARG;                 // one weight rule and kernel per class
+        }
+        c->members.push_back(i);
+    }
+    for (BatchClass& c : b->cls) {
+        const int m = (int)c.members.size();
+        std::vector<BatchPatch> hp(m);
+        std::vector<int> first(3 * (m + 1), 0);
+        for (int j = 0; j < m; ++j) {
+            const tffr_plan_s* p = plans[c.members[j]];
+            BatchPatch& d = hp[j];
+            d.pulse = p->pulse_order ? 1 : 0;
+            d.M = p->Mx;
+            d.n = p->nx;
+            d.P = p->P;
+            d.ldq = (p->P + 3) & ~3;
+            d.K = p->ell_k;
+            d.row_start = p->row_start.ptr;
+            d.row_end = p->row_end.ptr;
+            d.row_clo = p->row_clo.ptr;
+            d.row_len = p->row_len.ptr;
+            d.row_ly = p->row_ly.ptr;
+            d.row_fy = p->row_fy.ptr;
+            d.row_lam_y = p->row_lam_y.ptr;
+            d.rank_row = p->rank_row.ptr;
+            d.ell = p->ell.ptr;
+            d.deap_x = p->deap_x.ptr;
+            d.deap_y = p->deap_y.ptr;
+            d.F = p->T.ptr;
+            d.tap_start = p->tap_start.ptr;
+            d.taps = p->tap_list.ptr;
+            d.row_off = p->row_off.ptr;
+            d.R = p->R.ptr;
+            d.lam_x = p->lam_x;
+            d.user_D = p->wargs.mode == TFFR_WEIGHTS_USER ? p->D.ptr : nullptr;
+            d.values = reinterpret_cast<const float2*>(values[c.members[j]]);
+            d.image = reinterpret_cast<float2*>(images[c.members[j]]);
+            first[j + 1] = first[j] + p->P;                                        // row items
+            first[m + 1 + j + 1] = first[m + 1 + j] + (d.pulse ? 0 : p->nx);       // fine-row items
+            first[2 * (m + 1) + j + 1] = first[2 * (m + 1) + j] + p->Mx;           // column items
+        }
+        c.rows_total = first[m];
+        c.fine_total = first[2 * m + 1];
+        c.cols_total = first[3 * m + 2];
+        c.max_blocks = std::max(1, batch_max_blocks_per_sm(c.logn, c.w));
+        c.grid = b->sms * c.max_blocks;
+        e = cudaMalloc((void**)&c.d_patches, m * sizeof(BatchPatch));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c.d_first, first.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&c.d_counts, (2 * m + 1) * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(c.d_patches, hp.data(), m * sizeof(BatchPatch), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c.d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return bail(e);
+    }
+    e = cudaMalloc((void**)&b->d_err, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(e);
+    *out = b;
+    return TFFR_OK;
+}
+
+int tffr_batch_adjoint(tffr_batch_t b) {
+    if (!b) return TFFR_ERR_INVALID_ARG;
+    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return TFFR_ERR_CUDA;
+    for (const BatchClass& c : b->cls) {
+        if (cudaStreamWaitEvent(c.st, b->fork, 0) != cudaSuccess) return TFFR_ERR_CUDA;
+        if (launch_class(b, c) != cudaSuccess) return TFFR_ERR_CUDA;
+        if (cudaEventRecord(c.ev, c.st) != cudaSuccess) return TFFR_ERR_CUDA;
+        if (cudaStreamWaitEvent(b->stream, c.ev, 0) != cudaSuccess) return TFFR_ERR_CUDA;
+    }
+    return TFFR_OK;
+}
+
+int tffr_batch_wait(tffr_batch_t b) {
+    if (!b) return TFFR_ERR_INVALID_ARG;
+    int err[2] = {0, 0};
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TFFR_ERR_CUDA;
+    if (cudaMemcpy(err, b->d_err, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess) return TFFR_ERR_CUDA;
+    if (err[0] || err[1]) {
+        if (cudaMemset(b->d_err, 0, sizeof(err)) != cudaSuccess) return TFFR_ERR_CUDA;
+        return TFFR_ERR_TIMEOUT;
+    }
+    return TFFR_OK;
+}
+
+int tffr_batch_set_wait(tffr_batch_t b, double wait_s, int hold_rows) {
+    if (!b || !(wait_s > 0.0) || wait_s > 60.0) return TFFR_ERR_INVALID_ARG;
+    b->wait_ns = (unsigned long long)(wait_s * 1e9);
+    b->hold = hold_rows ? 1 : 0;
+    return TFFR_OK;
+}
+
+int tffr_batch_tune(tffr_batch_t b, int reps) {
+    if (!b || reps < 1 || reps > 1000) return TFFR_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TFFR_ERR_CUDA;
+    cudaEvent_t t0, t1;
+    if (cudaEventCreate(&t0) != cudaSuccess) return TFFR_ERR_CUDA;
+    if (cudaEventCreate(&t1) != cudaSuccess) {
+        cudaEventDestroy(t0);
+        return TFFR_ERR_CUDA;
+    }
+    int status = TFFR_OK;
+    const int runs[3] = {4, 8, 16};
+    for (BatchClass& c : b->cls) {
+        float best = 1e30f;
+        int best_grid = c.grid, best_run = c.run;
+        std::vector<int> blocks;                                      // 1, 2, 4, ... and the most that fit
+        for (int x = 1; x < c.max_blocks; x *= 2) blocks.push_back(x);
+        blocks.push_back(c.max_blocks);
+        for (int run : runs) {
+            for (int bps : blocks) {
+                c.run = run;
+                c.grid = b->sms * bps;
+                cudaError_t e = launch_class(b, c);                 // warm
+                if (e == cudaSuccess) e = cudaEventRecord(t0, c.st);
+                for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_class(b, c);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, c.st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+                if (e != cudaSuccess) {
+                    status = TFFR_ERR_CUDA;
+                    break;
+                }
+                if (ms < best) {
+                    best = ms;
+                    best_grid = c.grid;
+                    best_run = run;
+                }
+            }
+            if (status != TFFR_OK) break;
+        }
+        c.grid = best_grid;
+        c.run = best_run;
+        c.tuned_ms = best / (float)reps;
+        if (status != TFFR_OK) break;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (status == TFFR_OK) {
+        b->tuned = 1;
+        status = tffr_batch_wait(b);                                  // a timed-out tuning launch shows here
+    }
+    return status;
+}
+
+int tffr_batch_get_info(tffr_batch_t b, tffr_batch_info* info) {
+    if (!b || !info) return TFFR_ERR_INVALID_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n_patches = b->n;
+    info->n_classes = (int)b->cls.size();
+    info->samples = b->samples;
+    info->tuned = b->tuned;
+    for (int i = 0; i < (int)b->cls.size() && i < TFFR_BATCH_MAX_CLASSES; ++i) {
+        const BatchClass& c = b->cls[i];
+        info->class_side[i] = (1 << c.logn) / 2;
+        info->class_width[i] = c.w;
+        info->class_patches[i] = (int)c.members.size();
+        info->class_blocks[i] = c.grid;
+        info->class_run[i] = c.run;
+        info->class_ms[i] = c.tuned_ms;
+    }
+    return TFFR_OK;
+}
+
+int tffr_batch_destroy(tffr_batch_t b) {
+    batch_free(b);
+    return TFFR_OK;
+}
+
 int tffr_weights_noalloc(int64_t N, const double* lam_x, const double* lam_y, int Mx, int My,
                          const tffr_weight_opts* opts, float* D_out, int64_t* n_kept, tffr_stream_t stream) {
     if (N < 0 || N > kNaMaxN || Mx < 1 || My < 1) return TFFR_ERR_INVALID_ARG;
@@ -1254,6 +1779,12 @@ int tffr_weights_noalloc(int64_t N, const double* lam_x, const double* lam_y, in
     if (N == 0) {
         if (n_kept) *n_kept = 0;
         return TFFR_OK;
+    }
+    if (o.mode == TFFR_WEIGHTS_USER) {
+        // the kernel reads user_D while it writes D_out: the two ranges must not overlap
+        const uintptr_t d0 = reinterpret_cast<uintptr_t>(D_out), u0 = reinterpret_cast<uintptr_t>(o.user_D);
+        const uintptr_t bytes = (uintptr_t)N * sizeof(float);
+        if (d0 < u0 + bytes && u0 < d0 + bytes) return TFFR_ERR_INVALID_ARG;
     }
     WeightArgs A;
     std::memset(&A, 0, sizeof(A));

@@ -1,20 +1,22 @@
 """Differentiable tFFR and a least-squares image solver, on the library's kernels.
 
 With E the non-uniform Fourier matrix (E[n, j] = exp(-2 pi i lam_n . x_j)) and
-D = diag(D_n) the frame weights, the library's two calls are
+D = diag(D_n) the frame weights, the library's calls are
 
-    adjoint:  f = E^H D y        (the tFFR image, Eq. (fstraight) with alpha_n = D_n)
-    forward:  y = D E f          (apply_weights=True)   or   E f   (apply_weights=False)
+    adjoint:             f = E^H D y     (the tFFR image, Eq. (fstraight) with alpha_n = D_n)
+    adjoint_unweighted:  f = E^H y
+    forward:             y = D E f       (apply_weights=True)   or   E f   (apply_weights=False)
 
-so each is the other's Hermitian transpose and serves as its backward pass.
-PyTorch's convention for a real loss L of complex tensors is that a tensor's
-gradient is dL/d(conj z) (up to the factor 2 shared by every tensor), hence for
-f = E^H D y:
+so each serves as another's backward pass.  PyTorch's convention for a real
+loss L of complex tensors is that a tensor's gradient is dL/d(conj z) (up to
+the factor 2 shared by every tensor), hence for f = E^H D y:
 
     grad_y = D E grad_f                       (the forward twin with weights)
-    grad_D = Re(conj(E grad_f) * y)           (real weights, USER mode)
+    grad_D = Re(conj(E grad_f) * y)           (real weights, USER mode: tffr_weight_grad)
 
-Every product runs in the CUDA kernels; this module only orders the calls.
+and for y = D E f, grad_f = E^H D grad_y; for y = E f, grad_f = E^H grad_y.
+Every product, and every step of the conjugate-gradient solver, runs in the
+library's CUDA kernels; this module orders the calls and converts dtypes.
 """
 
 from __future__ import annotations
@@ -28,31 +30,35 @@ def _c64(t: torch.Tensor) -> torch.Tensor:
     return t if t.dtype == torch.complex64 else t.to(torch.complex64)
 
 
+def _set_user_weights(plan: Plan, D):
+    if D is not None:
+        plan.weights(mode="user", user_D=D.detach().float().contiguous(), count=False)
+
+
 class _Adjoint(torch.autograd.Function):
     """f = E^H D y (D: the plan's weights, or the given user weights)."""
 
     @staticmethod
     def forward(ctx, values, D, plan: Plan):
-        if D is not None:
-            plan.weights(mode="user", user_D=D.detach().float().contiguous(), count=False)
-        f = plan.adjoint(_c64(values).contiguous())
+        _set_user_weights(plan, D)
+        v = _c64(values).contiguous()
+        f = plan.adjoint(v)
         ctx.plan = plan
-        ctx.save_for_backward(values, D)
+        ctx.values_dtype = values.dtype
+        ctx.save_for_backward(v, D)
         return f
 
     @staticmethod
     def backward(ctx, grad_f):
         plan = ctx.plan
-        values, D = ctx.saved_tensors
-        g = grad_f.contiguous().to(torch.complex64)
+        v, D = ctx.saved_tensors
+        g = _c64(grad_f).contiguous()
         grad_y = grad_D = None
-        if D is not None:
-            plan.weights(mode="user", user_D=D.detach().float().contiguous(), count=False)
+        _set_user_weights(plan, D)
         if ctx.needs_input_grad[0]:
-            grad_y = plan.forward(g, apply_weights=True).to(values.dtype)
+            grad_y = plan.forward(g, apply_weights=True).to(ctx.values_dtype)
         if D is not None and ctx.needs_input_grad[1]:
-            Eg = plan.forward(g, apply_weights=False).to(torch.complex128)
-            grad_D = (Eg.conj() * values.to(torch.complex128)).real.to(D.dtype)
+            grad_D = plan.weight_grad(g, v).to(D.dtype)
         return grad_y, grad_D, None
 
 
@@ -68,13 +74,11 @@ class _Forward(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_y):
         plan = ctx.plan
-        g = grad_y.contiguous().to(torch.complex64)
+        g = _c64(grad_y).contiguous()
         if ctx.apply_weights:
             grad_f = plan.adjoint(g)                      # (D E)^H = E^H D
         else:
-            # E^H alone: the adjoint with unit weights, then the plan's weights back
-            raise NotImplementedError("backward of the unweighted forward needs unit weights; "
-                                      "use apply_weights=True or a unit-weight plan")
+            grad_f = plan.adjoint_unweighted(g)           # E^H
         return grad_f.to(ctx.dtype), None, None
 
 
@@ -85,47 +89,23 @@ def tffr_image(plan: Plan, values: torch.Tensor, D: torch.Tensor | None = None) 
     return _Adjoint.apply(values, D, plan)
 
 
-def tffr_samples(plan: Plan, image: torch.Tensor) -> torch.Tensor:
-    """Differentiable y = D E f with the plan's current weights."""
-    return _Forward.apply(image, plan, True)
+def tffr_samples(plan: Plan, image: torch.Tensor, apply_weights: bool = True) -> torch.Tensor:
+    """Differentiable y = D E f (or E f with apply_weights=False) with the plan's current weights."""
+    return _Forward.apply(image, plan, apply_weights)
 
 
-def cg_normal(plan: Plan, values: torch.Tensor, iters: int = 20, tol: float = 0.0,
-              x0: torch.Tensor | None = None, toeplitz: bool = False):
-    """Conjugate gradients on the weighted normal equations E^H D E f = E^H D y.
+def cg_normal(plan: Plan, values: torch.Tensor, iters: int = 20, toeplitz: bool = False):
+    """Conjugate gradients on the weighted normal equations E^H D E f = E^H D y, from f = 0.
 
-    The minimiser of || D^(1/2) (E f - y) ||^2 over images f.  N f = E^H D E f
-    is one forward twin without weights and one adjoint (which applies D), or,
-    with toeplitz=True, the plan's Toeplitz normal operator (three line-FFT
-    passes on the 2M grid, independent of the number of samples; built here by
-    plan.normal_setup()).  Returns (f, residual norms ||b - N f_k|| for
-    k = 0..iters).  FP32 kernels: the residual levels off near 1e-6 of ||b||.
+    The minimiser of || D^(1/2) (E f - y) ||^2 over images f.  E^H D E is one
+    forward twin without weights and one adjoint (which applies D), or, with
+    toeplitz=True, the plan's Toeplitz normal operator (three line-FFT passes on
+    the 2M grid, independent of the number of samples; built here by
+    plan.normal_setup()).  The whole iteration (operator, dot products, vector
+    updates) runs in the library (tffr_cg).  Returns (f, residual norms
+    ||b - N f_k|| for k = 0..iters).  FP32 kernels: the residual levels off near
+    1e-6 of ||b||.
     """
     if toeplitz:
         plan.normal_setup()
-
-        def normal(f):
-            return plan.normal(f.contiguous())
-    else:
-        def normal(f):
-            return plan.adjoint(plan.forward(f.contiguous(), apply_weights=False))
-
-    b = plan.adjoint(_c64(values).contiguous())
-    x = torch.zeros_like(b) if x0 is None else x0.to(torch.complex64).clone()
-    r = b - normal(x) if x0 is not None else b.clone()
-    p = r.clone()
-    rr = torch.vdot(r.flatten(), r.flatten()).real
-    hist = [float(rr.sqrt())]
-    bnorm = float(torch.linalg.vector_norm(b))
-    for _ in range(iters):
-        Ap = normal(p)
-        alpha = rr / torch.vdot(p.flatten(), Ap.flatten()).real
-        x = x + alpha * p
-        r = r - alpha * Ap
-        rr_new = torch.vdot(r.flatten(), r.flatten()).real
-        hist.append(float(rr_new.sqrt()))
-        if tol > 0 and hist[-1] <= tol * bnorm:
-            break
-        p = r + (rr_new / rr) * p
-        rr = rr_new
-    return x, hist
+    return plan.cg(_c64(values).contiguous(), iters=iters, toeplitz=toeplitz)

@@ -8,6 +8,7 @@ to the oracle's arithmetic shows up as a test failure
 ``tests/test_oracle_pins.py``.
 """
 
+import argparse
 import os
 import sys
 
@@ -19,6 +20,15 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import oracle  # noqa: E402
 
 M = 64
+CROP = 256
+CROP_WORKLOAD = "stripmap_4096"
+CROP_FILE = "stripmap_4096_crop256.npy"
+
+
+def crop_box(Mimg: int, side: int = CROP):
+    """The centre crop: pixels j in [M/2 - side/2, M/2 + side/2) on both axes, as (jx0, jy0, nx, ny)."""
+    j0 = Mimg // 2 - side // 2
+    return (j0, j0, side, side)
 
 
 def weight_points():
@@ -41,7 +51,21 @@ def tiny_inputs():
     return lam_x, lam_y, y, jx, jy
 
 
+def write_crop():
+    """The 256 x 256 centre crop of the weighted adjoint (Eq. (fstraight), alpha_n = D_n,
+    tau = 0.97) of the 16,714,266-sample, 4096 x 4096 stripmap workload, by the direct FP64
+    sum: 65,536 pixels x 16.7M terms (about 85 minutes on 8 cores)."""
+    from synth import make_workload
+    wl = make_workload(CROP_WORKLOAD)
+    D = oracle.tffr_weights(wl.lam_x, wl.M)
+    img = oracle.adjoint_image(wl.lam_x, wl.lam_y, wl.values, D, wl.M, wl.M, crop=crop_box(wl.M))
+    np.save(os.path.join(HERE, CROP_FILE), img.astype(np.complex128))
+
+
 def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--crop", action="store_true", help="also write the stripmap_4096 centre crop (slow)")
+    args = ap.parse_args()
     lam = weight_points()
     G = oracle.diag_psi_w(lam, M)
     D97 = oracle.tffr_weights(lam, M, tau=0.97)
@@ -63,6 +87,8 @@ def main():
         f.write("# jx  jy  re  im\n")
         for row in zip(jx, jy, f_px.real, f_px.imag):
             f.write("%d %d %.17g %.17g\n" % row)
+    if args.crop:
+        write_crop()
 
 
 if __name__ == "__main__":

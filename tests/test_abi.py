@@ -78,3 +78,46 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", txt).lower().replace("oracle_", ""), f
+
+
+def test_noalloc_rejects_overlapping_user_weights_and_output_without_touching_the_gpu(lib):
+    """In user mode the no-alloc kernel reads user_D while it writes D_out: the C entry point
+    refuses overlapping ranges before any CUDA call (the pointers are never dereferenced)."""
+    from paper_1910_10908_gb300 import _abi
+    lib = _abi.load()
+    o = _abi.tffr_weight_opts()
+    lib.tffr_default_weight_opts(ctypes.byref(o))
+    o.mode = _abi.WEIGHT_MODES["user"]
+    base = 0x7f0000000000
+    for off in (0, 4 * 100, -4 * 999):               # same array, partial overlaps either way
+        o.user_D = base
+        assert lib.tffr_weights_noalloc(1000, None, None, 64, 64, ctypes.byref(o), ctypes.c_void_p(base + off),
+                                        None, None) == _abi.TFFR_ERR_INVALID_ARG
+
+
+def test_noalloc_wrapper_checks_lengths_and_devices_before_the_call(monkeypatch):
+    """The binding refuses inputs shorter than D_out, and tensors off the current device,
+    before it reaches the library (CPU tensors here; the library is never called)."""
+    import torch
+
+    import paper_1910_10908_gb300 as tf
+
+    def no_call():
+        raise AssertionError("the library must not be reached")
+
+    monkeypatch.setattr(tf._abi, "load", no_call)
+    D = torch.empty(100, dtype=torch.float32)
+    long_x = torch.zeros(100, dtype=torch.float64)
+    short = torch.zeros(99, dtype=torch.float64)
+    with pytest.raises(ValueError, match="lam_x"):
+        tf.tffr_weights_noalloc(short, long_x, 64, 64, D)
+    with pytest.raises(ValueError, match="lam_y"):
+        tf.tffr_weights_noalloc(long_x, short, 64, 64, D, separable=True)
+    with pytest.raises(ValueError, match="user_D"):
+        tf.tffr_weights_noalloc(long_x, long_x, 64, 64, D, mode="user", user_D=torch.zeros(50))
+    with pytest.raises(ValueError, match="user_D"):
+        tf.tffr_weights_noalloc(long_x, long_x, 64, 64, D, mode="user")
+    # a short lam_y is fine when it is not read (range-only weights)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    with pytest.raises(ValueError, match="current CUDA device"):
+        tf.tffr_weights_noalloc(long_x, short, 64, 64, D)

@@ -34,3 +34,20 @@ def test_tiny_adjoint_matches_the_stored_values():
     D = oracle.tffr_weights(lam_x, 8)
     got = oracle.adjoint_pixels(lam_x, lam_y, y, D, 8, 8, jx.astype(np.int64), jy.astype(np.int64))
     np.testing.assert_allclose(got, re + 1j * im, rtol=1e-12, atol=1e-12)
+
+
+def test_stored_stripmap_4096_crop_is_the_oracle_direct_sum():
+    """The stored 256 x 256 centre crop of the 16.7M-sample workload (the reference of the
+    GPU crop test and of the bench's accuracy) against the direct FP64 sum recomputed here
+    at its corners, edge midpoints and centre."""
+    mg = _maker()
+    crop = np.load(os.path.join(GOLDEN, mg.CROP_FILE))
+    assert crop.shape == (mg.CROP, mg.CROP) and crop.dtype == np.complex128
+    from synth import make_workload
+    wl = make_workload(mg.CROP_WORKLOAD)
+    jx0, jy0, nx, ny = mg.crop_box(wl.M)
+    ix = np.array([0, nx - 1, 0, nx - 1, nx // 2, 0, nx - 1, nx // 2, nx // 2])
+    iy = np.array([0, 0, ny - 1, ny - 1, 0, ny // 2, ny // 2, ny - 1, ny // 2])
+    D = oracle.tffr_weights(wl.lam_x, wl.M)
+    got = oracle.adjoint_pixels(wl.lam_x, wl.lam_y, wl.values, D, wl.M, wl.M, jx0 + ix, jy0 + iy)
+    np.testing.assert_allclose(got, crop[iy, ix], rtol=1e-12, atol=1e-9 * np.abs(crop).max())

@@ -7,6 +7,8 @@ random points, which the tests therefore run at width 8, ~1e-7).
 Reduced-precision sample storage has its own bound from its rounding unit.
 """
 
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -450,3 +452,86 @@ def test_both_orders_of_the_fft_passes(order):
         y = plan.forward(dev(f)).cpu().numpy().astype(np.complex128)
     yref = oracle.forward_samples(lx2, ly2, f, Dref2)
     assert rel_l2(y, yref) <= TOL
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_crop():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(GOLDEN, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    return mg, np.load(os.path.join(GOLDEN, mg.CROP_FILE))
+
+
+def test_stripmap_4096_centre_crop_against_the_stored_fp64_crop():
+    """The bench configuration (16,714,266 samples -> 4096^2, c64, FP32 path) against the
+    FP64 oracle's 256 x 256 centre crop, stored by tests/golden/make_golden.py: every one of
+    the 65,536 pixels, as rel-L2 over the crop and as the largest pixel error against the
+    crop's largest magnitude.  The FP16 / BF16 sample-storage variants are held to the
+    rounding unit of their storage on the same crop."""
+    mg, ref = _golden_crop()
+    wl = make_workload(mg.CROP_WORKLOAD)
+    jx0, jy0, nx, ny = mg.crop_box(wl.M)
+    img, _, kept, info = gpu_adjoint(wl.lam_x, wl.lam_y, wl.values, wl.M)
+    assert info["pulse_order"] == 1 and kept == wl.N
+    got = img[jy0:jy0 + ny, jx0:jx0 + nx]
+    assert got.shape == ref.shape == (256, 256)
+    assert rel_l2(got, ref) <= TOL
+    assert np.max(np.abs(got - ref)) <= TOL * np.max(np.abs(ref))
+    v = dev(wl.values)
+    for values, t, bound in (("f16", v.to(torch.complex32), 1e-3),
+                             ("bf16", torch.view_as_real(v).to(torch.bfloat16).contiguous(), 8e-3)):
+        img_v, _, _, _ = gpu_adjoint(wl.lam_x, wl.lam_y, t, wl.M, values=values)
+        assert rel_l2(img_v[jy0:jy0 + ny, jx0:jx0 + nx], ref) <= bound, values
+
+
+def test_stripmap_2048_crop_and_brightest_pixels():
+    """The 2048^2 configuration of the differentiable variant (1024 pulses x 2048
+    frequencies, 2,089,290 samples): a 64 x 64 centre crop and the 16 brightest pixels
+    against the FP64 oracle."""
+    wl = make_workload("stripmap_2048")
+    img, D, kept, info = gpu_adjoint(wl.lam_x, wl.lam_y, wl.values, wl.M)
+    assert info["layout"] == 2 and info["n_rows"] == 1024 and kept == wl.N
+    Dref = oracle.tffr_weights(wl.lam_x, wl.M)
+    j0 = wl.M // 2 - 32
+    crop = oracle.adjoint_image(wl.lam_x, wl.lam_y, wl.values, Dref, wl.M, wl.M, crop=(j0, j0, 64, 64))
+    assert rel_l2(img[j0:j0 + 64, j0:j0 + 64], crop) <= TOL
+    flat = np.argsort(np.abs(img).ravel())[-16:]
+    jy, jx = flat // wl.M, flat % wl.M
+    ref = oracle.adjoint_pixels(wl.lam_x, wl.lam_y, wl.values, Dref, wl.M, wl.M, jx, jy)
+    assert rel_l2(img[jy, jx], ref) <= TOL
+
+
+def _oracle_weights_threaded(lam, M):
+    from concurrent.futures import ThreadPoolExecutor
+    chunks = np.array_split(lam, 16)
+    with ThreadPoolExecutor(8) as ex:
+        return np.concatenate(list(ex.map(lambda c: oracle.tffr_weights(c, M), chunks)))
+
+
+def test_every_patch_of_the_64_patch_batch():
+    """The bench's batch of 64 uneven sub-aperture patches (43.7M samples, sides 256-1024),
+    run as one batch (graph replay): every patch's image against the FP64 oracle at 12
+    random pixels and its 4 brightest."""
+    from paper_1910_10908_gb300.batched import PatchBatch
+    from synth import patch_batch
+    pb = patch_batch(64)
+    with PatchBatch([(m, m, dev(lx), dev(ly)) for m, lx, ly, _ in pb]) as batch:
+        for k, (_, _, _, v) in enumerate(pb):
+            batch.load(k, dev(v))
+        batch.capture()
+        batch.replay()
+        batch.stream.synchronize()
+        images = [im.cpu().numpy().astype(np.complex128) for im in batch.images]
+    g = np.random.default_rng(25)
+    errs = []
+    for (M, lx, ly, v), img in zip(pb, images):
+        D = _oracle_weights_threaded(lx, M)
+        bright = np.argsort(np.abs(img).ravel())[-4:]
+        jx = np.concatenate([g.integers(0, M, 12), bright % M])
+        jy = np.concatenate([g.integers(0, M, 12), bright // M])
+        ref = oracle.adjoint_pixels(lx, ly, v, D, M, M, jx, jy)
+        errs.append(rel_l2(img[jy, jx], ref))
+    assert max(errs) <= TOL, max(errs)
