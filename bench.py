@@ -37,9 +37,7 @@ WORKLOAD = "stripmap_4096"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a stage's
 # kernel on this workload, from one ncu capture of that kernel; an entry is removed
 # when its kernel changes, and a stage without one reports null.
-DRAM_TRAFFIC = {
-    ("col_fft", "pulse_rows"): 228_804_608,     # k_adj_cols_pulse<13>
-}
+DRAM_TRAFFIC = {}
 
 
 def peaks():
@@ -230,10 +228,15 @@ def run_reference(args, world, rank):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def timed_ms(run, stream, world, min_s: float = 1.0, min_iters: int = 3):
+SECTION_S = 1.0          # minimum device time of each side section (--section-s)
+
+
+def timed_ms(run, stream, world, min_s: float | None = None, min_iters: int = 3):
     """Mean milliseconds per call of run() (its work ordered on `stream`), over at least
     min_iters calls and about min_s seconds of device time, max over ranks."""
     import torch
+    if min_s is None:
+        min_s = SECTION_S
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     run()
     torch.cuda.synchronize()
@@ -308,7 +311,8 @@ def run_gpu(args, world, rank, local):
     # ---- timed region: exactly K steps per region, device events on the plan's stream.  When
     # K steps last under a second the region is repeated (back to back, each exactly K steps)
     # so that the clock sampler sees the load; ms_per_step is the median over the regions. ----
-    repeats = max(1, int(1000.0 / max(est_ms * args.steps, 1e-3)) + 1) if args.steps * est_ms < 1000.0 else 1
+    region_ms = 1e3 * SECTION_S
+    repeats = max(1, int(region_ms / max(est_ms * args.steps, 1e-3)) + 1) if args.steps * est_ms < region_ms else 1
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(repeats)]
     launches0 = plan.info()["kernel_launches"]
     with ClockSampler(gpu_id_for_smi(local)) as clk:
@@ -327,7 +331,7 @@ def run_gpu(args, world, rank, local):
     value = whole_job_rate(N, world, ms_max)
 
     # ---- per-kernel times: a separate pass with stage events on the stream ----
-    kp = 200
+    kp = 200 if SECTION_S >= 1.0 else 5
     plan.profile(True)
     for _ in range(kp):
         step()
@@ -413,7 +417,7 @@ def run_gpu(args, world, rank, local):
         return ev_a.elapsed_time(ev_b)
 
     e2e_run(4)
-    e2e_iters = max(8, int(1000.0 / max(e2e_run(8) / 8, 1e-3)))
+    e2e_iters = max(8, int(1e3 * SECTION_S / max(e2e_run(8) / 8, 1e-3)))
     barrier(world)
     e2e_ms = max_over_ranks(e2e_run(e2e_iters) / e2e_iters, world)
     h2d = int(h_lx.numel() * 8 + h_ly.numel() * 8 + h_v.numel() * 8)
@@ -447,7 +451,7 @@ def run_gpu(args, world, rank, local):
             batch.load(k, torch.from_numpy(pv).to(dev))
         timings["per_plan_8_streams"], _ = timed_ms(batch.adjoint_eager, batch.stream, world)
         timings["persistent"], _ = timed_ms(batch.adjoint, batch.stream, world)
-        tuned = batch.tune(reps=10)
+        tuned = batch.tune(reps=10 if SECTION_S >= 1.0 else 1)
         timings["persistent_tuned"], _ = timed_ms(batch.adjoint, batch.stream, world)
         batch.capture()
         timings["graph"], _ = timed_ms(batch.replay, batch.stream, world)
@@ -459,9 +463,9 @@ def run_gpu(args, world, rank, local):
                    "per_plan_8_streams_ms": timings["per_plan_8_streams"],
                    "persistent_ms": timings["persistent"], "persistent_tuned_ms": timings["persistent_tuned"],
                    "graph_ms": timings["graph"],
-                   "launches_per_step": tuned["n_classes"],
-                   "autotuned": [{k: c[k] for k in ("side", "patches", "blocks", "run", "ms")}
-                                 for c in tuned["classes"]],
+                   "launches_per_step": 2 + tuned["n_classes"],
+                   "spread_ms": tuned["spread_ms"],
+                   "autotuned": [{k: c[k] for k in ("side", "patches", "blocks", "ms")} for c in tuned["classes"]],
                    "value": whole_job_rate(batch.samples, world, timings["graph"]), "unit": UNIT}
     del pb, patches
 
@@ -644,7 +648,12 @@ def main():
                     help="run W + K steps of the main workload and nothing else (for ncu captures)")
     ap.add_argument("--batch-only", action="store_true",
                     help="run W + K persistent adjoints of the 64-patch batch and nothing else (for ncu captures)")
+    ap.add_argument("--section-s", type=float, default=1.0,
+                    help="minimum timed length of each side section and of the main timed region (s); "
+                         "the main region still times exactly K steps per repeat")
     args = ap.parse_args()
+    global SECTION_S
+    SECTION_S = max(0.0, args.section_s)
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()

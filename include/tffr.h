@@ -247,46 +247,46 @@ int tffr_cg(tffr_plan_t plan, const void* values, void* image, int iters, int us
  * Batches of independent reconstructions (sub-aperture patches of uneven
  * size; the per-slice structure of Algorithm 1 repeated over patches).  A
  * batch takes plans that each have points and weights set (pulse-row layout,
- * complex64 values, square images of side 256, 512 or 1024, spreading width 6
- * or 8) and fixed device buffers for each plan's samples and image.  Its
- * adjoint runs every patch with one persistent launch per image side: blocks
- * claim work items from a device counter, first one item per pulse row of
- * every patch (range spread; in the pulse-row order of the passes fused with
- * the x FFT, the row kept in shared memory), then, for patches in the
- * fine-row order (more pulse rows than image rows), one item per fine row
- * (azimuth taps and x FFT), then one item per image column (azimuth taps or
- * the fine rows' column, y FFT, deapodisation, image store).  An item waits for
- * the items of its patch it reads; the wait is bounded (1 s of device time by
- * default) and a wait that runs out makes every later wait give up, so the
- * launch always ends; tffr_batch_wait then returns TFFR_ERR_TIMEOUT.
+ * complex64 values, square images of side 256, 512 or 1024, one spreading
+ * width and one set of weight options for all) and fixed device buffers for
+ * each plan's samples and image.  Its adjoint is one spread launch over every
+ * pulse row of every patch (the row buffers), then one persistent FFT launch
+ * per image side whose blocks claim work items from a device counter: one
+ * item per pulse row of the patches in the pulse-row order of the passes (x
+ * FFT), one per fine row of the others (more pulse rows than image rows:
+ * azimuth taps and x FFT), then one per image column (azimuth taps or the
+ * fine rows' column, y FFT, deapodisation, image store).  A column item waits
+ * for its patch's rows; the wait is bounded (1 s of device time by default)
+ * and a wait that runs out makes every later wait give up, so the launch
+ * always ends; tffr_batch_wait then returns TFFR_ERR_TIMEOUT.
  */
 typedef struct tffr_batch_s* tffr_batch_t;
 
 #define TFFR_BATCH_MAX_CLASSES 8
 typedef struct {
     int n_patches;
-    int n_classes;                              /* launches per adjoint: one per (image side, width) */
+    int n_classes;                              /* persistent FFT launches per adjoint: one per image side */
     int64_t samples;                            /* samples of all patches */
     int tuned;                                  /* 1 after tffr_batch_tune */
+    int width;                                  /* spreading width of every patch */
+    float spread_ms;                            /* the tuner's time of the spread launch (0 untuned) */
     int class_side[TFFR_BATCH_MAX_CLASSES];     /* image side of each class */
-    int class_width[TFFR_BATCH_MAX_CLASSES];    /* spreading width */
     int class_patches[TFFR_BATCH_MAX_CLASSES];  /* patches in the class */
     int class_blocks[TFFR_BATCH_MAX_CLASSES];   /* blocks of the class's persistent launch */
-    int class_run[TFFR_BATCH_MAX_CLASSES];      /* spread samples per thread and tile */
-    float class_ms[TFFR_BATCH_MAX_CLASSES];     /* the tuner's best time of the class's launch alone (0 untuned) */
+    float class_ms[TFFR_BATCH_MAX_CLASSES];     /* the tuner's best time of the class's launch (0 untuned) */
 } tffr_batch_info;
 
 /*
  * Create a batch of n plans.  values[i] (device complex64, plan i's N samples)
  * and images[i] (device complex64 [M][M]) stay the batch's buffers: load new
- * samples into them between adjoints.  The batch keeps pointers into the plans:
- * recreate it after tffr_set_points or tffr_weights on any of them.  stream:
- * the stream tffr_batch_adjoint is ordered on (the batch forks its classes to
- * streams of its own and joins them back).  Allocates and synchronises.
+ * samples into them between adjoints.  The batch keeps pointers into the plans
+ * and uses their row buffers and intermediates: recreate it after
+ * tffr_set_points or tffr_weights on any of them, and do not run the plans'
+ * own adjoints concurrently with it.  stream: the stream tffr_batch_adjoint is
+ * ordered on.  Allocates and synchronises.
  * Errors: INVALID_ARG (NULL pointers, n < 1, a plan outside the supported
- * layout, value type, sides or width, or two plans of one class with different
- * weight options or kernel shape); NOT_READY (a plan without points or
- * weights); OOM; CUDA.
+ * layout, value type or sides, or plans with different widths, kernel shapes
+ * or weight options); NOT_READY (a plan without points or weights); OOM; CUDA.
  */
 int tffr_batch_create(const tffr_plan_t* plans, int n, const void* const* values, void* const* images,
                       tffr_stream_t stream, tffr_batch_t* out);
@@ -300,10 +300,11 @@ int tffr_batch_adjoint(tffr_batch_t batch);
  * earlier adjoint: TFFR_ERR_TIMEOUT, else TFFR_OK.  Errors: CUDA. */
 int tffr_batch_wait(tffr_batch_t batch);
 
-/* Autotuner: for each class, time reps launches of every candidate (spread
- * samples per thread and tile 4, 8, 16; blocks per SM 1, 2, 4, ... up to what
- * fits) and keep the fastest; tffr_batch_get_info reports the choice.
- * Synchronises.  Errors: INVALID_ARG (reps outside [1, 1000]); CUDA; TIMEOUT. */
+/* Autotuner: for each class, time reps launches of the persistent FFT kernel
+ * with every candidate grid (blocks per SM 1, 2, 4, ... up to what fits) and
+ * keep the fastest; tffr_batch_get_info reports the choice.  Runs the spread
+ * once first; synchronises.  Errors: INVALID_ARG (reps outside [1, 1000]);
+ * CUDA; TIMEOUT. */
 int tffr_batch_tune(tffr_batch_t batch, int reps);
 
 /* Limit of one wait of a column item for its patch's rows, in seconds of device

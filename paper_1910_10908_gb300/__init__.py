@@ -178,10 +178,10 @@ def tffr_batch_get_info(batch) -> dict:
     info = _abi.tffr_batch_info()
     _check(_abi.load().tffr_batch_get_info(batch, ctypes.byref(info)))
     k = info.n_classes
-    out = {"n_patches": info.n_patches, "n_classes": k, "samples": info.samples, "tuned": bool(info.tuned)}
-    out["classes"] = [{"side": info.class_side[i], "width": info.class_width[i], "patches": info.class_patches[i],
-                       "blocks": info.class_blocks[i], "run": info.class_run[i], "ms": info.class_ms[i]}
-                      for i in range(min(k, 8))]
+    out = {"n_patches": info.n_patches, "n_classes": k, "samples": info.samples, "tuned": bool(info.tuned),
+           "width": info.width, "spread_ms": info.spread_ms}
+    out["classes"] = [{"side": info.class_side[i], "patches": info.class_patches[i],
+                       "blocks": info.class_blocks[i], "ms": info.class_ms[i]} for i in range(min(k, 8))]
     return out
 
 

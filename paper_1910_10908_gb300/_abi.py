@@ -41,9 +41,10 @@ class tffr_plan_info(ctypes.Structure):
 
 class tffr_batch_info(ctypes.Structure):
     _fields_ = [("n_patches", ctypes.c_int), ("n_classes", ctypes.c_int), ("samples", ctypes.c_int64),
-                ("tuned", ctypes.c_int), ("class_side", ctypes.c_int * 8), ("class_width", ctypes.c_int * 8),
+                ("tuned", ctypes.c_int), ("width", ctypes.c_int), ("spread_ms", ctypes.c_float),
+                ("class_side", ctypes.c_int * 8),
                 ("class_patches", ctypes.c_int * 8), ("class_blocks", ctypes.c_int * 8),
-                ("class_run", ctypes.c_int * 8), ("class_ms", ctypes.c_float * 8)]
+                ("class_ms", ctypes.c_float * 8)]
 
 
 STAGES = ["points", "weights", "spread", "row_fft", "col_fft", "fwd_col_fft", "fwd_row_fft", "interp"]

@@ -2,11 +2,12 @@
 sizes).
 
 Each patch has its own plan (points and weights set once, fixed value and
-image buffers).  The batch's adjoint is one persistent launch per image side
-(tffr_batch_adjoint): blocks claim work items from a device counter, a fused
-range spread + x FFT per pulse row of every patch, then the column pass of
-every patch, so that small patches, which cannot fill the GPU on their own,
-share it without a launch of their own.  The launch neither allocates nor
+image buffers).  The batch's adjoint (tffr_batch_adjoint) is one spread launch
+over every pulse row of every patch, then one persistent FFT launch per image
+side whose blocks claim work items from a device counter (the x FFT of every
+pulse row or fine row, then the column pass of every patch), so that small
+patches, which cannot fill the GPU on their own, share it without launches of
+their own.  The launch neither allocates nor
 synchronises, so it is captured once into a CUDA graph and replayed; new
 samples are copied into the fixed value buffers between replays.
 
@@ -28,8 +29,8 @@ class PatchBatch:
 
     patches: list of (Mx, My, lam_x, lam_y) with device float64 coordinates
     (kept by reference, like Plan.set_points).  persistent=True builds the
-    persistent batch (square patches of side 256, 512 or 1024 with complex64
-    samples and width 6 or 8); persistent=False keeps only the per-plan path.
+    batch launches (square patches of side 256, 512 or 1024 with complex64
+    samples); persistent=False keeps only the per-plan path.
     """
 
     def __init__(self, patches, *, values: str = "c64", width: int = 6, device=None, streams: int = 8,
@@ -77,7 +78,7 @@ class PatchBatch:
         tffr_batch_wait(self._persistent())
 
     def tune(self, reps: int = 5) -> dict:
-        """Autotune the persistent launches (blocks per SM, spread run length); returns info()."""
+        """Autotune the persistent FFT launches (blocks per SM); returns info()."""
         tffr_batch_tune(self._persistent(), reps)
         return self.info()
 

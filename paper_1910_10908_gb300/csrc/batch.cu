@@ -1,24 +1,27 @@
-// Persistent adjoint of a batch of pulse-row patches (sub-apertures of uneven
-// size), one launch per image-size class.
+// Adjoint of a batch of pulse-row patches (sub-apertures of uneven size):
+// one spread launch over every pulse row of every patch, then one persistent
+// FFT launch per image side.
 //
-// Every block loops over work items claimed from one device counter:
-//   row items (one per pulse row of every patch): the row is spread into
-//     shared memory (the range spread of the single-image path, with the FP64
-//     weight decisions taken inline); in the pulse-row order of the passes it
-//     is transformed along x right there (the x pass, with its sparse first
-//     stage), the M kept modes going to the patch's intermediate F; in the
-//     fine-row order it is stored to the patch's row buffers R;
-//   fine-row items (fine-row order only, one per fine row): wait for the
-//     patch's row items, add the azimuth taps of the row buffers, transform
-//     along x into the intermediate T;
-//   column items (one per image column of every patch): wait for the patch's
-//     row (or fine-row) items, gather the column's azimuth taps from F (or read
-//     the column of T), transform along y, deapodise and store the column of
-//     the image.
-// Items are claimed in that order, so a wait is only ever on items that
-// running blocks have already claimed, and it ends; it is still bounded
-// (wait_ns of device time), and a wait that runs out raises an error bit and
-// an abort flag that ends every later wait at once.
+// The spread launch (k_batch_spread) is the range spread of the single-image
+// path with the patches' rows as one grid: block b looks up its patch and
+// pulse row, stages the row's samples in shared memory and writes the row
+// buffer R_p; the samples whose weight needs the FP64 decision are added by
+// k_batch_spread_deferred.
+//
+// The persistent FFT launch of a class (k_batch_fft) loops over work items
+// claimed from one device counter:
+//   row items (pulse-row order of the passes, one per pulse row): the x FFT
+//     of R_p, the M kept modes into the patch's intermediate F (column-major:
+//     F[jx ldq + q]);
+//   fine-row items (fine-row order, one per fine row): the azimuth taps of the
+//     row buffers, then the x FFT into T (column-major: T[jx n + r]);
+//   column items (one per image column): wait until the patch's row (or
+//     fine-row) items are done, gather the azimuth taps from the column of F
+//     (or read the column of T), FFT along y, deapodise, store the column.
+// Items are claimed in that order, so a column item only ever waits for items
+// that running blocks have already claimed, and the wait ends; it is still
+// bounded (wait_ns of device time), and a wait that runs out raises an error
+// bit and an abort flag that ends every later wait at once.
 
 #include "batch_launch.h"
 #include "kernels_spread.cuh"
@@ -51,6 +54,123 @@ __device__ __forceinline__ int find_patch(const int* __restrict__ first, int n, 
     return lo;
 }
 
+// ---------------------------------------------------------------------------
+// Spread of every pulse row of every patch
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kSpreadThreads, 4)
+k_batch_spread(BatchSpreadArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* s_lam = reinterpret_cast<double*>(smem_raw);
+    float2* s_val = reinterpret_cast<float2*>(s_lam + kSpreadStageElems);
+    float2* s_row = s_val + kSpreadStageElems;
+    constexpr int H = W / 2;
+    const int tid = threadIdx.x;
+    const int k = find_patch(a.row_first, a.npatch, blockIdx.x);
+    const BatchPatch* __restrict__ bp = a.patches + k;
+    const int p = blockIdx.x - __ldg(&a.row_first[k]);
+    const int M = __ldg(&bp->M), n = __ldg(&bp->n);
+    const int len = __ldg(&bp->row_len[p]), clo = __ldg(&bp->row_clo[p]);
+    const bool periodic = (len == n) && (clo == 0);
+    const int64_t s0 = __ldg(&bp->row_start[p]);
+    const int L = (int)(__ldg(&bp->row_end[p]) - s0);
+    const WeightArgs& wa = a.wa;
+    for (int i = tid; i < len; i += kSpreadThreads) s_row[i] = make_float2(0.f, 0.f);
+    float dy = 1.0f;
+    bool dy_exact = false, edges = true;
+    const double lam_y_row = __ldg(&bp->row_lam_y[p]);
+    if (wa.mode == 0) {
+        if (wa.separable) {
+            const float gy = g_fitted(__ldg(&bp->row_ly[p]), __ldg(&bp->row_fy[p]), M, wa, dy_exact);
+            dy = (gy != 0.0f) ? __frcp_rn(gy) : 0.0f;
+        }
+        const int mn = clo + (H - 1), mx = clo + len - H - 1;
+        edges = periodic || (mn >> 1) - wa.reach < -(M / 2) || (mx >> 1) + wa.reach >= M - M / 2;
+    }
+    const int run = (tid >> 5) + (kSpreadThreads / 32) * (tid & 31);
+    const double* __restrict__ g_lam = bp->lam_x + s0;
+    const float2* __restrict__ g_val = bp->values + s0;
+    const float* user_D = bp->user_D;
+    const int tag = (k << 16) | p;                         // the deferred list's row field: patch and row
+    for (int t0 = 0; t0 < L; t0 += kSpreadTile) {
+        const int cnt = min(kSpreadTile, L - t0);
+        __syncthreads();                                   // row zeroed / previous tile consumed
+        for (int e = tid; e < cnt; e += kSpreadThreads) {
+            cp_async_elem<8>(&s_lam[spread_pad(e)], &g_lam[t0 + e]);
+            cp_async_elem<8>(&s_val[spread_pad(e)], &g_val[t0 + e]);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // a short tile spreads its samples over every thread: runs of
+        // ceil(cnt / threads) samples (at most kSpreadRun)
+        const int rl = min(kSpreadRun, (cnt + kSpreadThreads - 1) / kSpreadThreads);
+        const int i0 = t0 + run * rl;
+        const int i1 = min(t0 + cnt, i0 + rl);
+        if (i0 >= i1) continue;
+        const StagedSamples<float2> src{s_lam, s_val, t0};
+        if (wa.mode == 0)
+            spread_run<float2, W, 0>(s0, i0, i1, tag, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp,
+                                     a.defer, s_row, user_D);
+        else if (wa.mode == 1)
+            spread_run<float2, W, 1>(s0, i0, i1, tag, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp,
+                                     a.defer, s_row, user_D);
+        else
+            spread_run<float2, W, 2>(s0, i0, i1, tag, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp,
+                                     a.defer, s_row, user_D);
+    }
+    __syncthreads();
+    float2* out = bp->R + __ldg(&bp->row_off[p]);
+    for (int i = tid; i < len; i += kSpreadThreads) out[i] = s_row[i];
+}
+
+// The deferred samples of k_batch_spread: D_n decided in FP64, then added into
+// their row buffers with global atomics (after k_batch_spread stored them).
+template <int W>
+__global__ void __launch_bounds__(256)
+k_batch_spread_deferred(BatchSpreadArgs a) {
+    constexpr int H = W / 2;
+    __shared__ int s_count;
+    const DeferList& defer = a.defer;
+    if (threadIdx.x == 0) s_count = *(volatile int*)defer.count;
+    __syncthreads();
+    const int count = min(s_count, defer.cap);
+    // the last block to have read the count puts both counters back to zero
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&defer.count[1], 1) == (int)gridDim.x - 1) {
+            defer.count[0] = 0;
+            defer.count[1] = 0;
+        }
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const int2 e = defer.item[i];
+        const int n = e.x, k = e.y >> 16, p = e.y & 0xffff;
+        const BatchPatch* __restrict__ bp = a.patches + k;
+        const int M = bp->M, nx = bp->n;
+        const double lam = bp->lam_x[n];
+        int cell;
+        float f;
+        fine_coord(lam, cell, f);
+        const float d = weight_exact(lam, bp->row_lam_y[p], M, M, a.wa);
+        if (d == 0.0f) continue;
+        const float2 v = cscale(bp->values[n], d);
+        float wt[W];
+        taps_all<W>(a.tp, f, wt);
+        const int len = bp->row_len[p], clo = bp->row_clo[p];
+        const bool periodic = (len == nx) && (clo == 0);
+        float2* out = bp->R + bp->row_off[p];
+#pragma unroll
+        for (int s = 0; s < W; ++s) {
+            const int c = cell - (H - 1) + s;
+            atomicAdd(&out[periodic ? wrapmod(c, nx) : (c - clo)], cscale(v, wt[s]));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent FFT items of one class
+// ---------------------------------------------------------------------------
+
 // Column epilogue: keep the M = N/2 wanted y modes, deapodise, store column jx.
 template <int LOGN>
 struct ColStore {
@@ -67,22 +187,44 @@ struct ColStore {
     }
 };
 
-// x FFT of a row held in buf[0, len) (line cell j = buf[(j - clo) mod N]),
+// Row epilogue into a column-major intermediate: keep the M = N/2 wanted x
+// modes, deapodise (and undo a shift with the thread's phase factor), store
+// entry `row` of column jx at X[jx ld + row].  The column items then read
+// their column contiguously; the scattered stores are the row items' (stores
+// do not stall the issuing thread).
+template <int LOGN, bool RAMP>
+struct RowOutCM {
+    int row, ld;
+    const float* deap_x;
+    float2* X;
+    float2 ramp;
+    __device__ __forceinline__ void operator()(int o, float2 v) const {
+        constexpr int N = 1 << LOGN, HALF = N / 4;
+        int jx;
+        if (o < HALF) jx = o + HALF;
+        else if (o >= N - HALF) jx = o - (N - HALF);
+        else return;
+        if constexpr (RAMP) v = cmul(v, ramp);
+        X[(size_t)jx * ld + row] = cscale(v, __ldg(&deap_x[jx]));
+    }
+};
+
+// x FFT of a row buffer Rp[0, len) (line cell j = Rp[(j - clo) mod N]),
 // shifted by a multiple of T so that a short row touches only the first U of
-// each thread's V first-stage points (see k_adj_rows_pulse).
+// each thread's V first-stage points (the shift s = j0 T is undone by the
+// phase factor W_V^{j0 k}, k = tid mod V for every output of the thread).
 template <int LOGN, int U>
-__device__ __forceinline__ void row_fft_sparse(float2* buf, int off, int len, int j0, const Twiddles& tw,
-                                               QuadOut<LOGN, true>& epi) {
+__device__ __forceinline__ void row_fft_sparse(const float2* __restrict__ Rp, int off, int len, int j0, float2* buf,
+                                               const Twiddles& tw, RowOutCM<LOGN, true>& epi) {
     using L = Line<LOGN>;
     const int tid = threadIdx.x;
     float2 v[L::V];
 #pragma unroll
     for (int u = 0; u < L::V; ++u) {
         const int i = tid + u * L::T - off;
-        v[u] = (u < U && i >= 0 && i < len) ? buf[i] : make_float2(0.f, 0.f);
+        v[u] = (u < U && i >= 0 && i < len) ? __ldg(&Rp[i]) : make_float2(0.f, 0.f);
     }
     epi.ramp = tw.t[((j0 * tid) & (L::V - 1)) * (L::NT / L::V)];
-    __syncthreads();                                   // buf read before the first stage overwrites it
     fft_line_epilogue_regs_sparse<LOGN, U, +1>(v, buf, tw, epi);
 }
 
@@ -120,79 +262,31 @@ __device__ __forceinline__ void publish(const BatchClassArgs& a, int* cnt) {
     if (threadIdx.x == 0 && !a.hold) atomicAdd(cnt, 1);
 }
 
-template <int LOGN, int W>
+// Row item (pulse-row order): x FFT of the row buffer of place q.
+template <int LOGN>
 __device__ void batch_row(const BatchClassArgs& a, int item, float2* buf, const Twiddles& tw) {
     using L = Line<LOGN>;
-    constexpr int N = L::N, M = N / 2, H = W / 2;
+    constexpr int N = L::N;
     const int tid = threadIdx.x;
     const int k = find_patch(a.row_first, a.npatch, item);
     const BatchPatch* __restrict__ bp = a.patches + k;
     const int q = item - __ldg(&a.row_first[k]);
-    const bool pulse = __ldg(&bp->pulse) != 0;
-    const int p = pulse ? __ldg(&bp->rank_row[q]) : q;      // fine-row order: pulse row q
+    const int p = __ldg(&bp->rank_row[q]);
     const int len = __ldg(&bp->row_len[p]), clo = __ldg(&bp->row_clo[p]);
-    const bool periodic = (len == N) && (clo == 0);
-    const int64_t s0 = __ldg(&bp->row_start[p]);
-    const int Lr = (int)(__ldg(&bp->row_end[p]) - s0);
-    const double* lam_x = bp->lam_x;
-    const float2* values = bp->values;
-    const WeightArgs& wa = a.wa;
-    const float* user_D = bp->user_D;
-    for (int i = tid; i < len; i += L::T) buf[i] = make_float2(0.f, 0.f);
-    float dy = 1.0f;
-    bool dy_exact = false, edges = true;
-    const double lam_y_row = __ldg(&bp->row_lam_y[p]);
-    if (wa.mode == 0) {
-        if (wa.separable) {
-            const float gy = g_fitted(__ldg(&bp->row_ly[p]), __ldg(&bp->row_fy[p]), M, wa, dy_exact);
-            dy = (gy != 0.0f) ? __frcp_rn(gy) : 0.0f;
-        }
-        const int mn = clo + (H - 1), mx = clo + len - H - 1;
-        edges = periodic || (mn >> 1) - wa.reach < -(M / 2) || (mx >> 1) + wa.reach >= M - M / 2;
-    }
-    __syncthreads();
-    // range spread (runs of a.run consecutive samples per thread and tile; the
-    // lanes of a warp are T / 32 runs apart)
-    const int run = L::T >= 32 ? (tid >> 5) + (L::T / 32) * (tid & 31) : tid;
-    const int tile = L::T * a.run;
-    const DeferList none{nullptr, nullptr, 0};
-    const GlobalSamples<float2> src{lam_x, values, s0};
-    for (int t0 = 0; t0 < Lr; t0 += tile) {
-        const int i0 = t0 + run * a.run;
-        const int i1 = min(Lr, i0 + a.run);
-        if (i0 >= i1) continue;
-        if (wa.mode == 0)
-            spread_run<float2, W, 0, true>(s0, i0, i1, p, N, clo, len, periodic, M, edges, dy, dy_exact, src, wa,
-                                           a.tp, none, buf, user_D, lam_y_row, M);
-        else if (wa.mode == 1)
-            spread_run<float2, W, 1, true>(s0, i0, i1, p, N, clo, len, periodic, M, edges, dy, dy_exact, src, wa,
-                                           a.tp, none, buf, user_D, lam_y_row, M);
-        else
-            spread_run<float2, W, 2, true>(s0, i0, i1, p, N, clo, len, periodic, M, edges, dy, dy_exact, src, wa,
-                                           a.tp, none, buf, user_D, lam_y_row, M);
-    }
-    __syncthreads();
-    if (!pulse) {
-        // fine-row order: the row buffer goes to R for the fine-row items
-        float2* out = bp->R + __ldg(&bp->row_off[p]);
-        for (int i = tid; i < len; i += L::T) out[i] = buf[i];
-        publish(a, &a.done[k]);
-        return;
-    }
-    // x FFT of the row, M kept modes into F (entry q of every column)
-    const int c = wrapmod(clo, N);
-    const int j0 = c / L::T, off = c - j0 * L::T;
-    const int U = (off + len + L::T - 1) / L::T;
+    const float2* Rp = bp->R + __ldg(&bp->row_off[p]);
     float2* F = bp->F;
     const int ldq = __ldg(&bp->ldq);
     const float* deap_x = bp->deap_x;
+    const int c = wrapmod(clo, N);
+    const int j0 = c / L::T, off = c - j0 * L::T;
+    const int U = (off + len + L::T - 1) / L::T;
     bool done = false;
     if constexpr (L::V >= 8) {
         if (U <= L::V / 4) {
-            QuadOut<LOGN, true> epi{q, ldq, deap_x, F, make_float2(1.f, 0.f)};
-            if (U <= 1) row_fft_sparse<LOGN, 1>(buf, off, len, j0, tw, epi);
-            else if (U <= 2) row_fft_sparse<LOGN, 2>(buf, off, len, j0, tw, epi);
-            else if constexpr (L::V >= 16) row_fft_sparse<LOGN, 4>(buf, off, len, j0, tw, epi);
+            RowOutCM<LOGN, true> epi{q, ldq, deap_x, F, make_float2(1.f, 0.f)};
+            if (U <= 1) row_fft_sparse<LOGN, 1>(Rp, off, len, j0, buf, tw, epi);
+            else if (U <= 2) row_fft_sparse<LOGN, 2>(Rp, off, len, j0, buf, tw, epi);
+            else if constexpr (L::V >= 16) row_fft_sparse<LOGN, 4>(Rp, off, len, j0, buf, tw, epi);
             done = true;
         }
     }
@@ -201,20 +295,18 @@ __device__ void batch_row(const BatchClassArgs& a, int item, float2* buf, const 
 #pragma unroll
         for (int u = 0; u < L::V; ++u) {
             const int o = wrapmod(tid + u * L::T - clo, N);
-            v[u] = (o < len) ? buf[o] : make_float2(0.f, 0.f);
+            v[u] = (o < len) ? __ldg(&Rp[o]) : make_float2(0.f, 0.f);
         }
-        __syncthreads();
-        QuadOut<LOGN> epi{q, ldq, deap_x, F, make_float2(1.f, 0.f)};
+        RowOutCM<LOGN, false> epi{q, ldq, deap_x, F, make_float2(1.f, 0.f)};
         fft_line_epilogue_regs<LOGN, +1>(v, buf, tw, epi);
     }
     publish(a, &a.done[k]);
 }
 
 // Fine-row item (fine-row order): fine row r of the patch = sum of its azimuth
-// taps times the pulse-row buffers (written in this launch: read through L2),
-// then the x FFT, the M kept modes into row r of T.
+// taps times the pulse-row buffers, then the x FFT, the M kept modes into T.
 template <int LOGN>
-__device__ void batch_fine(const BatchClassArgs& a, int item, float2* buf, const Twiddles& tw, int* s_ok) {
+__device__ void batch_fine(const BatchClassArgs& a, int item, float2* buf, const Twiddles& tw) {
     using L = Line<LOGN>;
     constexpr int N = L::N;
     const int tid = threadIdx.x;
@@ -222,21 +314,22 @@ __device__ void batch_fine(const BatchClassArgs& a, int item, float2* buf, const
     const BatchPatch* __restrict__ bp = a.patches + k;
     const int r = item - __ldg(&a.fine_first[k]);
     for (int i = tid; i < L::PADLEN; i += L::T) buf[i] = make_float2(0.f, 0.f);
-    if (!wait_count(a, &a.done[k], __ldg(&bp->P), s_ok)) return;      // (also orders the zeroing)
+    __syncthreads();
     const float2* R = bp->R;
     const int e0 = __ldg(&bp->tap_start[r]), e1 = __ldg(&bp->tap_start[r + 1]);
     for (int e = e0; e < e1; ++e) {
         const TapEntry te = bp->taps[e];
         const float2* Rp = R + te.off;
         for (int i = tid; i < te.len; i += L::T)
-            atomic_add_f2_shared(&buf[L::pad(wrapmod(te.clo + i, N))], cscale(__ldcg(&Rp[i]), te.wy));
+            atomic_add_f2_shared(&buf[L::pad(wrapmod(te.clo + i, N))], cscale(__ldg(&Rp[i]), te.wy));
     }
     __syncthreads();
-    RowOut<LOGN> epi{r, bp->deap_x, bp->F};
+    RowOutCM<LOGN, false> epi{r, N, bp->deap_x, bp->F, make_float2(1.f, 0.f)};
     fft_line_epilogue<LOGN, +1>(buf, tw, epi);
     publish(a, &a.fine_done[k]);
 }
 
+// Column item: wait for the patch's rows, then the y pass of column jx.
 template <int LOGN>
 __device__ void batch_col(const BatchClassArgs& a, int item, float2* buf, const Twiddles& tw, int* s_ok) {
     using L = Line<LOGN>;
@@ -248,12 +341,12 @@ __device__ void batch_col(const BatchClassArgs& a, int item, float2* buf, const 
     const int P = __ldg(&bp->P);
     ColStore<LOGN> epi{bp->deap_y, bp->image, jx};
     if (!__ldg(&bp->pulse)) {
-        // fine-row order: column jx of T [N][M] straight into the first stage's registers
+        // fine-row order: column jx of T straight into the first stage's registers
         if (!wait_count(a, &a.fine_done[k], N, s_ok)) return;
-        const float2* Tc = bp->F + jx;
+        const float2* Tc = bp->F + (size_t)jx * N;
         float2 v[V];
 #pragma unroll
-        for (int u = 0; u < V; ++u) v[u] = __ldcg(&Tc[(size_t)(tid + u * L::T) * (N / 2)]);
+        for (int u = 0; u < V; ++u) v[u] = __ldcg(&Tc[tid + u * L::T]);
         fft_line_epilogue_regs<LOGN, +1>(v, buf, tw, epi);
         return;
     }
@@ -261,8 +354,8 @@ __device__ void batch_col(const BatchClassArgs& a, int item, float2* buf, const 
     // column jx of F into shared memory (read through L2: written in this launch)
     float2* fcol = buf + N / 2;
     const int ldq = __ldg(&bp->ldq);
-    const float2* Fb = bp->F + (size_t)(jx >> 2) * ldq * 4 + (jx & 3);
-    for (int qq = tid; qq < P; qq += L::T) fcol[qq] = __ldcg(&Fb[(size_t)qq * 4]);
+    const float2* Fc = bp->F + (size_t)jx * ldq;
+    for (int qq = tid; qq < P; qq += L::T) fcol[qq] = __ldcg(&Fc[qq]);
     __syncthreads();
     // azimuth taps gathered from the fine-row table (K slots per fine row)
     const int2* ell = bp->ell;
@@ -285,10 +378,11 @@ __device__ void batch_col(const BatchClassArgs& a, int item, float2* buf, const 
     fft_line_epilogue_regs<LOGN, +1>(v, buf, tw, epi);
 }
 
-// 128 registers a thread: Line<LOGN>::T threads, 65536 / (128 T) blocks an SM.
-template <int LOGN, int W>
-__global__ void __launch_bounds__(Line<LOGN>::T, 65536 / (128 * Line<LOGN>::T))
-k_batch_adjoint(BatchClassArgs a) {
+// 96 registers a thread (Line<LOGN>::T threads, 65536 / (96 T) blocks an SM),
+// as the single-image x pass of these line lengths.
+template <int LOGN>
+__global__ void __launch_bounds__(Line<LOGN>::T, 65536 / (96 * Line<LOGN>::T))
+k_batch_fft(BatchClassArgs a) {
     extern __shared__ float2 smem[];
     LineSmem<LOGN> S(smem);
     __shared__ int s_item, s_ok;
@@ -300,22 +394,16 @@ k_batch_adjoint(BatchClassArgs a) {
         const int item = s_item;
         __syncthreads();                               // read by every thread before the next claim
         if (item >= a.total) break;
-        if (item < a.rows_total) batch_row<LOGN, W>(a, item, S.buf, tw);
-        else if (item < a.rows_total + a.fine_total) batch_fine<LOGN>(a, item - a.rows_total, S.buf, tw, &s_ok);
+        if (item < a.rows_total) batch_row<LOGN>(a, item, S.buf, tw);
+        else if (item < a.rows_total + a.fine_total) batch_fine<LOGN>(a, item - a.rows_total, S.buf, tw);
         else batch_col<LOGN>(a, item - a.rows_total - a.fine_total, S.buf, tw, &s_ok);
     }
 }
 
-template <int LOGN, int W>
-cudaError_t attr_one() {
-    return cudaFuncSetAttribute(k_batch_adjoint<LOGN, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)line_smem_bytes<LOGN>());
-}
-
-template <int LOGN, int W>
+template <int LOGN>
 int occupancy_one() {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_adjoint<LOGN, W>, Line<LOGN>::T,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_fft<LOGN>, Line<LOGN>::T,
                                                       line_smem_bytes<LOGN>()) != cudaSuccess)
         return 0;
     return b;
@@ -323,51 +411,70 @@ int occupancy_one() {
 
 }  // namespace
 
-// Image sides 256, 512 and 1024 (lines of 512, 1024, 2048 fine cells),
-// spreading widths 6 and 8.
-#define TFFR_BATCH_SWITCH(logn, w, CALL)                       \
-    switch ((logn) * 16 + (w)) {                               \
-        case 9 * 16 + 6: CALL(9, 6); break;                    \
-        case 9 * 16 + 8: CALL(9, 8); break;                    \
-        case 10 * 16 + 6: CALL(10, 6); break;                  \
-        case 10 * 16 + 8: CALL(10, 8); break;                  \
-        case 11 * 16 + 6: CALL(11, 6); break;                  \
-        case 11 * 16 + 8: CALL(11, 8); break;                  \
-        default: break;                                        \
-    }
+bool batch_class_supported(int logn, int w) { return logn >= 9 && logn <= 11 && w >= 2 && w <= 8 && !(w & 1); }
 
-bool batch_class_supported(int logn, int w) { return logn >= 9 && logn <= 11 && (w == 6 || w == 8); }
-
-int batch_threads(int logn) { return (1 << logn) / line_v(1 << logn); }
-
-size_t batch_smem(int logn) {
-    switch (logn) {
-        case 9: return line_smem_bytes<9>();
-        case 10: return line_smem_bytes<10>();
-        default: return line_smem_bytes<11>();
-    }
+size_t batch_spread_smem(int max_len) {
+    return (size_t)kSpreadStageElems * (sizeof(double) + sizeof(float2)) + (size_t)max_len * sizeof(float2);
 }
 
 cudaError_t batch_set_attributes() {
-    cudaError_t e = cudaSuccess;
-#define A(LG, W) if (e == cudaSuccess) e = attr_one<LG, W>()
-    A(9, 6); A(9, 8); A(10, 6); A(10, 8); A(11, 6); A(11, 8);
-#undef A
+    const int spread_max = (int)batch_spread_smem(kFftNMax);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_spread<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, spread_max);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_spread<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, spread_max);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_spread<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, spread_max);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_spread<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, spread_max);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_fft<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)line_smem_bytes<9>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_fft<10>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)line_smem_bytes<10>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_fft<11>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)line_smem_bytes<11>());
     return e;
 }
 
-int batch_max_blocks_per_sm(int logn, int w) {
-    int b = 0;
-#define O(LG, W) b = occupancy_one<LG, W>()
-    TFFR_BATCH_SWITCH(logn, w, O)
-#undef O
-    return b;
+int batch_max_blocks_per_sm(int logn) {
+    switch (logn) {
+        case 9: return occupancy_one<9>();
+        case 10: return occupancy_one<10>();
+        case 11: return occupancy_one<11>();
+        default: return 0;
+    }
 }
 
-void launch_batch_class(int logn, int w, int grid, cudaStream_t s, const BatchClassArgs& a) {
-#define L(LG, W) k_batch_adjoint<LG, W><<<grid, Line<LG>::T, line_smem_bytes<LG>(), s>>>(a)
-    TFFR_BATCH_SWITCH(logn, w, L)
-#undef L
+void launch_batch_spread(int w, int rows, int max_len, cudaStream_t s, const BatchSpreadArgs& a) {
+    const size_t smem = batch_spread_smem(max_len);
+    const bool deferred = a.wa.mode == 0;                  // FP64 decisions exist in tFFR mode only
+    switch (w) {
+        case 2:
+            k_batch_spread<2><<<rows, kSpreadThreads, smem, s>>>(a);
+            if (deferred) k_batch_spread_deferred<2><<<152 * 2, 256, 0, s>>>(a);
+            break;
+        case 4:
+            k_batch_spread<4><<<rows, kSpreadThreads, smem, s>>>(a);
+            if (deferred) k_batch_spread_deferred<4><<<152 * 2, 256, 0, s>>>(a);
+            break;
+        case 6:
+            k_batch_spread<6><<<rows, kSpreadThreads, smem, s>>>(a);
+            if (deferred) k_batch_spread_deferred<6><<<152 * 2, 256, 0, s>>>(a);
+            break;
+        default:
+            k_batch_spread<8><<<rows, kSpreadThreads, smem, s>>>(a);
+            if (deferred) k_batch_spread_deferred<8><<<152 * 2, 256, 0, s>>>(a);
+            break;
+    }
+}
+
+void launch_batch_fft(int logn, int grid, cudaStream_t s, const BatchClassArgs& a) {
+    switch (logn) {
+        case 9: k_batch_fft<9><<<grid, Line<9>::T, line_smem_bytes<9>(), s>>>(a); break;
+        case 10: k_batch_fft<10><<<grid, Line<10>::T, line_smem_bytes<10>(), s>>>(a); break;
+        default: k_batch_fft<11><<<grid, Line<11>::T, line_smem_bytes<11>(), s>>>(a); break;
+    }
 }
 
 }  // namespace tffr

@@ -1,23 +1,24 @@
-// Persistent adjoint of a batch of pulse-row patches: device descriptors and
-// the host launcher (batch.cu).  One launch per image-size class runs every
-// patch of that class: fused spread + x-FFT items for all pulse rows, then
-// column items, claimed from a device counter.
+// Adjoint of a batch of pulse-row patches: device descriptors and the host
+// launchers (batch.cu).  One spread launch over every pulse row of every
+// patch, then one persistent FFT launch per image-size class over the class's
+// row, fine-row and column items, claimed from a device counter.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "kernels_points.cuh"
+#include "kernels_spread.cuh"
 #include "types.cuh"
 
 namespace tffr {
 
 // One patch: the plan's arrays (points, weights, pulse rows, tap table,
 // intermediate) and the caller's fixed value and image buffers.  Patches in
-// the pulse-row order of the passes (at most M pulse rows) run fused spread +
-// x FFT items per pulse row and gather the azimuth taps in the column items;
-// the others run spread items (row buffers R), then fine-row items (azimuth
-// taps and x FFT of each of the n fine rows into T), then plain column items.
+// the pulse-row order of the passes (at most M pulse rows) run x-FFT items per
+// pulse row and gather the azimuth taps in the column items; the others run
+// fine-row items (azimuth taps and x FFT of each of the n fine rows into T),
+// then plain column items.
 struct BatchPatch {
     int pulse;                          // 1: pulse-row order, 0: fine-row order
     int M, n, P, ldq, K;                // image side (square), fine grid side 2M, pulse rows, F stride, tap slots
@@ -32,7 +33,7 @@ struct BatchPatch {
     const int2* ell;                    // [K][n] fine-row tap table
     const float* deap_x;                // [M]
     const float* deap_y;                // [M]
-    float2* F;                          // pulse-row order: [M / 4][ldq][4]; fine-row order: T [n][M]
+    float2* F;                          // column-major: pulse-row order F [M][ldq]; fine-row order T [M][n]
     const int* tap_start;               // fine-row order: [n + 1] azimuth taps of each fine row (CSR)
     const TapEntry* taps;
     const int64_t* row_off;             // offset of each pulse row's buffer in R
@@ -43,10 +44,20 @@ struct BatchPatch {
     float2* image;                      // caller's image [M][M]
 };
 
-// Every launch-wide argument of one class's kernel.
+// The spread launch over every pulse row of every patch.
+struct BatchSpreadArgs {
+    const BatchPatch* patches;          // [npatch] every patch of the batch (npatch < 2^15, rows < 2^16)
+    const int* row_first;               // [npatch + 1] first block (pulse row) of each patch
+    int npatch;
+    WeightArgs wa;                      // the batch's weight evaluation (the patch's M decides the edges)
+    TapPoly tp;
+    DeferList defer;                    // samples for the FP64 decision: (sample, patch << 16 | row)
+};
+
+// Every launch-wide argument of one class's persistent FFT kernel.
 struct BatchClassArgs {
-    const BatchPatch* patches;          // [npatch]
-    const int* row_first;               // [npatch + 1] first row item of each patch (P each)
+    const BatchPatch* patches;          // [npatch] the class's patches
+    const int* row_first;               // [npatch + 1] first row item (P each in pulse-row order, else 0)
     const int* fine_first;              // [npatch + 1] first fine-row item (n each in fine-row order, else 0)
     const int* col_first;               // [npatch + 1] first column item of each patch (M each)
     int npatch, rows_total, fine_total, total;   // items: rows, then fine rows, then columns
@@ -55,25 +66,23 @@ struct BatchClassArgs {
     int* fine_done;                     // [npatch] finished fine-row items, zero before the launch
     int* err;                           // [0] error bits (1: a wait timed out), [1] abort flag
     unsigned long long wait_ns;         // limit of one wait for a patch's rows
-    int run;                            // samples per thread per spread tile
-    int hold;                           // test hook: row items never publish (every wait times out)
-    WeightArgs wa;                      // the class's weight evaluation (the patch's Mx decides the edges)
-    TapPoly tp;
+    int hold;                           // test hook: items never publish (every wait times out)
     FftTables tab;                      // twiddles of the class's line length
 };
+
+// Whether a class (line length 2^logn, spreading width w) is supported.
+bool batch_class_supported(int logn, int w);
+
+// Dynamic shared memory of the spread launch for rows of up to max_len cells.
+size_t batch_spread_smem(int max_len);
 
 // Kernel attributes (dynamic shared memory) of every instantiation.
 cudaError_t batch_set_attributes();
 
-// Whether a class (line length 2^logn, spreading width w) has a kernel.
-bool batch_class_supported(int logn, int w);
+// Blocks of a class's FFT kernel that fit on one SM.
+int batch_max_blocks_per_sm(int logn);
 
-// Threads per block and dynamic shared memory of a class's kernel.
-int batch_threads(int logn);
-size_t batch_smem(int logn);
-// Blocks of the class's kernel that fit on one SM.
-int batch_max_blocks_per_sm(int logn, int w);
-
-void launch_batch_class(int logn, int w, int grid, cudaStream_t s, const BatchClassArgs& a);
+void launch_batch_spread(int w, int rows, int max_len, cudaStream_t s, const BatchSpreadArgs& a);
+void launch_batch_fft(int logn, int grid, cudaStream_t s, const BatchClassArgs& a);
 
 }  // namespace tffr

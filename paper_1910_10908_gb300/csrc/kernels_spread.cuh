@@ -210,8 +210,11 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
         }
         cp_async_wait_all();
         __syncthreads();
-        const int i0 = t0 + run * kSpreadRun;
-        const int i1 = min(t0 + cnt, i0 + kSpreadRun);
+        // a short tile spreads its samples over every thread: runs of
+        // ceil(cnt / threads) samples (at most kSpreadRun)
+        const int rl = min(kSpreadRun, (cnt + kSpreadThreads - 1) / kSpreadThreads);
+        const int i0 = t0 + run * rl;
+        const int i1 = min(t0 + cnt, i0 + rl);
         if (i0 >= i1) continue;
         const StagedSamples<VT> src{s_lam, s_val, t0};
         if (wa.mode == 0)

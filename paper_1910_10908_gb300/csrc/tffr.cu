@@ -1464,18 +1464,14 @@ int tffr_cg(tffr_plan_t p, const void* values, void* image, int iters, int use_t
 namespace {
 
 struct BatchClass {
-    int logn = 0, w = 0;
+    int logn = 0;
     std::vector<int> members;                          // indices into the batch's plans
     BatchPatch* d_patches = nullptr;
     int* d_first = nullptr;                            // row_first[n + 1], fine_first[n + 1], col_first[n + 1]
     int* d_counts = nullptr;                           // next item, done[n], fine_done[n]
     int rows_total = 0, fine_total = 0, cols_total = 0;
-    int grid = 0, run = 8, max_blocks = 1;
+    int grid = 0, max_blocks = 1;
     float tuned_ms = 0.0f;                             // the tuner's best time per launch
-    cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
-    WeightArgs wa;
-    TapPoly tp;
     FftTables tab;
 };
 
@@ -1484,12 +1480,19 @@ struct BatchClass {
 struct tffr_batch_s {
     cudaStream_t stream = nullptr;
     std::vector<BatchClass> cls;
+    BatchPatch* d_patches = nullptr;                   // every patch (the spread launch)
+    int* d_row_first = nullptr;                        // [n + 1] first pulse row of each patch
+    int rows_total = 0, max_len = 0, w = 6;
+    WeightArgs wa;
+    TapPoly tp;
     int* d_err = nullptr;                              // [0] error bits, [1] abort flag
-    cudaEvent_t fork = nullptr;
+    int* d_defer_count = nullptr;                      // the spread's deferred samples: count, finished blocks
+    int2* d_defer = nullptr;                           // [samples]
     int n = 0;
     int64_t samples = 0;
     unsigned long long wait_ns = 1000000000ull;
     int hold = 0, tuned = 0, sms = 0;
+    float spread_ms = 0.0f;                            // the tuner's time of the spread launch
 };
 
 namespace {
@@ -1498,15 +1501,15 @@ void batch_free(tffr_batch_s* b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     for (BatchClass& c : b->cls) {
-        if (c.st) cudaStreamSynchronize(c.st);
         if (c.d_patches) cudaFree(c.d_patches);
         if (c.d_first) cudaFree(c.d_first);
         if (c.d_counts) cudaFree(c.d_counts);
-        if (c.ev) cudaEventDestroy(c.ev);
-        if (c.st) cudaStreamDestroy(c.st);
     }
+    if (b->d_patches) cudaFree(b->d_patches);
+    if (b->d_row_first) cudaFree(b->d_row_first);
+    if (b->d_defer_count) cudaFree(b->d_defer_count);
+    if (b->d_defer) cudaFree(b->d_defer);
     if (b->d_err) cudaFree(b->d_err);
-    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 
@@ -1526,23 +1529,63 @@ BatchClassArgs class_args(const tffr_batch_s* b, const BatchClass& c) {
     a.fine_done = c.d_counts + 1 + n;
     a.err = b->d_err;
     a.wait_ns = b->wait_ns;
-    a.run = c.run;
     a.hold = b->hold;
-    a.wa = c.wa;
-    a.tp = c.tp;
     a.tab = c.tab;
     return a;
 }
 
+cudaError_t launch_spread(const tffr_batch_s* b) {
+    BatchSpreadArgs a;
+    a.patches = b->d_patches;
+    a.row_first = b->d_row_first;
+    a.npatch = b->n;
+    a.wa = b->wa;
+    a.tp = b->tp;
+    a.defer = DeferList{b->d_defer_count, b->d_defer, (int)b->samples};
+    launch_batch_spread(b->w, b->rows_total, b->max_len, b->stream, a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_class(const tffr_batch_s* b, const BatchClass& c) {
-    cudaError_t e = cudaMemsetAsync(c.d_counts, 0, (2 * c.members.size() + 1) * sizeof(int), c.st);
+    cudaError_t e = cudaMemsetAsync(c.d_counts, 0, (2 * c.members.size() + 1) * sizeof(int), b->stream);
     if (e != cudaSuccess) return e;
-    launch_batch_class(c.logn, c.w, c.grid, c.st, class_args(b, c));
+    launch_batch_fft(c.logn, c.grid, b->stream, class_args(b, c));
     return cudaGetLastError();
 }
 
 bool same_weights(const WeightArgs& x, const WeightArgs& y) {
     return x.mode == y.mode && x.separable == y.separable && x.tau_d == y.tau_d && x.a == y.a && x.q == y.q;
+}
+
+BatchPatch patch_desc(const tffr_plan_s* p, const void* values, void* image) {
+    BatchPatch d;
+    d.pulse = p->pulse_order ? 1 : 0;
+    d.M = p->Mx;
+    d.n = p->nx;
+    d.P = p->P;
+    d.ldq = (p->P + 3) & ~3;
+    d.K = p->ell_k;
+    d.row_start = p->row_start.ptr;
+    d.row_end = p->row_end.ptr;
+    d.row_clo = p->row_clo.ptr;
+    d.row_len = p->row_len.ptr;
+    d.row_ly = p->row_ly.ptr;
+    d.row_fy = p->row_fy.ptr;
+    d.row_lam_y = p->row_lam_y.ptr;
+    d.rank_row = p->rank_row.ptr;
+    d.ell = p->ell.ptr;
+    d.deap_x = p->deap_x.ptr;
+    d.deap_y = p->deap_y.ptr;
+    d.F = p->T.ptr;
+    d.tap_start = p->tap_start.ptr;
+    d.taps = p->tap_list.ptr;
+    d.row_off = p->row_off.ptr;
+    d.R = p->R.ptr;
+    d.lam_x = p->lam_x;
+    d.user_D = p->wargs.mode == TFFR_WEIGHTS_USER ? p->D.ptr : nullptr;
+    d.values = reinterpret_cast<const float2*>(values);
+    d.image = reinterpret_cast<float2*>(image);
+    return d;
 }
 
 }  // namespace
@@ -1561,11 +1604,18 @@ int tffr_batch_create(const tffr_plan_t* plans, int n, const void* const* values
         if (p->layout != TFFR_POINTS_ROWS || p->values != TFFR_VALUES_C64 || p->Mx != p->My || p->P < 1 ||
             !batch_class_supported(p->lognx, p->w))
             return TFFR_ERR_INVALID_ARG;
+        // one kernel shape and one weight rule for the whole batch
+        if (p->w != plans[0]->w || p->beta != plans[0]->beta || !same_weights(p->wargs, plans[0]->wargs))
+            return TFFR_ERR_INVALID_ARG;
+        if (p->P >= (1 << 16) || i >= (1 << 15)) return TFFR_ERR_INVALID_ARG;   // the deferred list's encoding
     }
     tffr_batch_s* b = new (std::nothrow) tffr_batch_s();
     if (!b) return TFFR_ERR_OOM;
     b->stream = (cudaStream_t)stream;
     b->n = n;
+    b->w = plans[0]->w;
+    b->wa = plans[0]->wargs;
+    b->tp = plans[0]->taps;
     auto bail = [&](cudaError_t e) {
         batch_free(b);
         return e == cudaErrorMemoryAllocation ? TFFR_ERR_OOM : TFFR_ERR_CUDA;
@@ -1574,95 +1624,75 @@ int tffr_batch_create(const tffr_plan_t* plans, int n, const void* const* values
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return bail(e);
-    // classes: patches of one line length and spreading width share a launch
+    // the spread launch: every patch, one block per pulse row
+    std::vector<BatchPatch> all(n);
+    std::vector<int> row_first(n + 1, 0);
     for (int i = 0; i < n; ++i) {
         const tffr_plan_s* p = plans[i];
+        all[i] = patch_desc(p, values[i], images[i]);
+        row_first[i + 1] = row_first[i] + p->P;
         b->samples += p->N;
-        BatchClass* c = nullptr;
+        b->max_len = std::max(b->max_len, p->max_len);
+        BatchClass* c = nullptr;                          // classes: one line length each
         for (BatchClass& x : b->cls)
-            if (x.logn == p->lognx && x.w == p->w) c = &x;
+            if (x.logn == p->lognx) c = &x;
         if (!c) {
             b->cls.emplace_back();
             c = &b->cls.back();
             c->logn = p->lognx;
-            c->w = p->w;
-            c->wa = p->wargs;
-            c->tp = p->taps;
             c->tab = tables_x(p);
-        } else if (!same_weights(c->wa, p->wargs) || plans[c->members[0]]->beta != p->beta) {
-            batch_free(b);
-            return TFFR_ERR_INVALID_ARG;                 // one weight rule and kernel per class
         }
         c->members.push_back(i);
     }
+    b->rows_total = row_first[n];
+    e = cudaMalloc((void**)&b->d_patches, n * sizeof(BatchPatch));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_row_first, (n + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_patches, all.data(), n * sizeof(BatchPatch), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_row_first, row_first.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(e);
     for (BatchClass& c : b->cls) {
         const int m = (int)c.members.size();
         std::vector<BatchPatch> hp(m);
         std::vector<int> first(3 * (m + 1), 0);
         for (int j = 0; j < m; ++j) {
             const tffr_plan_s* p = plans[c.members[j]];
-            BatchPatch& d = hp[j];
-            d.pulse = p->pulse_order ? 1 : 0;
-            d.M = p->Mx;
-            d.n = p->nx;
-            d.P = p->P;
-            d.ldq = (p->P + 3) & ~3;
-            d.K = p->ell_k;
-            d.row_start = p->row_start.ptr;
-            d.row_end = p->row_end.ptr;
-            d.row_clo = p->row_clo.ptr;
-            d.row_len = p->row_len.ptr;
-            d.row_ly = p->row_ly.ptr;
-            d.row_fy = p->row_fy.ptr;
-            d.row_lam_y = p->row_lam_y.ptr;
-            d.rank_row = p->rank_row.ptr;
-            d.ell = p->ell.ptr;
-            d.deap_x = p->deap_x.ptr;
-            d.deap_y = p->deap_y.ptr;
-            d.F = p->T.ptr;
-            d.tap_start = p->tap_start.ptr;
-            d.taps = p->tap_list.ptr;
-            d.row_off = p->row_off.ptr;
-            d.R = p->R.ptr;
-            d.lam_x = p->lam_x;
-            d.user_D = p->wargs.mode == TFFR_WEIGHTS_USER ? p->D.ptr : nullptr;
-            d.values = reinterpret_cast<const float2*>(values[c.members[j]]);
-            d.image = reinterpret_cast<float2*>(images[c.members[j]]);
-            first[j + 1] = first[j] + p->P;                                        // row items
-            first[m + 1 + j + 1] = first[m + 1 + j] + (d.pulse ? 0 : p->nx);       // fine-row items
+            hp[j] = all[c.members[j]];
+            const bool pulse = hp[j].pulse != 0;
+            first[j + 1] = first[j] + (pulse ? p->P : 0);                          // row items
+            first[m + 1 + j + 1] = first[m + 1 + j] + (pulse ? 0 : p->nx);         // fine-row items
             first[2 * (m + 1) + j + 1] = first[2 * (m + 1) + j] + p->Mx;           // column items
         }
         c.rows_total = first[m];
         c.fine_total = first[2 * m + 1];
         c.cols_total = first[3 * m + 2];
-        c.max_blocks = std::max(1, batch_max_blocks_per_sm(c.logn, c.w));
+        c.max_blocks = std::max(1, batch_max_blocks_per_sm(c.logn));
         c.grid = b->sms * c.max_blocks;
         e = cudaMalloc((void**)&c.d_patches, m * sizeof(BatchPatch));
         if (e == cudaSuccess) e = cudaMalloc((void**)&c.d_first, first.size() * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc((void**)&c.d_counts, (2 * m + 1) * sizeof(int));
         if (e == cudaSuccess) e = cudaMemcpy(c.d_patches, hp.data(), m * sizeof(BatchPatch), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(c.d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev, cudaEventDisableTiming);
         if (e != cudaSuccess) return bail(e);
     }
     e = cudaMalloc((void**)&b->d_err, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_defer_count, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_defer_count, 0, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_defer, std::max<int64_t>(1, b->samples) * sizeof(int2));
     if (e != cudaSuccess) return bail(e);
+    if (b->samples >= (int64_t)0x7fffffff) {
+        batch_free(b);
+        return TFFR_ERR_INVALID_ARG;
+    }
     *out = b;
     return TFFR_OK;
 }
 
 int tffr_batch_adjoint(tffr_batch_t b) {
     if (!b) return TFFR_ERR_INVALID_ARG;
-    if (cudaEventRecord(b->fork, b->stream) != cudaSuccess) return TFFR_ERR_CUDA;
-    for (const BatchClass& c : b->cls) {
-        if (cudaStreamWaitEvent(c.st, b->fork, 0) != cudaSuccess) return TFFR_ERR_CUDA;
+    if (launch_spread(b) != cudaSuccess) return TFFR_ERR_CUDA;
+    for (const BatchClass& c : b->cls)
         if (launch_class(b, c) != cudaSuccess) return TFFR_ERR_CUDA;
-        if (cudaEventRecord(c.ev, c.st) != cudaSuccess) return TFFR_ERR_CUDA;
-        if (cudaStreamWaitEvent(b->stream, c.ev, 0) != cudaSuccess) return TFFR_ERR_CUDA;
-    }
     return TFFR_OK;
 }
 
@@ -1687,6 +1717,7 @@ int tffr_batch_set_wait(tffr_batch_t b, double wait_s, int hold_rows) {
 
 int tffr_batch_tune(tffr_batch_t b, int reps) {
     if (!b || reps < 1 || reps > 1000) return TFFR_ERR_INVALID_ARG;
+    if (launch_spread(b) != cudaSuccess) return TFFR_ERR_CUDA;     // the FFT launches read the row buffers
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return TFFR_ERR_CUDA;
     cudaEvent_t t0, t1;
     if (cudaEventCreate(&t0) != cudaSuccess) return TFFR_ERR_CUDA;
@@ -1695,38 +1726,42 @@ int tffr_batch_tune(tffr_batch_t b, int reps) {
         return TFFR_ERR_CUDA;
     }
     int status = TFFR_OK;
-    const int runs[3] = {4, 8, 16};
+    {
+        cudaError_t e = cudaEventRecord(t0, b->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_spread(b);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e != cudaSuccess) status = TFFR_ERR_CUDA;
+        b->spread_ms = ms / (float)reps;
+    }
     for (BatchClass& c : b->cls) {
+        if (status != TFFR_OK) break;
         float best = 1e30f;
-        int best_grid = c.grid, best_run = c.run;
+        int best_grid = c.grid;
         std::vector<int> blocks;                                      // 1, 2, 4, ... and the most that fit
         for (int x = 1; x < c.max_blocks; x *= 2) blocks.push_back(x);
         blocks.push_back(c.max_blocks);
-        for (int run : runs) {
-            for (int bps : blocks) {
-                c.run = run;
-                c.grid = b->sms * bps;
-                cudaError_t e = launch_class(b, c);                 // warm
-                if (e == cudaSuccess) e = cudaEventRecord(t0, c.st);
-                for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_class(b, c);
-                if (e == cudaSuccess) e = cudaEventRecord(t1, c.st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-                float ms = 0.f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-                if (e != cudaSuccess) {
-                    status = TFFR_ERR_CUDA;
-                    break;
-                }
-                if (ms < best) {
-                    best = ms;
-                    best_grid = c.grid;
-                    best_run = run;
-                }
+        for (int bps : blocks) {
+            c.grid = b->sms * bps;
+            cudaError_t e = launch_class(b, c);                       // warm
+            if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_class(b, c);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            if (e != cudaSuccess) {
+                status = TFFR_ERR_CUDA;
+                break;
             }
-            if (status != TFFR_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_grid = c.grid;
+            }
         }
         c.grid = best_grid;
-        c.run = best_run;
         c.tuned_ms = best / (float)reps;
         if (status != TFFR_OK) break;
     }
@@ -1745,14 +1780,14 @@ int tffr_batch_get_info(tffr_batch_t b, tffr_batch_info* info) {
     info->n_patches = b->n;
     info->n_classes = (int)b->cls.size();
     info->samples = b->samples;
+    info->width = b->w;
+    info->spread_ms = b->spread_ms;
     info->tuned = b->tuned;
     for (int i = 0; i < (int)b->cls.size() && i < TFFR_BATCH_MAX_CLASSES; ++i) {
         const BatchClass& c = b->cls[i];
         info->class_side[i] = (1 << c.logn) / 2;
-        info->class_width[i] = c.w;
         info->class_patches[i] = (int)c.members.size();
         info->class_blocks[i] = c.grid;
-        info->class_run[i] = c.run;
         info->class_ms[i] = c.tuned_ms;
     }
     return TFFR_OK;

@@ -1,7 +1,8 @@
 """Batches of uneven patches (GPU): the per-plan path replayed as one CUDA graph, and
-the persistent launches (one per image side over every patch's rows, then columns)
-against the per-plan images and the FP64 oracle; the bounded wait of the persistent
-launch, made to run out on purpose; the autotuner."""
+the batch launches (one spread over every patch's pulse rows, then one persistent FFT
+launch per image side over rows, fine rows and columns) against the per-plan images
+and the FP64 oracle; the bounded wait of the persistent launch, made to run out on
+purpose; the autotuner."""
 
 import numpy as np
 import pytest
@@ -144,7 +145,7 @@ def test_autotuner_and_graph_capture_of_the_persistent_batch():
         assert info["tuned"]
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         for c in info["classes"]:
-            assert c["run"] in (4, 8, 16) and c["blocks"] % sms == 0 and c["blocks"] >= sms
+            assert c["blocks"] % sms == 0 and c["blocks"] >= sms and c["ms"] > 0
         batch.capture()
         for _ in range(2):
             with torch.cuda.stream(batch.stream):
