@@ -356,23 +356,28 @@ __device__ void batch_col(const BatchClassArgs& a, int item, float2* buf, const 
     const int ldq = __ldg(&bp->ldq);
     const float2* Fc = bp->F + (size_t)jx * ldq;
     for (int qq = tid; qq < P; qq += L::T) fcol[qq] = __ldcg(&Fc[qq]);
+    if (tid < kPlaceCopies) fcol[P + tid] = __ldcg(&Fc[tid % P]);   // the run of a fine row wraps modulo P
     __syncthreads();
-    // azimuth taps gathered from the fine-row table (K slots per fine row)
-    const int2* ell = bp->ell;
+    // azimuth taps gathered from the fine-row table (first place, then one
+    // weight per slot)
+    const int* first = bp->ell_first;
+    const float4* wt = bp->ell_w;
     const int K = __ldg(&bp->K);
     float2 v[V];
+    if (K <= 4) {
 #pragma unroll
-    for (int u = 0; u < V; ++u) {
-        const int r = tid + u * L::T;
-        float2 acc = make_float2(0.f, 0.f);
-        for (int s = 0; s < K; ++s) {
-            const int2 e = __ldg(&ell[(size_t)s * N + r]);
-            const float2 f = fcol[e.x];
-            const float g = __int_as_float(e.y);
-            acc.x = fmaf(g, f.x, acc.x);
-            acc.y = fmaf(g, f.y, acc.y);
+        for (int u = 0; u < V; ++u) {
+            const int r = tid + u * L::T;
+            const float4 w4[1] = {__ldg(&wt[r])};
+            v[u] = gather_taps<1>(fcol, __ldg(&first[r]), w4);
         }
-        v[u] = acc;
+    } else {
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+            const int r = tid + u * L::T;
+            const float4 w4[2] = {__ldg(&wt[r]), __ldg(&wt[N + r])};
+            v[u] = gather_taps<2>(fcol, __ldg(&first[r]), w4);
+        }
     }
     __syncthreads();                                   // fcol read before the first stage overwrites buf
     fft_line_epilogue_regs<LOGN, +1>(v, buf, tw, epi);

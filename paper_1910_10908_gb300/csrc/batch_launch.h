@@ -30,7 +30,8 @@ struct BatchPatch {
     const float* row_fy;
     const double* row_lam_y;
     const int* rank_row;                // pulse row at each place in fine-y order
-    const int2* ell;                    // [K][n] fine-row tap table
+    const int* ell_first;               // [n] first place of each fine row's taps (fine-y order)
+    const float4* ell_w;                // [2][n] tap weights of slots 0-3 and 4-7
     const float* deap_x;                // [M]
     const float* deap_y;                // [M]
     float2* F;                          // column-major: pulse-row order F [M][ldq]; fine-row order T [M][n]

@@ -223,4 +223,12 @@ __device__ __forceinline__ void atomic_add_f2_shared(float2* p, float2 v) {
     asm volatile("red.shared.add.f32 [%0+4], %1;" ::"r"(a), "f"(v.y) : "memory");
 }
 
+// cp.async of one element (4, 8 or 16 bytes) from global into shared memory.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 }  // namespace tffr

@@ -486,19 +486,28 @@ k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_l
 // Azimuth taps as a table of fixed width per fine row (pulse-row order of
 // the FFT passes).  Each pulse row p first takes its place q in fine-y order,
 // q = ly_first[c] + (its arrival among the rows of its fine y cell c), and
-// rank_row[q] = p: the x pass puts row p at place q of F, so that the rows a
-// warp's consecutive fine rows gather are neighbouring words of shared
-// memory; the row's y cell and taps are copied to place q (q_ly, q_wy) for
-// the forward twin.  Slot k of fine row r then holds (q, tap weight) in
-// ell[k * ny + r]; slots past the row's count stay (0, 0).  cell_cursor and
-// row_cursor (arrivals per fine y cell and per fine row): zeroed.
+// rank_row[q] = p: the x pass puts row p at place q of F; the row's y cell
+// and taps are copied to place q (q_ly, q_wy) for the forward twin.
+//
+// Row p reaches the fine rows c - h + 1 .. c + h (h = w / 2, modulo ny), so
+// fine row r receives the rows whose cell lies in the cyclic window
+// [r - h, r + h - 1]: in fine-y order a run of consecutive places (modulo P)
+// starting at first[r] = ly_first[(r - h) mod ny] (an empty cell's ly_first is
+// the next row's place; P stands for 0).  The table therefore stores first[r]
+// and the weight of each place of the run by its slot k = q - first[r]
+// (modulo P): slots 0-3 in the float4 w[r], slots 4-7 in w[ny + r]; slots
+// past the row's count stay 0.  A gather reads F at first[r] + k, so the
+// reader keeps copies of the first 8 places after the last.  cell_cursor
+// (arrivals per fine y cell): zeroed.
 static __global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny, int w, const int* __restrict__ row_ly,
                            const float* __restrict__ row_wy, const int* __restrict__ ly_first,
                            int* __restrict__ rank_row, int* __restrict__ q_ly, float4* __restrict__ q_wy,
-                           int* __restrict__ cell_cursor, int* __restrict__ row_cursor, int2* __restrict__ ell) {
+                           int* __restrict__ cell_cursor, int* __restrict__ first, float* __restrict__ wt) {
     const int P = min(*runs, cap);
     const int h = w / 2;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < ny; r += stride) first[r] = ly_first[wrapmod(r - h, ny)];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
         const int ly = row_ly[p];
         const int c = wrapmod(ly, ny);
         const int q = ly_first[c] + atomicAdd(&cell_cursor[c], 1);
@@ -506,15 +515,12 @@ static __global__ void k_ell_fill(const int* __restrict__ runs, int cap, int ny,
         q_ly[q] = ly;
         q_wy[2 * q] = reinterpret_cast<const float4*>(row_wy)[2 * p];
         q_wy[2 * q + 1] = reinterpret_cast<const float4*>(row_wy)[2 * p + 1];
-        int k[8];                                      // w <= 8: the slot claims overlap
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-            if (t < w) k[t] = atomicAdd(&row_cursor[wrapmod(ly - (h - 1) + t, ny)], 1);
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-            if (t < w && k[t] < kEllMax)
-                ell[(size_t)k[t] * ny + wrapmod(ly - (h - 1) + t, ny)] =
-                    make_int2(q, __float_as_int(row_wy[(size_t)p * 8 + t]));
+        for (int t = 0; t < w; ++t) {
+            const int r = wrapmod(c - (h - 1) + t, ny);
+            int k = q - ly_first[wrapmod(r - h, ny)];
+            if (k < 0) k += P;
+            if (k < kEllMax) wt[((size_t)(k >> 2) * ny + r) * 4 + (k & 3)] = row_wy[(size_t)p * 8 + t];
+        }
     }
 }
 

@@ -152,14 +152,6 @@ struct StagedSamples {
     __device__ __forceinline__ float2 val(int i) const { return to_f2(s_val[spread_pad(i - t0)]); }
 };
 
-// cp.async of one element (4, 8 or 16 bytes) from global into shared memory.
-template <int BYTES>
-__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 // Adjoint, step 1: R_p[c] = sum_{n in row p} D_n v_n phi(c - u_n) over the W
 // taps of each sample.  Each tile of kSpreadTile samples is staged in shared
 // memory by asynchronous copies (coalesced, every load in flight at once);

@@ -30,7 +30,8 @@ cudaError_t attrs_for() {
     if (e == cudaSuccess) e = smem_attr(k_fwd_rows<LOGN, false>, b);
     if (e == cudaSuccess) e = smem_attr(k_adj_rows_pulse<LOGN>, b);
     if (e == cudaSuccess) e = smem_attr(k_fwd_rows_pulse<LOGN>, b);
-    if (e == cudaSuccess) e = smem_attr(k_adj_cols_pulse<LOGN>, line_smem_pulse_cols<LOGN>());
+    if (e == cudaSuccess) e = smem_attr(k_adj_cols_pulse<LOGN, 1>, line_smem_pulse_cols<LOGN>());
+    if (e == cudaSuccess) e = smem_attr(k_adj_cols_pulse<LOGN, 2>, line_smem_pulse_cols<LOGN>());
     if (e == cudaSuccess) e = smem_attr(k_fwd_cols_pulse<LOGN>, line_smem_pulse_cols<LOGN>());
     if (e == cudaSuccess) e = smem_attr(k_fft_rows<LOGN, -1>, b);
     if (e == cudaSuccess) e = smem_attr(k_fft_rows<LOGN, +1>, b);
@@ -110,11 +111,18 @@ void launch_adj_rows_pulse(int lognx, int P, cudaStream_t s, const RowsView& rv,
 }
 
 void launch_adj_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float2* F, FftTables tab,
-                           const int2* ell, int K, const float* deap_y, float2* img) {
-#define L(LG) k_adj_cols_pulse<LG><<<Mx, Line<LG>::T, line_smem_pulse_cols<LG>(), s>>>(F, P, Mx, tab, ell, K, \
-                                                                                      deap_y, img)
-    TFFR_LOGN_SWITCH(logny, L)
+                           const int* ell_first, const float4* ell_w, int K, const float* deap_y, float2* img) {
+    if (K <= 4) {
+#define L(LG) k_adj_cols_pulse<LG, 1><<<Mx, Line<LG>::T, line_smem_pulse_cols<LG>(), s>>>(F, P, Mx, tab, ell_first, \
+                                                                                         ell_w, deap_y, img)
+        TFFR_LOGN_SWITCH(logny, L)
 #undef L
+    } else {
+#define L(LG) k_adj_cols_pulse<LG, 2><<<Mx, Line<LG>::T, line_smem_pulse_cols<LG>(), s>>>(F, P, Mx, tab, ell_first, \
+                                                                                         ell_w, deap_y, img)
+        TFFR_LOGN_SWITCH(logny, L)
+#undef L
+    }
 }
 
 void launch_fwd_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float2* img, FftTables tab,

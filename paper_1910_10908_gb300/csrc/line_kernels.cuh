@@ -489,10 +489,32 @@ struct ClusterWait {
     __device__ __forceinline__ void operator()() const { cluster_wait(); }
 };
 
-template <int LOGN>
+// Places after the last of an F column that keep copies of the first ones, so
+// that a fine row's run of places (modulo P) is read without a wrap test.
+constexpr int kPlaceCopies = 8;
+
+// Azimuth taps of fine row r: sum over slots k < 4 K4 of ell_w[k / 4][r].k
+// times fcol[ell_first[r] + k] (slots past the row's count weigh 0).
+template <int K4>
+__device__ __forceinline__ float2 gather_taps(const float2* fcol, int q, const float4 (&wt)[K4]) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < K4; ++h) {
+        const float g[4] = {wt[h].x, wt[h].y, wt[h].z, wt[h].w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 f = fcol[q + 4 * h + k];
+            acc.x = fmaf(g[k], f.x, acc.x);
+            acc.y = fmaf(g[k], f.y, acc.y);
+        }
+    }
+    return acc;
+}
+
+template <int LOGN, int K4>
 __global__ void __cluster_dims__(kColCluster, 1, 1) __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
-k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, const int2* __restrict__ ell, int K,
-                 const float* __restrict__ deap_y, float2* __restrict__ img) {
+k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, const int* __restrict__ ell_first,
+                 const float4* __restrict__ ell_w, const float* __restrict__ deap_y, float2* __restrict__ img) {
     using L = Line<LOGN>;
     constexpr int NY = L::N, MY = NY / 2, V = L::V;
     constexpr int OROWS = MY / kColCluster;            // image rows each CTA of the cluster writes
@@ -529,35 +551,36 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
 #pragma unroll
         for (int u = 0; u < V; ++u) {
             const int i = base + tid + u * L::T;
-            if (i < nel) peer_f[p0 + i / kColCluster] = tmp[u];
+            if (i < nel) {
+                const int q = p0 + i / kColCluster;
+                peer_f[q] = tmp[u];
+                // copies after the last place: P + j holds place j mod P
+                for (int j = q; j < kPlaceCopies; j += P) peer_f[P + j] = tmp[u];
+            }
         }
     }
     if (nel == 0) cluster_wait();                      // (A)
     cluster_arrive_release();                          // (B)
     cluster_wait();
-    // azimuth taps, gathered: fine row r = sum over its table slots k < K of
-    // weight_k fcol[q_k] (K: the most pulse rows any fine row receives; q_k
-    // the tap's place in fine-y order, so that a warp's lanes read
-    // neighbouring words of fcol), straight into the registers of the first
-    // FFT stage (row tid + u T)
+    // azimuth taps, gathered: fine row r sums its run of places in fine-y
+    // order (first place ell_first[r], one weight per slot; a warp's lanes
+    // read neighbouring words of fcol), straight into the registers of the
+    // first FFT stage (row tid + u T)
     float2 v[V];
-#pragma unroll
-    for (int u = 0; u < V; ++u) v[u] = make_float2(0.f, 0.f);
     constexpr int UB = V >= 8 ? 8 : V;
 #pragma unroll
     for (int u0 = 0; u0 < V; u0 += UB) {
-        for (int k = 0; k < K; ++k) {
-            int2 e[UB];
+        int q[UB];
+        float4 wt[UB][K4];
 #pragma unroll
-            for (int j = 0; j < UB; ++j) e[j] = __ldg(&ell[(size_t)k * NY + tid + (u0 + j) * L::T]);
+        for (int j = 0; j < UB; ++j) {
+            const int r = tid + (u0 + j) * L::T;
+            q[j] = __ldg(&ell_first[r]);
 #pragma unroll
-            for (int j = 0; j < UB; ++j) {
-                const float2 f = fcol[e[j].x];
-                const float g = __int_as_float(e[j].y);
-                v[u0 + j].x = fmaf(g, f.x, v[u0 + j].x);
-                v[u0 + j].y = fmaf(g, f.y, v[u0 + j].y);
-            }
+            for (int h = 0; h < K4; ++h) wt[j][h] = __ldg(&ell_w[h * NY + r]);
         }
+#pragma unroll
+        for (int j = 0; j < UB; ++j) v[u0 + j] = gather_taps<K4>(fcol, q[j], wt[j]);
     }
     cluster_arrive_release();                          // (C): this CTA's fcol reads are done
     ColPush<LOGN> epi{deap_y,

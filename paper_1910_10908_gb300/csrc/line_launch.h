@@ -33,9 +33,11 @@ void launch_fwd_rows(int lognx, int ny, bool rows, cudaStream_t s, const RowsVie
 // cell, q_wy: [P][8] azimuth taps), its x pass reads it.
 void launch_adj_rows_pulse(int lognx, int P, cudaStream_t s, const RowsView& rv, const float2* R, FftTables tab,
                            const float* deap_x, float2* F);
-// ell: [K][2 My] azimuth-tap table of the fine rows (place q in F's columns, weight).
+// Azimuth taps of the fine rows: fine row r sums weight k of ell_w (slots 0-3
+// in ell_w[r], 4-7 in ell_w[2 My + r]) times the place ell_first[r] + k of F's
+// column, k < K (places taken modulo P).
 void launch_adj_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float2* F, FftTables tab,
-                           const int2* ell, int K, const float* deap_y, float2* img);
+                           const int* ell_first, const float4* ell_w, int K, const float* deap_y, float2* img);
 void launch_fwd_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float2* img, FftTables tab,
                            const float* deap_y, const float* deap_x, const int* q_ly, const float* q_wy, int w,
                            float2* F);

@@ -87,7 +87,8 @@ struct tffr_plan_s {
     int row_cap = 0;                       // capacity of the per-row arrays
     bool pulse_order = false;              // FFT passes in pulse-row order (F in T's memory)
     DevBuf<float> row_wy;                  // [cap][8] azimuth taps of each pulse row
-    DevBuf<int2> ell;                      // [kEllMax][ny] fine-row tap table (pulse-row order)
+    DevBuf<int> ell_first;                 // [ny] first place in fine-y order of each fine row's taps
+    DevBuf<float4> ell_w;                  // [2][ny] tap weights of slots 0-3 and 4-7 (pulse-row order)
     int ell_k = 0;                         // slots in use: the most pulse rows a fine row receives
     DevBuf<int> row_start, row_end, row_clo, row_len, row_ly, row_min, row_max, bucket_start;
     DevBuf<float> row_fy;
@@ -542,11 +543,13 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     // fine-row order).
     CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 10 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaEventRecord(p->readback, p->stream));
-    CK(grow(p, p->ell, (int64_t)kEllMax * ny));
-    CK(cudaMemsetAsync(p->ell.ptr, 0, (size_t)kEllMax * ny * sizeof(int2), p->stream));
+    CK(grow(p, p->ell_first, ny));
+    CK(grow(p, p->ell_w, (int64_t)(kEllMax / 4) * ny));
+    CK(cudaMemsetAsync(p->ell_w.ptr, 0, (size_t)(kEllMax / 4) * ny * sizeof(float4), p->stream));
     k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, ly_first,
                                             p->rank_row.ptr, p->q_ly.ptr, reinterpret_cast<float4*>(p->q_wy.ptr),
-                                            ly_first + ny, p->cursor.ptr, p->ell.ptr);
+                                            ly_first + ny, p->ell_first.ptr,
+                                            reinterpret_cast<float*>(p->ell_w.ptr));
     CK_LAUNCH("k_ell_fill");
     CK(cudaEventSynchronize(p->readback));
     int hs[5];
@@ -663,7 +666,7 @@ int adjoint_impl(tffr_plan_s* p, const void* values, float2* image, bool weighte
             CK_LAUNCH("k_adj_rows_pulse");
             STAGE_END(TFFR_STAGE_ROW_FFT);
             STAGE_BEGIN(TFFR_STAGE_COL_FFT);
-            launch_adj_cols_pulse(p->logny, p->Mx, p->P, p->stream, p->T.ptr, tables_y(p), p->ell.ptr, p->ell_k,
+            launch_adj_cols_pulse(p->logny, p->Mx, p->P, p->stream, p->T.ptr, tables_y(p), p->ell_first.ptr, p->ell_w.ptr, p->ell_k,
                                   p->deap_y.ptr, image);
             CK_LAUNCH("k_adj_cols_pulse");
             STAGE_END(TFFR_STAGE_COL_FFT);
@@ -954,7 +957,8 @@ int tffr_destroy(tffr_plan_t p) {
     if (p->readback) cudaEventDestroy(p->readback);
     release(p->row_start); release(p->row_clo); release(p->row_len); release(p->row_ly);
     release(p->row_min); release(p->row_max); release(p->row_end); release(p->row_wy);
-    release(p->ell);
+    release(p->ell_first);
+    release(p->ell_w);
     release(p->bucket_start); release(p->row_fy); release(p->row_lam_y); release(p->row_off); release(p->R);
     release(p->tap_start); release(p->tap_list); release(p->rank_row); release(p->q_ly); release(p->q_wy);
     release(p->lx); release(p->ly); release(p->perm); release(p->slx); release(p->cursor);
@@ -1573,7 +1577,8 @@ BatchPatch patch_desc(const tffr_plan_s* p, const void* values, void* image) {
     d.row_fy = p->row_fy.ptr;
     d.row_lam_y = p->row_lam_y.ptr;
     d.rank_row = p->rank_row.ptr;
-    d.ell = p->ell.ptr;
+    d.ell_first = p->ell_first.ptr;
+    d.ell_w = p->ell_w.ptr;
     d.deap_x = p->deap_x.ptr;
     d.deap_y = p->deap_y.ptr;
     d.F = p->T.ptr;
