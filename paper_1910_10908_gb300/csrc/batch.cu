@@ -66,9 +66,9 @@ k_batch_spread(BatchSpreadArgs a) {
     float2* s_row = s_val + kSpreadStageElems;
     constexpr int H = W / 2;
     const int tid = threadIdx.x;
-    const int k = find_patch(a.row_first, a.npatch, blockIdx.x);
+    const int tag = __ldg(&a.row_tag[blockIdx.x]);         // also the deferred list's row field
+    const int k = tag >> 16, p = tag & 0xffff;
     const BatchPatch* __restrict__ bp = a.patches + k;
-    const int p = blockIdx.x - __ldg(&a.row_first[k]);
     const int M = __ldg(&bp->M), n = __ldg(&bp->n);
     const int len = __ldg(&bp->row_len[p]), clo = __ldg(&bp->row_clo[p]);
     const bool periodic = (len == n) && (clo == 0);
@@ -78,7 +78,6 @@ k_batch_spread(BatchSpreadArgs a) {
     for (int i = tid; i < len; i += kSpreadThreads) s_row[i] = make_float2(0.f, 0.f);
     float dy = 1.0f;
     bool dy_exact = false, edges = true;
-    const double lam_y_row = __ldg(&bp->row_lam_y[p]);
     if (wa.mode == 0) {
         if (wa.separable) {
             const float gy = g_fitted(__ldg(&bp->row_ly[p]), __ldg(&bp->row_fy[p]), M, wa, dy_exact);
@@ -91,7 +90,6 @@ k_batch_spread(BatchSpreadArgs a) {
     const double* __restrict__ g_lam = bp->lam_x + s0;
     const float2* __restrict__ g_val = bp->values + s0;
     const float* user_D = bp->user_D;
-    const int tag = (k << 16) | p;                         // the deferred list's row field: patch and row
     for (int t0 = 0; t0 < L; t0 += kSpreadTile) {
         const int cnt = min(kSpreadTile, L - t0);
         __syncthreads();                                   // row zeroed / previous tile consumed
@@ -144,14 +142,16 @@ k_batch_spread_deferred(BatchSpreadArgs a) {
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         const int2 e = defer.item[i];
-        const int n = e.x, k = e.y >> 16, p = e.y & 0xffff;
+        const int n = e.x, k = (e.y >> 16) & 0x7fff, p = e.y & 0xffff;
         const BatchPatch* __restrict__ bp = a.patches + k;
         const int M = bp->M, nx = bp->n;
         const double lam = bp->lam_x[n];
         int cell;
         float f;
         fine_coord(lam, cell, f);
-        const float d = weight_exact(lam, bp->row_lam_y[p], M, M, a.wa);
+        const float d = (e.y & kDeferCoordOnly)
+                            ? weight_tffr(lam, cell, f, bp->row_lam_y[p], bp->row_ly[p], bp->row_fy[p], M, M, a.wa)
+                            : weight_exact(lam, bp->row_lam_y[p], M, M, a.wa);
         if (d == 0.0f) continue;
         const float2 v = cscale(bp->values[n], d);
         float wt[W];

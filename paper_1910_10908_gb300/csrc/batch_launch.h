@@ -48,7 +48,7 @@ struct BatchPatch {
 // The spread launch over every pulse row of every patch.
 struct BatchSpreadArgs {
     const BatchPatch* patches;          // [npatch] every patch of the batch (npatch < 2^15, rows < 2^16)
-    const int* row_first;               // [npatch + 1] first block (pulse row) of each patch
+    const int* row_tag;                 // [blocks] (patch << 16) | pulse row of each block
     int npatch;
     WeightArgs wa;                      // the batch's weight evaluation (the patch's M decides the edges)
     TapPoly tp;

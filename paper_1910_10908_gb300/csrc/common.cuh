@@ -109,6 +109,72 @@ static __device__ __noinline__ FineCoord fine_coord_general(double v) {
     return FineCoord{cell, frac, true};
 }
 
+// floor(2v) and the fraction 2v - floor(2v) as a 32-bit fixed-point number
+// (the fraction's leading 32 bits, truncated), without branches: the fast
+// form covers 2^-11 <= |2v| < 2^21 with 32-bit integer operations and returns
+// false for other magnitudes (cell and F are then meaningless), which
+// fixed_coord_general covers (and returns false for a non-finite v or
+// |v| >= 2^28).
+static __device__ __noinline__ bool fixed_coord_general(double v, int& cell, unsigned& F);
+
+__device__ __forceinline__ bool fixed_coord_fast(double v, int& cell, unsigned& F) {
+    const int hi = __double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const int sft = 1042 - ((hi >> 20) & 0x7ff);      // |2v| = (mh 2^32 + lo) 2^-(32 + sft)
+    const unsigned mh = ((unsigned)hi & 0xFFFFFu) | 0x100000u;
+    const unsigned I = mh >> (sft & 31);
+    const unsigned Fp = __funnelshift_r(lo, mh, (unsigned)sft);
+    // negative v: 1 - fraction, the bits below the 32 kept ones borrowing one unit
+    const unsigned tail = __funnelshift_lc(0u, lo, (unsigned)(32 - sft));
+    const bool neg = hi < 0;
+    cell = neg ? ((Fp | tail) ? ~(int)I : -(int)I) : (int)I;
+    F = neg ? (tail ? ~Fp : 0u - Fp) : Fp;
+    return (unsigned)sft <= 31u;
+}
+
+static __device__ __noinline__ bool fixed_coord_general(double v, int& cell, unsigned& F) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    cell = 0;
+    F = 0u;
+    if (e > 1050) return false;                        // |v| >= 2^28 (also inf, NaN)
+    if (e == 0) return true;                           // zero or subnormal
+    const bool neg = (b >> 63) != 0ull;
+    const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int sh = 1074 - e;                           // |2v| = m 2^-sh, sh >= 24
+    unsigned long long I, X;                           // integer part; fraction, sh bits (sh < 64)
+    if (sh < 64) {
+        I = m >> sh;
+        X = m & ((1ull << sh) - 1ull);
+    } else {
+        I = 0ull;
+        X = m;
+    }
+    if (neg && X != 0ull) {
+        cell = -(int)I - 1;
+        if (sh < 64) {
+            X = (1ull << sh) - X;
+        } else {
+            // 1 - m 2^-sh, leading 32 bits: the complement of m's leading
+            // bits, borrowing one unit when bits below them are set
+            const int r = sh - 32;
+            const unsigned long long top = (r < 64) ? (m >> r) : 0ull;
+            const bool below = (r >= 64) || ((m & ((1ull << r) - 1ull)) != 0ull);
+            F = below ? ~(unsigned)top : 0u - (unsigned)top;
+            return true;
+        }
+    } else {
+        cell = neg ? -(int)I : (int)I;
+        if (sh >= 64) {
+            const int r = sh - 32;
+            F = (r < 64) ? (unsigned)(m >> r) : 0u;
+            return true;
+        }
+    }
+    F = (sh >= 32) ? (unsigned)(X >> (sh - 32)) : (unsigned)(X << (32 - sh));
+    return true;
+}
+
 // Spreading-kernel taps as polynomials in t = 2f - 1 (f the fine-cell offset
 // in [0, 1]): tap s (fine cell floor(u) - (w/2 - 1) + s) has weight
 // P_s(t) = sum_k c[s][k] t^k, fitted at plan time in FP64 to the ES kernel
@@ -132,10 +198,9 @@ __device__ __forceinline__ float tap_eval(const TapPoly& P, int s, float t) {
 
 // All W taps; mirrored pairs share the even and odd parts in t^2.
 template <int W>
-__device__ __forceinline__ void taps_all(const TapPoly& P, float f, float (&wt)[W]) {
+__device__ __forceinline__ void taps_all_t(const TapPoly& P, float t, float (&wt)[W]) {
     constexpr int NC = tap_coefs(W);
     constexpr int TOP_E = (NC - 1) & ~1, TOP_O = ((NC - 2) | 1);        // highest even / odd power
-    const float t = 2.0f * f - 1.0f;
     const float t2 = t * t;
 #pragma unroll
     for (int s = 0; s < W / 2; ++s) {
@@ -148,6 +213,11 @@ __device__ __forceinline__ void taps_all(const TapPoly& P, float f, float (&wt)[
         wt[s] = fmaf(t, o, e);
         wt[W - 1 - s] = fmaf(-t, o, e);
     }
+}
+
+template <int W>
+__device__ __forceinline__ void taps_all(const TapPoly& P, float f, float (&wt)[W]) {
+    taps_all_t<W>(P, 2.0f * f - 1.0f, wt);
 }
 
 // Exponential-of-semicircle spreading kernel of width w (fine-grid cells):

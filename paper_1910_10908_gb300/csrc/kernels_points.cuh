@@ -133,6 +133,22 @@ __device__ __forceinline__ float d_fitted(int cell, float f, const WeightArgs& A
     return (G != 0.0f) ? __frcp_rn(G) : 0.0f;
 }
 
+// d_fitted's piece 0 from the fine cell and the fixed-point offset F
+// (fixed_coord_fast): lam - floor(lam) is the 0.32 fixed-point number
+// (cell & 1, F) >> 1.  No branch: a sample outside piece 0 (v >= vb, which
+// includes the truncation breakpoints) sets exact, and its value is not used.
+__device__ __forceinline__ float d_fixed0(int cell, unsigned F, const WeightArgs& A, bool& exact) {
+    const unsigned D = __funnelshift_r(F, (unsigned)cell, 1);
+    const float v = fabsf(fmaf(__uint2float_rn(D), 0x1p-32f, -0.5f));   // |lam - floor(lam) - 1/2|
+    exact |= !(v < A.vb);
+    const float r = v * A.inv_vb;
+    const float s = fmaf(2.0f * r, r, -1.0f);
+    float d = A.d0[kD0Coefs - 1];
+#pragma unroll
+    for (int k = kD0Coefs - 2; k >= 0; --k) d = fmaf(d, s, A.d0[k]);
+    return d;
+}
+
 static __device__ __noinline__ float weight_exact_args(double lam_x, double lam_y, int Mx, int My, double a, double q,
                                                 double e_minus, double e_plus, int reach, double tau, int separable) {
     double G = diag_psi_w(lam_x, Mx, a, q, e_minus, e_plus, reach);

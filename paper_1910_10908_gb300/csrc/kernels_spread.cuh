@@ -22,10 +22,15 @@ constexpr int kSpreadTile = kSpreadThreads * kSpreadRun;
 // tau, a grid edge or a truncation breakpoint; rare) are not spread inline:
 // k_spread_rows lists them and k_spread_deferred adds them afterwards.  The
 // FP64 closed form then stays out of the hot kernel (and its registers).
+// Flag in a deferred item's row field: the sample lacks only the fast
+// coordinate split; its weight is the fitted one unless that needs the FP64
+// decision too.
+constexpr int kDeferCoordOnly = (int)0x80000000u;
+
 struct DeferList {
     int* count;                     // [0] listed samples, [1] finished blocks of k_spread_deferred;
                                     // both zero before the spread, and left zero by k_spread_deferred
-    int2* item;                     // [cap] (sample, pulse row)
+    int2* item;                     // [cap] (sample, pulse row | kDeferCoordOnly flag)
     int cap;                        // N: every sample is listed at most once per adjoint
 };
 
@@ -36,19 +41,19 @@ struct DeferList {
 // adds tap s into cell s + dlt (a select, no branch); a sample further right
 // flushes the window into the shared row and starts a new one (rare).  D_n:
 // MODE 0 the tFFR weight (the direct FP32 fit of 1/G times the row's azimuth
-// factor, deferred to the FP64 kernel near tau, on a truncation breakpoint or,
-// for rows not inside the grid's interior, near a grid edge), 1 unit, 2 the
-// caller's array.
-// INLINE: samples that need the FP64 decision take it here (weight_exact with
-// the row's lam_y and the grid sizes Mx, My) instead of being deferred.
+// factor), 1 unit, 2 the caller's array.  In MODE 0 a sample whose weight
+// needs the FP64 decision (near tau, off the fit's first piece or on a
+// truncation breakpoint, near a grid edge for rows not inside the grid's
+// interior, or with |2 lam| outside the fast coordinate split) is listed for
+// k_spread_deferred and adds nothing here.  The per-sample path has two
+// branches, both rarely taken: the listing and the window flush.
 // Sample i of the run comes from src.lam(i), src.val(i) (the caller's arrays
 // or a staged copy in shared memory); n0 + i is its index in the caller's order.
-template <typename VT, int W, int MODE, bool INLINE = false, typename Src>
+template <typename VT, int W, int MODE, typename Src>
 __device__ __forceinline__ void spread_run(int64_t n0, int i0, int i1, int p, int nx, int clo, int len, bool periodic,
                                            int Mx, bool edges, float dy, bool dy_exact, const Src& src,
                                            const WeightArgs& wa, const TapPoly& tp, const DeferList& defer,
-                                           float2* s_row, const float* __restrict__ user_D,
-                                           double lam_y_row = 0.0, int My = 0) {
+                                           float2* s_row, const float* __restrict__ user_D) {
     constexpr int H = W / 2;
     constexpr int kNoBase = -(1 << 30);                // below every cell (|cell| < 2^29), no overflow
     float2 acc[W + 1];
@@ -66,42 +71,51 @@ __device__ __forceinline__ void spread_run(int64_t n0, int i0, int i1, int p, in
             acc[s] = make_float2(0.f, 0.f);
         }
     };
+    // grid-edge test as one unsigned compare: image cell j0 = floor(lam) needs
+    // the FP64 decision unless e_lo <= j0 < e_lo + e_span (rows inside the
+    // interior: never)
+    int e_lo = -(1 << 30);
+    unsigned e_span = 1u << 31;
+    if (MODE == 0 && edges) {
+        e_lo = wa.reach - Mx / 2;
+        e_span = (unsigned)max(0, (Mx - Mx / 2 - wa.reach) - e_lo);
+    }
+    const float tau_band = wa.guard * fabsf(wa.tau);
+    int prev = clo + (H - 1);                          // a cell whose taps lie in the row
     for (int i = i0; i < i1; ++i) {
         const int64_t n = n0 + i;
         const double lam = src.lam(i);
         const float2 v0 = src.val(i);
         int cell;
-        float f;
-        fine_coord(lam, cell, f);
+        unsigned F;
+        const bool fast = fixed_coord_fast(lam, cell, F);
         float d;
-        if constexpr (MODE == 1) {
-            d = 1.0f;
-        } else if constexpr (MODE == 2) {
-            d = __ldg(&user_D[n]);
-        } else {
-            bool exact = dy_exact;
-            if (edges) {
-                const int j0 = cell >> 1;
-                exact |= (j0 - wa.reach < -(Mx / 2)) | (j0 + wa.reach >= Mx - Mx / 2);
-            }
-            d = d_fitted(cell, f, wa, exact) * dy;
-            if (exact | !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau))) {
-                if constexpr (INLINE) {
-                    d = weight_exact(lam, lam_y_row, Mx, My, wa);
-                } else {
-                    const int slot = atomicAdd(defer.count, 1);
-                    if (slot < defer.cap) defer.item[slot] = make_int2((int)n, p);
-                    d = 0.0f;
-                }
+        if constexpr (MODE == 0) {
+            // a sample without the fast split is deferred: it keeps the previous
+            // cell (its window stays put) and adds nothing here
+            cell = fast ? cell : prev;
+            bool exact = dy_exact | ((unsigned)((cell >> 1) - e_lo) >= e_span);
+            d = d_fixed0(cell, F, wa, exact) * dy;
+            if (!fast | exact | !(fabsf(d - wa.tau) > tau_band)) {
+                // listed with bit 31 of the row field set when only the
+                // coordinate split is missing (the fitted weight then decides)
+                const int slot = atomicAdd(defer.count, 1);
+                if (slot < defer.cap) defer.item[slot] = make_int2((int)n, fast ? p : (p | kDeferCoordOnly));
+                d = 0.0f;
             }
             d = (d >= wa.tau) ? d : 0.0f;
+        } else {
+            if (!fast) fixed_coord_general(lam, cell, F);
+            d = (MODE == 1) ? 1.0f : __ldg(&user_D[n]);
         }
+        prev = cell;
+        const float t = fmaf(__uint2float_rn(F), 0x1p-31f, -1.0f);   // 2 f - 1
         const float2 v = cscale(v0, d);
         float wt[W];
-        taps_all<W>(tp, f, wt);
+        taps_all_t<W>(tp, t, wt);
         const int c0 = cell - (H - 1);
         int dlt = c0 - base;
-        if (dlt < 0 || dlt > 1) {                      // first sample of the run, or a jump: new window
+        if ((unsigned)dlt > 1u) {                      // first sample of the run, or a jump: new window
             if (base != kNoBase) flush();
             base = c0;
             dlt = 0;
@@ -246,12 +260,14 @@ k_spread_deferred(RowsView rv, int nx, int Mx, int My, const double* __restrict_
     }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         const int2 e = defer.item[i];
-        const int n = e.x, p = e.y;
+        const int n = e.x, p = e.y & ~kDeferCoordOnly;
         const double lam = lam_x[n];
         int cell;
         float f;
         fine_coord(lam, cell, f);
-        const float d = weight_exact(lam, rv.row_lam_y[p], Mx, My, wa);
+        const float d = (e.y & kDeferCoordOnly)
+                            ? weight_tffr(lam, cell, f, rv.row_lam_y[p], rv.row_ly[p], rv.row_fy[p], Mx, My, wa)
+                            : weight_exact(lam, rv.row_lam_y[p], Mx, My, wa);
         if (d == 0.0f) continue;
         const float2 v = cscale(ValueIO<VT>::load(values, n), d);
         float wt[W];

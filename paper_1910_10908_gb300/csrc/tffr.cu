@@ -1485,7 +1485,7 @@ struct tffr_batch_s {
     cudaStream_t stream = nullptr;
     std::vector<BatchClass> cls;
     BatchPatch* d_patches = nullptr;                   // every patch (the spread launch)
-    int* d_row_first = nullptr;                        // [n + 1] first pulse row of each patch
+    int* d_row_tag = nullptr;                          // [rows_total] (patch << 16) | pulse row of each spread block
     int rows_total = 0, max_len = 0, w = 6;
     WeightArgs wa;
     TapPoly tp;
@@ -1510,7 +1510,7 @@ void batch_free(tffr_batch_s* b) {
         if (c.d_counts) cudaFree(c.d_counts);
     }
     if (b->d_patches) cudaFree(b->d_patches);
-    if (b->d_row_first) cudaFree(b->d_row_first);
+    if (b->d_row_tag) cudaFree(b->d_row_tag);
     if (b->d_defer_count) cudaFree(b->d_defer_count);
     if (b->d_defer) cudaFree(b->d_defer);
     if (b->d_err) cudaFree(b->d_err);
@@ -1541,7 +1541,7 @@ BatchClassArgs class_args(const tffr_batch_s* b, const BatchClass& c) {
 cudaError_t launch_spread(const tffr_batch_s* b) {
     BatchSpreadArgs a;
     a.patches = b->d_patches;
-    a.row_first = b->d_row_first;
+    a.row_tag = b->d_row_tag;
     a.npatch = b->n;
     a.wa = b->wa;
     a.tp = b->tp;
@@ -1650,10 +1650,14 @@ int tffr_batch_create(const tffr_plan_t* plans, int n, const void* const* values
         c->members.push_back(i);
     }
     b->rows_total = row_first[n];
+    std::vector<int> row_tag(std::max(1, b->rows_total));
+    for (int i = 0; i < n; ++i)
+        for (int r = row_first[i]; r < row_first[i + 1]; ++r) row_tag[r] = (i << 16) | (r - row_first[i]);
     e = cudaMalloc((void**)&b->d_patches, n * sizeof(BatchPatch));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_row_first, (n + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_row_tag, row_tag.size() * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_patches, all.data(), n * sizeof(BatchPatch), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_row_first, row_first.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_row_tag, row_tag.data(), row_tag.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return bail(e);
     for (BatchClass& c : b->cls) {
         const int m = (int)c.members.size();
