@@ -135,16 +135,6 @@ __device__ __forceinline__ void spread_run(int64_t n0, int i0, int i1, int p, in
     if (base != kNoBase) flush();
 }
 
-// Samples read straight from the caller's arrays (index relative to n0).
-template <typename VT>
-struct GlobalSamples {
-    const double* lam_x;
-    const void* values;
-    int64_t n0;
-    __device__ __forceinline__ double lam(int i) const { return __ldg(&lam_x[n0 + i]); }
-    __device__ __forceinline__ float2 val(int i) const { return ValueIO<VT>::load(values, n0 + i); }
-};
-
 // A staged value (the caller's bytes in shared memory) as FP32 complex.
 __device__ __forceinline__ float2 to_f2(const float2& v) { return v; }
 __device__ __forceinline__ float2 to_f2(const double2& v) { return make_float2((float)v.x, (float)v.y); }

@@ -534,32 +534,46 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
     cluster_arrive_relaxed();                          // (A)
     const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
     // The cluster's block of four columns of F is one contiguous run; CTA rank
-    // reads the quarter of places [p0, p0 + PQ) and sends entry i of it
-    // (place p0 + i / 4, column i % 4 = tid % 4) to the fcol of CTA i % 4.
-    float2* const peer_f = cluster.map_shared_rank(fcol, tid % kColCluster);
+    // reads the quarter of places [p0, p0 + PQ), each place's 32-byte piece by
+    // one thread (two 16-byte loads), and sends column c of it to the fcol of
+    // CTA c: a warp's store then carries 32 neighbouring places to one CTA.
+    // Places 0 .. 7 also go to P .. P + 7 (modulo P), so that a fine row's run
+    // of places is read without a wrap test.
+    constexpr int KP = (V / 8) > 0 ? V / 8 : 1;        // places per thread: PQ <= N / 8 = KP T
     const int ldq = pulse_ldq(P), PQ = ldq / kColCluster;
-    const int p0 = rank * PQ, nel = max(0, min(P, p0 + PQ) - p0) * kColCluster;
-    const float2* const Fq = F + ((size_t)(jx0 / kColCluster) * ldq + p0) * kColCluster;
-    for (int base = 0; base < nel; base += V * L::T) {
-        float2 tmp[V];
+    const int p0 = rank * PQ, nq = max(0, min(P, p0 + PQ) - p0);
+    const float4* const Fq = reinterpret_cast<const float4*>(F + ((size_t)(jx0 / kColCluster) * ldq + p0) * kColCluster);
+    float4 lo[KP], hi[KP];
 #pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const int i = base + tid + u * L::T;
-            tmp[u] = (i < nel) ? __ldg(&Fq[i]) : make_float2(0.f, 0.f);
+    for (int k = 0; k < KP; ++k) {
+        const int j = tid + k * L::T;
+        if (j < nq) {
+            lo[k] = __ldg(&Fq[2 * j]);
+            hi[k] = __ldg(&Fq[2 * j + 1]);
         }
-        if (base == 0) cluster_wait();                 // (A), behind the first loads
+    }
+    cluster_wait();                                    // (A), behind the loads
+    float2* const peer0 = cluster.map_shared_rank(fcol, 0);
+    float2* const peer1 = cluster.map_shared_rank(fcol, 1);
+    float2* const peer2 = cluster.map_shared_rank(fcol, 2);
+    float2* const peer3 = cluster.map_shared_rank(fcol, 3);
 #pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const int i = base + tid + u * L::T;
-            if (i < nel) {
-                const int q = p0 + i / kColCluster;
-                peer_f[q] = tmp[u];
-                // copies after the last place: P + j holds place j mod P
-                for (int j = q; j < kPlaceCopies; j += P) peer_f[P + j] = tmp[u];
+    for (int k = 0; k < KP; ++k) {
+        const int j = tid + k * L::T;
+        if (j < nq) {
+            const int q = p0 + j;
+            peer0[q] = make_float2(lo[k].x, lo[k].y);
+            peer1[q] = make_float2(lo[k].z, lo[k].w);
+            peer2[q] = make_float2(hi[k].x, hi[k].y);
+            peer3[q] = make_float2(hi[k].z, hi[k].w);
+            for (int r = q; r < kPlaceCopies; r += P) {
+                peer0[P + r] = make_float2(lo[k].x, lo[k].y);
+                peer1[P + r] = make_float2(lo[k].z, lo[k].w);
+                peer2[P + r] = make_float2(hi[k].x, hi[k].y);
+                peer3[P + r] = make_float2(hi[k].z, hi[k].w);
             }
         }
     }
-    if (nel == 0) cluster_wait();                      // (A)
     cluster_arrive_release();                          // (B)
     cluster_wait();
     // azimuth taps, gathered: fine row r sums its run of places in fine-y
