@@ -295,6 +295,10 @@ def run_gpu(args, world, rank, local):
     stream = plan.stream
 
     def step():
+        # set_points + weights + adjoint in one library call (tffr_reconstruct)
+        plan.reconstruct(lx, ly, vals, out=img)
+
+    def step_three_calls():
         plan.set_points(lx, ly)
         plan.weights(count=False)
         plan.adjoint(vals, out=img)
@@ -374,6 +378,7 @@ def run_gpu(args, world, rank, local):
     # ---- forward twin, timed on its own ----
     yout = torch.empty(N, dtype=torch.complex64, device=dev)
     fwd_ms, _ = timed_ms(lambda: plan.forward(img, out=yout), stream, world)
+    three_ms, _ = timed_ms(step_three_calls, stream, world)
 
     # ---- end to end through host buffers ----
     # Every step copies its inputs in from pinned host memory and its image out
@@ -398,9 +403,7 @@ def run_gpu(args, world, rank, local):
             d_lx.copy_(h_lx, non_blocking=True)
             d_ly.copy_(h_ly, non_blocking=True)
             d_v.copy_(h_v, non_blocking=True)
-        pl.set_points(d_lx, d_ly)
-        pl.weights(count=False)
-        pl.adjoint(d_v, out=d_img[k])
+        pl.reconstruct(d_lx, d_ly, d_v, out=d_img[k])
         with torch.cuda.stream(s):
             h_img[k].copy_(d_img[k], non_blocking=True)
 
@@ -530,9 +533,7 @@ def run_gpu(args, world, rank, local):
         img_v = torch.empty_like(img)
 
         def step_v():
-            plan_v.set_points(lx, ly)
-            plan_v.weights(count=False)
-            plan_v.adjoint(v_low, out=img_v)
+            plan_v.reconstruct(lx, ly, v_low, out=img_v)
 
         ms_v, _ = timed_ms(step_v, plan_v.stream, world)
         variants[vt] = {"value": whole_job_rate(N, world, ms_v), "unit": UNIT, "ms_per_step": ms_v,
@@ -559,7 +560,8 @@ def run_gpu(args, world, rank, local):
                        "freqs": wl.n_freq, "sigma": 2, "width": 6, "beta": info["beta"], "values": "c64",
                        "layout": "rows" if info["layout"] == 2 else "general", "pulse_rows": info["n_rows"],
                        "pass_order": "pulse_rows" if pulse else "fine_rows",
-                       "step": "set_points+weights+adjoint", "l2": "inputs (402 MB/step) larger than L2",
+                       "step": "set_points+weights+adjoint (one tffr_reconstruct call)",
+                       "l2": "inputs (402 MB/step) larger than L2",
                        "timed_regions": repeats,
                        "parallelism": "independent images per GPU" if world > 1 else "single GPU"},
             "roofline": roof,
@@ -568,6 +570,8 @@ def run_gpu(args, world, rank, local):
             "adjoint_only_samples_per_s": N / (sum(stages[k][0] / max(stages[k][1], 1)
                                                    for k in ("spread", "row_fft", "col_fft")) * 1e-3),
             "forward": {"value": N / (fwd_ms * 1e-3), "unit": UNIT, "ms": fwd_ms},
+            "step_as_three_calls": {"ms": three_ms, "value": N / (three_ms * 1e-3), "unit": UNIT,
+                                    "calls": "tffr_set_points, tffr_weights, tffr_adjoint"},
             "accuracy": {"rel_l2_vs_fp64_oracle_crop256": crop_rel_l2(img, ref, box),
                          "pixels": 0 if ref is None else int(ref.size),
                          "reference": "tests/golden/stripmap_4096_crop256.npy (FP64 direct sum, centre crop)"},
@@ -609,9 +613,7 @@ def run_step_only(args, local):
     with Plan(wl.M, values="c64", device=dev) as plan:
         img = torch.empty((wl.M, wl.M), dtype=torch.complex64, device=dev)
         for _ in range(args.warmup + args.steps):
-            plan.set_points(lx, ly)
-            plan.weights(count=False)
-            plan.adjoint(vals, out=img)
+            plan.reconstruct(lx, ly, vals, out=img)
         plan.forward(img)
         torch.cuda.synchronize()
     print(json.dumps({"step_only": True, "steps": args.warmup + args.steps, "N": wl.N}), flush=True)

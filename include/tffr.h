@@ -196,6 +196,19 @@ int tffr_weights(tffr_plan_t plan, const tffr_weight_opts* opts, float* D_out, i
 int tffr_adjoint(tffr_plan_t plan, const void* values, void* image);
 
 /*
+ * One whole reconstruction (Sec. II.B Eq. (fstraight) with the weights of
+ * Algorithm 1): tffr_set_points(plan, N, lam_x, lam_y), tffr_weights(plan,
+ * opts, NULL, NULL) and tffr_adjoint(plan, values, image) in one call, with
+ * the same arguments, ownership and results as those three.  The adjoint's
+ * first launch follows set_points' read-back with no return to the caller in
+ * between, so the device does not wait on the caller's own work there.
+ * Errors: those of the three calls, from the first that fails (the later ones
+ * are then not made).
+ */
+int tffr_reconstruct(tffr_plan_t plan, int64_t N, const double* lam_x, const double* lam_y,
+                     const tffr_weight_opts* opts, const void* values, void* image);
+
+/*
  * The forward twin: values[n] = (apply_weights ? D_n : 1) * sum_j image_j
  * exp(-2 pi i lam_n . x_j).  image: device complex64 [My][Mx].  values:
  * device, N samples (complex128 for the C128 value type, complex64 otherwise).

@@ -19,7 +19,7 @@ import torch
 from . import _abi
 from ._abi import VALUES, LAYOUTS, ORDERS, WEIGHT_MODES
 
-__all__ = ["TffrError", "Plan", "tffr_plan", "tffr_set_points", "tffr_weights", "tffr_adjoint",
+__all__ = ["TffrError", "Plan", "tffr_plan", "tffr_set_points", "tffr_weights", "tffr_adjoint", "tffr_reconstruct",
            "tffr_forward", "tffr_destroy", "tffr_plan_get_info", "tffr_profile", "tffr_profile_read",
            "tffr_weights_noalloc", "tffr_adjoint_unweighted", "tffr_weight_grad", "tffr_cg",
            "tffr_batch_create", "tffr_batch_adjoint", "tffr_batch_wait", "tffr_batch_tune",
@@ -93,10 +93,7 @@ def tffr_set_points(plan, lam_x: torch.Tensor, lam_y: torch.Tensor):
     _check(_abi.load().tffr_set_points(plan, N, px, py), plan)
 
 
-def tffr_weights(plan, *, mode: str = "tffr", separable: bool = False, a: float = 0.01, q: float = 3.0,
-                 tau: float = 0.97, user_D: torch.Tensor | None = None, D_out: torch.Tensor | None = None,
-                 count: bool = True):
-    lib = _abi.load()
+def _weight_opts(lib, mode: str, separable: bool, a: float, q: float, tau: float, user_D):
     o = _abi.tffr_weight_opts()
     lib.tffr_default_weight_opts(ctypes.byref(o))
     o.mode = WEIGHT_MODES[mode]
@@ -104,6 +101,14 @@ def tffr_weights(plan, *, mode: str = "tffr", separable: bool = False, a: float 
     o.a, o.q, o.tau = float(a), float(q), float(tau)
     if user_D is not None:
         o.user_D = _dev(user_D, "user_D", torch.float32).value
+    return o
+
+
+def tffr_weights(plan, *, mode: str = "tffr", separable: bool = False, a: float = 0.01, q: float = 3.0,
+                 tau: float = 0.97, user_D: torch.Tensor | None = None, D_out: torch.Tensor | None = None,
+                 count: bool = True):
+    lib = _abi.load()
+    o = _weight_opts(lib, mode, separable, a, q, tau, user_D)
     pd = _dev(D_out, "D_out", torch.float32) if D_out is not None and D_out.numel() else None
     kept = ctypes.c_int64(-1)
     _check(lib.tffr_weights(plan, ctypes.byref(o), pd, ctypes.byref(kept) if count else None), plan)
@@ -113,6 +118,25 @@ def tffr_weights(plan, *, mode: str = "tffr", separable: bool = False, a: float 
 def tffr_adjoint(plan, values: torch.Tensor, image: torch.Tensor):
     pv = _dev(values, "values") if values.numel() else None
     _check(_abi.load().tffr_adjoint(plan, pv, _dev(image, "image", torch.complex64)), plan)
+
+
+def tffr_reconstruct(plan, lam_x: torch.Tensor, lam_y: torch.Tensor, values: torch.Tensor, image: torch.Tensor, *,
+                     mode: str = "tffr", separable: bool = False, a: float = 0.01, q: float = 3.0,
+                     tau: float = 0.97, user_D: torch.Tensor | None = None):
+    """set_points + weights + adjoint in one library call (the coordinates are kept by pointer)."""
+    if lam_x.shape != lam_y.shape or lam_x.dim() != 1:
+        raise ValueError("lam_x and lam_y must be 1-D of equal length")
+    N = lam_x.shape[0]
+    if values.shape[0] != N:
+        raise ValueError("values must hold one sample per coordinate")
+    if user_D is not None and user_D.numel() < N:
+        raise ValueError("user_D shorter than the samples")
+    lib = _abi.load()
+    o = _weight_opts(lib, mode, separable, a, q, tau, user_D)
+    px = _dev(lam_x, "lam_x", torch.float64) if N else None
+    py = _dev(lam_y, "lam_y", torch.float64) if N else None
+    pv = _dev(values, "values") if values.numel() else None
+    _check(lib.tffr_reconstruct(plan, N, px, py, ctypes.byref(o), pv, _dev(image, "image", torch.complex64)), plan)
 
 
 def tffr_forward(plan, image: torch.Tensor, values: torch.Tensor, apply_weights: bool = True):
@@ -317,6 +341,20 @@ class Plan:
         if out is None:
             out = torch.empty((self.My, self.Mx), dtype=torch.complex64, device=self.device)
         tffr_adjoint(self._handle(), values, out)
+        return out
+
+    def reconstruct(self, lam_x: torch.Tensor, lam_y: torch.Tensor, values: torch.Tensor,
+                    out: torch.Tensor | None = None, **weight_opts) -> torch.Tensor:
+        """set_points, weights and adjoint in one library call; keep references to the coordinates."""
+        N = int(lam_x.shape[0])
+        if values.dtype not in _VALUE_DTYPES[self.values]:
+            raise TypeError("values dtype %s does not match the plan's %s" % (values.dtype, self.values))
+        if out is None:
+            out = torch.empty((self.My, self.Mx), dtype=torch.complex64, device=self.device)
+        self.N = None
+        tffr_reconstruct(self._handle(), lam_x, lam_y, values, out, **weight_opts)
+        self._coords = (lam_x, lam_y)
+        self.N = N
         return out
 
     def forward(self, image: torch.Tensor, out: torch.Tensor | None = None,

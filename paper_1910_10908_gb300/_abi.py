@@ -60,6 +60,8 @@ SIGNATURES = {
     "tffr_weights": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(tffr_weight_opts), ctypes.c_void_p,
                                     ctypes.POINTER(ctypes.c_int64)]),
     "tffr_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "tffr_reconstruct": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.POINTER(tffr_weight_opts), ctypes.c_void_p, ctypes.c_void_p]),
     "tffr_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "tffr_adjoint_unweighted": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "tffr_weight_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

@@ -1378,6 +1378,14 @@ int tffr_normal_apply(tffr_plan_t p, const void* image_in, void* image_out) {
     return TFFR_OK;
 }
 
+int tffr_reconstruct(tffr_plan_t p, int64_t N, const double* lam_x, const double* lam_y,
+                     const tffr_weight_opts* opts, const void* values, void* image) {
+    int st = tffr_set_points(p, N, lam_x, lam_y);
+    if (st == TFFR_OK) st = tffr_weights(p, opts, nullptr, nullptr);
+    if (st == TFFR_OK) st = tffr_adjoint(p, values, image);
+    return st;
+}
+
 int tffr_adjoint_unweighted(tffr_plan_t p, const void* values, void* image) {
     if (!p) return TFFR_ERR_INVALID_ARG;
     p->last_error.clear();

@@ -250,6 +250,41 @@ def test_errors_are_reported():
         assert e.value.status == 1
 
 
+@pytest.mark.parametrize("kw", [dict(), dict(tau=1.02), dict(separable=True, tau=1.0), dict(mode="unit")])
+def test_reconstruct_equals_the_three_calls(kw):
+    """tffr_reconstruct runs the same kernels as set_points + weights + adjoint: the same image up
+    to the order of the shared-memory additions (atomics: 1e-6 relative), and the oracle's; its
+    errors are those of the three calls."""
+    from paper_1910_10908_gb300 import Plan, TffrError
+    lx, ly, _, v = stolt_scene(96, 160, 128)
+    vals = dev(v.astype(np.complex64))
+    with Plan(128) as plan:
+        plan.set_points(dev(lx), dev(ly))
+        plan.weights(count=False, **kw)
+        three = plan.adjoint(vals).clone()
+        one = plan.reconstruct(dev(lx), dev(ly), vals, **kw)
+        torch.cuda.synchronize()
+        assert float(torch.linalg.vector_norm(one - three) / torch.linalg.vector_norm(three)) <= 1e-6
+        bad = lx.copy()
+        bad[3] = np.inf
+        with pytest.raises(TffrError) as e:
+            plan.reconstruct(dev(bad), dev(ly), vals, **kw)
+        assert e.value.status == 1
+        with pytest.raises(TffrError) as e:
+            plan.reconstruct(dev(lx), dev(ly), vals, q=-1.0)
+        assert e.value.status == 1
+        with pytest.raises(TffrError) as e:                # the failed calls left no weights
+            plan.adjoint(vals)
+        assert e.value.status == 2
+    if kw.get("mode") == "unit":
+        Dref = np.ones_like(lx)
+    else:
+        okw = {k: kw[k] for k in ("tau", "a", "q") if k in kw}
+        Dref = oracle.tffr_weights(lx, 128, lam_y=ly, My=128, separable=kw.get("separable", False), **okw)
+    ref = oracle.adjoint_image(lx, ly, v.astype(np.complex64), Dref, 128, 128)
+    assert rel_l2(one.cpu().numpy().astype(np.complex128), ref) <= TOL
+
+
 @pytest.mark.parametrize("kw", [dict(mode="unit"), dict(tau=1.02), dict(tau=1.05), dict(separable=True, tau=1.0),
                                 dict(a=0.5, q=2.5, tau=0.97)])
 def test_weight_modes_vs_oracle(kw):
