@@ -296,7 +296,8 @@ typedef struct {
  * and uses their row buffers and intermediates: recreate it after
  * tffr_set_points or tffr_weights on any of them, and do not run the plans'
  * own adjoints concurrently with it.  stream: the stream tffr_batch_adjoint is
- * ordered on.  Allocates and synchronises.
+ * ordered on.  Allocates and synchronises (the plans' streams and this one:
+ * the batch reads the plans' pulse rows once, into one record per row).
  * Errors: INVALID_ARG (NULL pointers, n < 1, a plan outside the supported
  * layout, value type or sides, or plans with different widths, kernel shapes
  * or weight options); NOT_READY (a plan without points or weights); OOM; CUDA.

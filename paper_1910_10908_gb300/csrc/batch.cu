@@ -23,6 +23,8 @@
 // bounded (wait_ns of device time), and a wait that runs out raises an error
 // bit and an abort flag that ends every later wait at once.
 
+#include <algorithm>
+
 #include "batch_launch.h"
 #include "kernels_spread.cuh"
 #include "line_kernels.cuh"
@@ -66,20 +68,19 @@ k_batch_spread(BatchSpreadArgs a) {
     float2* s_row = s_val + kSpreadStageElems;
     constexpr int H = W / 2;
     const int tid = threadIdx.x;
-    const int tag = __ldg(&a.row_tag[blockIdx.x]);         // also the deferred list's row field
-    const int k = tag >> 16, p = tag & 0xffff;
-    const BatchPatch* __restrict__ bp = a.patches + k;
-    const int M = __ldg(&bp->M), n = __ldg(&bp->n);
-    const int len = __ldg(&bp->row_len[p]), clo = __ldg(&bp->row_clo[p]);
+    const BatchRow row = a.rows[blockIdx.x];
+    const int tag = row.tag;                               // also the deferred list's row field
+    const int M = row.M, n = row.n, len = row.len, clo = row.clo, L = row.L;
+    const int64_t s0 = row.s0;
     const bool periodic = (len == n) && (clo == 0);
-    const int64_t s0 = __ldg(&bp->row_start[p]);
-    const int L = (int)(__ldg(&bp->row_end[p]) - s0);
     const WeightArgs& wa = a.wa;
     for (int i = tid; i < len; i += kSpreadThreads) s_row[i] = make_float2(0.f, 0.f);
     float dy = 1.0f;
     bool dy_exact = false, edges = true;
     if (wa.mode == 0) {
         if (wa.separable) {
+            const BatchPatch* __restrict__ bp = a.patches + (tag >> 16);
+            const int p = tag & 0xffff;
             const float gy = g_fitted(__ldg(&bp->row_ly[p]), __ldg(&bp->row_fy[p]), M, wa, dy_exact);
             dy = (gy != 0.0f) ? __frcp_rn(gy) : 0.0f;
         }
@@ -87,9 +88,9 @@ k_batch_spread(BatchSpreadArgs a) {
         edges = periodic || (mn >> 1) - wa.reach < -(M / 2) || (mx >> 1) + wa.reach >= M - M / 2;
     }
     const int run = (tid >> 5) + (kSpreadThreads / 32) * (tid & 31);
-    const double* __restrict__ g_lam = bp->lam_x + s0;
-    const float2* __restrict__ g_val = bp->values + s0;
-    const float* user_D = bp->user_D;
+    const double* __restrict__ g_lam = row.lam;
+    const float2* __restrict__ g_val = row.val;
+    const float* user_D = wa.mode == 2 ? a.patches[tag >> 16].user_D : nullptr;
     for (int t0 = 0; t0 < L; t0 += kSpreadTile) {
         const int cnt = min(kSpreadTile, L - t0);
         __syncthreads();                                   // row zeroed / previous tile consumed
@@ -117,8 +118,31 @@ k_batch_spread(BatchSpreadArgs a) {
                                      a.defer, s_row, user_D);
     }
     __syncthreads();
-    float2* out = bp->R + __ldg(&bp->row_off[p]);
-    for (int i = tid; i < len; i += kSpreadThreads) out[i] = s_row[i];
+    for (int i = tid; i < len; i += kSpreadThreads) row.out[i] = s_row[i];
+}
+
+// Each block's pulse row of the spread launch, from the row tags and the
+// patches' row arrays.
+static __global__ void k_batch_rows(BatchSpreadArgs a, int rows) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+        const int tag = a.row_tag[r];
+        const BatchPatch* bp = a.patches + (tag >> 16);
+        const int p = tag & 0xffff;
+        BatchRow row;
+        const int64_t s0 = bp->row_start[p];
+        row.lam = bp->lam_x + s0;
+        row.val = bp->values + s0;
+        row.out = bp->R + bp->row_off[p];
+        row.s0 = (int)s0;
+        row.L = (int)(bp->row_end[p] - s0);
+        row.clo = bp->row_clo[p];
+        row.len = bp->row_len[p];
+        row.tag = tag;
+        row.M = bp->M;
+        row.n = bp->n;
+        row.pad = 0;
+        a.rows[r] = row;
+    }
 }
 
 // The deferred samples of k_batch_spread: D_n decided in FP64, then added into
@@ -472,6 +496,10 @@ void launch_batch_spread(int w, int rows, int max_len, cudaStream_t s, const Bat
             if (deferred) k_batch_spread_deferred<8><<<152 * 2, 256, 0, s>>>(a);
             break;
     }
+}
+
+void launch_batch_rows(int rows, cudaStream_t s, const BatchSpreadArgs& a) {
+    k_batch_rows<<<std::max(1, std::min((rows + 255) / 256, 152 * 4)), 256, 0, s>>>(a, rows);
 }
 
 void launch_batch_fft(int logn, int grid, cudaStream_t s, const BatchClassArgs& a) {

@@ -45,9 +45,25 @@ struct BatchPatch {
     float2* image;                      // caller's image [M][M]
 };
 
+// One pulse row of the batch, for the spread launch (one block each): every
+// value its setup needs in one place, so that the block's staging copies
+// wait on a single load.
+struct BatchRow {
+    const double* lam;                  // the row's coordinates (the patch's lam_x + s0)
+    const float2* val;                  // the row's samples
+    float2* out;                        // the row's buffer in R
+    int s0;                             // first sample, as an index into the patch's arrays
+    int L;                              // samples
+    int clo, len;                       // first fine cell and cells of the row buffer
+    int tag;                            // (patch << 16) | pulse row
+    int M, n;                           // the patch's image side and fine-grid side
+    int pad;
+};
+
 // The spread launch over every pulse row of every patch.
 struct BatchSpreadArgs {
     const BatchPatch* patches;          // [npatch] every patch of the batch (npatch < 2^15, rows < 2^16)
+    BatchRow* rows;                     // [blocks] each block's pulse row (filled at the batch's creation)
     const int* row_tag;                 // [blocks] (patch << 16) | pulse row of each block
     int npatch;
     WeightArgs wa;                      // the batch's weight evaluation (the patch's M decides the edges)
@@ -84,6 +100,8 @@ cudaError_t batch_set_attributes();
 int batch_max_blocks_per_sm(int logn);
 
 void launch_batch_spread(int w, int rows, int max_len, cudaStream_t s, const BatchSpreadArgs& a);
+// Fills a.rows[0 .. rows) from the patches' row arrays (after their set_points).
+void launch_batch_rows(int rows, cudaStream_t s, const BatchSpreadArgs& a);
 void launch_batch_fft(int logn, int grid, cudaStream_t s, const BatchClassArgs& a);
 
 }  // namespace tffr

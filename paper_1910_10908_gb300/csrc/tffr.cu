@@ -1494,6 +1494,7 @@ struct tffr_batch_s {
     std::vector<BatchClass> cls;
     BatchPatch* d_patches = nullptr;                   // every patch (the spread launch)
     int* d_row_tag = nullptr;                          // [rows_total] (patch << 16) | pulse row of each spread block
+    BatchRow* d_rows = nullptr;                        // [rows_total] each spread block's pulse row
     int rows_total = 0, max_len = 0, w = 6;
     WeightArgs wa;
     TapPoly tp;
@@ -1519,6 +1520,7 @@ void batch_free(tffr_batch_s* b) {
     }
     if (b->d_patches) cudaFree(b->d_patches);
     if (b->d_row_tag) cudaFree(b->d_row_tag);
+    if (b->d_rows) cudaFree(b->d_rows);
     if (b->d_defer_count) cudaFree(b->d_defer_count);
     if (b->d_defer) cudaFree(b->d_defer);
     if (b->d_err) cudaFree(b->d_err);
@@ -1549,6 +1551,7 @@ BatchClassArgs class_args(const tffr_batch_s* b, const BatchClass& c) {
 cudaError_t launch_spread(const tffr_batch_s* b) {
     BatchSpreadArgs a;
     a.patches = b->d_patches;
+    a.rows = b->d_rows;
     a.row_tag = b->d_row_tag;
     a.npatch = b->n;
     a.wa = b->wa;
@@ -1666,6 +1669,19 @@ int tffr_batch_create(const tffr_plan_t* plans, int n, const void* const* values
     if (e == cudaSuccess) e = cudaMemcpy(b->d_patches, all.data(), n * sizeof(BatchPatch), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_row_tag, row_tag.data(), row_tag.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_rows, row_tag.size() * sizeof(BatchRow));
+    // each spread block's pulse row, from the plans' row arrays once their work is done
+    for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamSynchronize(plans[i]->stream);
+    if (e == cudaSuccess && b->rows_total > 0) {
+        BatchSpreadArgs ra;
+        ra.patches = b->d_patches;
+        ra.rows = b->d_rows;
+        ra.row_tag = b->d_row_tag;
+        ra.npatch = n;
+        launch_batch_rows(b->rows_total, b->stream, ra);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
     if (e != cudaSuccess) return bail(e);
     for (BatchClass& c : b->cls) {
         const int m = (int)c.members.size();
