@@ -226,6 +226,11 @@ struct RowScanArgs {
     int4* tile;                                        // [tiles] first row id (-1: none), last row id, first row start
     int2* head;                                        // [tiles] cell extent of the samples before the first start
     int* flags;                                        // [0] error bits, [1] rows, [3] overflow
+    // zeroed by the scan for the kernels after it (no separate memset launches)
+    int* zero_i;                                       // [n_zero_i] the per-fine-row and per-cell counters
+    int n_zero_i;
+    float4* zero_w;                                    // [n_zero_w] the fine-row tap weights
+    int n_zero_w;
 };
 
 // Error bits: 1 bad lam_y, 2 bad lam_x.  Local run index -1 marks the samples
@@ -238,6 +243,9 @@ k_scan_rows(int64_t N, const double* __restrict__ lam_x, const double* __restric
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int tile = blockIdx.x;
     const int64_t wbase = (int64_t)tile * kRowScanTile + (int64_t)wid * (32 * kRowScanK);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_zero_i; i += gridDim.x * blockDim.x) a.zero_i[i] = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n_zero_w; i += gridDim.x * blockDim.x)
+        a.zero_w[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (threadIdx.x == 0) {
         s_first = -1;
         s_hmin = kIntMax;

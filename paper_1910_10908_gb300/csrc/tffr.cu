@@ -510,6 +510,8 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     // cursor[ny + 1..2 ny]: pulse rows per fine y cell, then their first places
     // in fine-y order; cursor[2 ny + 1..3 ny]: arrivals per fine y cell
     int* const ly_first = p->cursor.ptr + ny + 1;
+    CK(grow(p, p->ell_first, ny));
+    CK(grow(p, p->ell_w, (int64_t)(kEllMax / 4) * ny));
     CK(cudaMemsetAsync(p->d_small.ptr, 0, 5 * sizeof(int), p->stream));
     RowScanArgs a;
     a.row_start = p->row_start.ptr;
@@ -520,10 +522,13 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     a.tile = p->tile_info.ptr;
     a.head = p->tile_head.ptr;
     a.flags = p->d_small.ptr;
+    a.zero_i = p->cursor.ptr;                          // every counter of cursor[], zero for k_row_finish
+    a.n_zero_i = 3 * ny + 1;
+    a.zero_w = p->ell_w.ptr;                           // the tap weights, zero for k_ell_fill
+    a.n_zero_w = (kEllMax / 4) * ny;
     k_scan_rows<<<(unsigned)ntiles, kRowScanWarps * 32, 0, p->stream>>>(N, p->lam_x, p->lam_y, a);
     CK_LAUNCH("k_scan_rows");
     const int* runs = p->d_small.ptr + 1;
-    CK(cudaMemsetAsync(p->cursor.ptr, 0, (size_t)(3 * ny + 1) * sizeof(int), p->stream));
     k_row_finish<<<prow, 256, 0, p->stream>>>(runs, cap, N, (int)ntiles, p->tile_info.ptr, p->tile_head.ptr, p->nx,
                                               ny, w, p->taps, p->lam_y, p->row_start.ptr, p->row_end.ptr,
                                               p->row_min.ptr, p->row_max.ptr, p->row_clo.ptr, p->row_len.ptr,
@@ -543,9 +548,6 @@ int scan_rows(tffr_plan_s* p, int* P_out) {
     // fine-row order).
     CK(cudaMemcpyAsync(p->h_small, p->d_small.ptr, 10 * sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     CK(cudaEventRecord(p->readback, p->stream));
-    CK(grow(p, p->ell_first, ny));
-    CK(grow(p, p->ell_w, (int64_t)(kEllMax / 4) * ny));
-    CK(cudaMemsetAsync(p->ell_w.ptr, 0, (size_t)(kEllMax / 4) * ny * sizeof(float4), p->stream));
     k_ell_fill<<<prow, 256, 0, p->stream>>>(runs, cap, ny, w, p->row_ly.ptr, p->row_wy.ptr, ly_first,
                                             p->rank_row.ptr, p->q_ly.ptr, reinterpret_cast<float4*>(p->q_wy.ptr),
                                             ly_first + ny, p->ell_first.ptr,
