@@ -202,10 +202,18 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[Line<LOGN>::V], const 
         if constexpr (NS > 1) {
             const int k = (threadIdx.x + b * L::T) & (NS - 1);
             if constexpr (NS * R <= L::NT) {
-                constexpr int TS = ilog2c(L::NT) - LOGNS - LOGR;     // W_{NS R} = W_NT^(2^TS)
+                if constexpr (L::V == 32) {
+                    // the transposed table (load_twiddles): entry r 32 + k = W_1024^(r k)
+                    static_assert(NS == 32 && R == 32, "the transposed direct table serves NS = R = 32 only");
 #pragma unroll
-                for (int r = 1; r < R; ++r)
-                    v[b * R + r] = cmul(v[b * R + r], conj_if<SGN>(tw.t[(r * k) << TS]));
+                    for (int r = 1; r < R; ++r)
+                        v[b * R + r] = cmul(v[b * R + r], conj_if<SGN>(tw.t[r * 32 + k]));
+                } else {
+                    constexpr int TS = ilog2c(L::NT) - LOGNS - LOGR;     // W_{NS R} = W_NT^(2^TS)
+#pragma unroll
+                    for (int r = 1; r < R; ++r)
+                        v[b * R + r] = cmul(v[b * R + r], conj_if<SGN>(tw.t[(r * k) << TS]));
+                }
             } else {
                 constexpr int TSHIFT = LOGN - LOGNS - LOGR;
                 float2 p[R];
@@ -373,7 +381,12 @@ __device__ __forceinline__ void fft_line_regs(float2 (&v)[Line<LOGN>::V], float2
 }
 
 // Load the twiddle tables of an N-point line into shared memory: the two
-// levels for any exponent and the direct table of the NT-th roots.
+// levels for any exponent and the direct table of the NT-th roots.  With 32
+// values a thread (the 8192-point line) the direct table serves one stage
+// only, the radix-32 stage with NS = 32, whose thread k needs W_1024^(r k) for
+// r < 32: it is stored transposed, entry r 32 + k, so that a warp's 32 lanes
+// (k = 0 .. 31) read 32 consecutive words (no bank conflict; in natural order
+// lane k reads word r k, up to 32-way conflicts for even r).
 template <int LOGN>
 __device__ __forceinline__ Twiddles load_twiddles(float2* s_twh, float2* s_twl, float2* s_tt,
                                                   const float2* __restrict__ twh, const float2* __restrict__ twl,
@@ -381,7 +394,12 @@ __device__ __forceinline__ Twiddles load_twiddles(float2* s_twh, float2* s_twl, 
     using L = Line<LOGN>;
     for (int i = threadIdx.x; i < L::NH; i += L::T) s_twh[i] = twh[i];
     for (int i = threadIdx.x; i < L::NL; i += L::T) s_twl[i] = twl[i];
-    for (int i = threadIdx.x; i < L::NT; i += L::T) s_tt[i] = tt[i];
+    if constexpr (L::V == 32) {
+        static_assert(L::NT == 1024, "the transposed direct table holds 32 x 32 roots");
+        for (int i = threadIdx.x; i < L::NT; i += L::T) s_tt[i] = tt[(i >> 5) * (i & 31)];
+    } else {
+        for (int i = threadIdx.x; i < L::NT; i += L::T) s_tt[i] = tt[i];
+    }
     return Twiddles{s_twh, s_twl, s_tt};
 }
 
