@@ -169,7 +169,8 @@ struct Line {
     static constexpr int NH = N >= 64 ? N / 64 : 1;       // twiddle table levels
     static constexpr int NL = N >= 64 ? 64 : N;
     static constexpr int NT = N >= 1024 ? 1024 : N;       // direct table of the NT-th roots of unity
-    static constexpr int SMEM_ELEMS = PADLEN + 128 + 64 + 1024;
+    static constexpr int NT2 = V == 16 ? 256 : 0;         // transposed 16 x 16 roots (see load_twiddles)
+    static constexpr int SMEM_ELEMS = PADLEN + 128 + 64 + 1024 + NT2;
     __device__ __forceinline__ static int pad(int i) { return i + (i >> LV); }
 };
 
@@ -177,6 +178,7 @@ struct Twiddles {
     const float2* h;        // shared: exp(2 pi i 64 h / N)
     const float2* l;        // shared: exp(2 pi i l / N)
     const float2* t;        // shared: exp(2 pi i m / NT), NT = min(N, 1024)
+    const float2* t2;       // shared (16 values a thread): exp(2 pi i r k / 256) at 16 r + k
     __device__ __forceinline__ float2 operator()(int m) const { return cmul(h[m >> 6], l[m & 63]); }
 };
 
@@ -208,6 +210,11 @@ __device__ __forceinline__ void stage_compute(float2 (&v)[Line<LOGN>::V], const 
 #pragma unroll
                     for (int r = 1; r < R; ++r)
                         v[b * R + r] = cmul(v[b * R + r], conj_if<SGN>(tw.t[r * 32 + k]));
+                } else if constexpr (L::V == 16 && NS == 16 && R == 16) {
+                    // the transposed 16 x 16 table (load_twiddles): entry r 16 + k = W_256^(r k)
+#pragma unroll
+                    for (int r = 1; r < R; ++r)
+                        v[b * R + r] = cmul(v[b * R + r], conj_if<SGN>(tw.t2[r * 16 + k]));
                 } else {
                     constexpr int TS = ilog2c(L::NT) - LOGNS - LOGR;     // W_{NS R} = W_NT^(2^TS)
 #pragma unroll
@@ -400,7 +407,16 @@ __device__ __forceinline__ Twiddles load_twiddles(float2* s_twh, float2* s_twl, 
     } else {
         for (int i = threadIdx.x; i < L::NT; i += L::T) s_tt[i] = tt[i];
     }
-    return Twiddles{s_twh, s_twl, s_tt};
+    // 16 values a thread: the radix-16 stage with NS = 16 (thread k needs
+    // W_256^(r k), r < 16) reads a transposed copy after the direct table, so
+    // that a half-warp's lanes read 16 consecutive words (in the direct table,
+    // at stride r NT / 256 words, every r conflicts at least 2-way)
+    float2* s_tt2 = s_tt + 1024;
+    if constexpr (L::NT2 > 0) {
+        static_assert(L::NT >= 256, "W_256 from the direct table");
+        for (int i = threadIdx.x; i < L::NT2; i += L::T) s_tt2[i] = tt[(i >> 4) * (i & 15) * (L::NT / 256)];
+    }
+    return Twiddles{s_twh, s_twl, s_tt, s_tt2};
 }
 
 }  // namespace tffr
