@@ -386,10 +386,11 @@ k_fwd_rows(RowsView rv, GeneralView gv, const float2* __restrict__ T, int ny, in
 // the 16 places of each 128 bytes fall in one shared-memory wavefront.  In the
 // adjoint the same area later receives the cluster's output rows: 4 columns
 // of N / 8 rows, each column padded by kRecvPad entries so that a column
-// starts half a bank cycle (64 bytes) after the previous one.
+// starts a quarter bank cycle (32 bytes) after the previous one: the 16 lanes
+// of a half-warp reading 4 rows x 4 columns then touch 16 different banks.
 template <int LOGN>
 constexpr int kPulseColOff = (Line<LOGN>::SMEM_ELEMS + 15) & ~15;
-constexpr int kRecvPad = 8;
+constexpr int kRecvPad = 4;
 
 template <int LOGN>
 __host__ __device__ constexpr size_t line_smem_pulse_cols() {
