@@ -631,30 +631,56 @@ k_fwd_cols_pulse(const float2* __restrict__ img, int Mx, FftTables tab, const fl
     const Twiddles tw = load_twiddles<LOGN>(S.twh, S.twl, S.tt, tab.twh, tab.twl, tab.tt);
     for (int i = MY / 2 + tid; i < NY - MY / 2; i += L::T) S.buf[L::pad(i)] = make_float2(0.f, 0.f);
     static_assert(L::T % kColCluster == 0, "line threads must be a multiple of the cluster size");
-    float2* const peer = cluster.map_shared_rank(S.buf, tid % kColCluster);
+    // The cluster's 4 image columns: CTA rank reads rows [rank IROWS, (rank + 1)
+    // IROWS), each row's 32-byte piece (all 4 columns) by one thread, and sends
+    // column c of it, deapodised and zero-padded into the line, to CTA c: a
+    // warp's store carries 32 neighbouring rows to one CTA.
     constexpr int IROWS = MY / kColCluster;
+    constexpr int KR = (IROWS + L::T - 1) / L::T;      // rows per thread
+    float2* peer[kColCluster];
+#pragma unroll
+    for (int c = 0; c < kColCluster; ++c) peer[c] = cluster.map_shared_rank(S.buf, c);
     {
         cluster_arrive_relaxed();                      // every CTA runs before its memory is written
-        float2 tmp[V / 2];
+        float4 lo[KR], hi[KR];
 #pragma unroll
-        for (int u = 0; u < V / 2; ++u) {
-            const int i = tid + u * L::T;
-            tmp[u] = __ldg(&img[(size_t)(rank * IROWS + i / kColCluster) * Mx + jx0 + i % kColCluster]);
+        for (int k = 0; k < KR; ++k) {
+            const int j = tid + k * L::T;
+            if (j < IROWS) {
+                const float4* src = reinterpret_cast<const float4*>(img + (size_t)(rank * IROWS + j) * Mx + jx0);
+                lo[k] = __ldg(src);
+                hi[k] = __ldg(src + 1);
+            }
         }
-        cluster_wait();
-        const float dx = __ldg(&deap_x[jx0 + tid % kColCluster]);
+        float dx[kColCluster];
 #pragma unroll
-        for (int u = 0; u < V / 2; ++u) {
-            const int i = tid + u * L::T;
-            const int jy = rank * IROWS + i / kColCluster;
-            peer[L::pad(wrapmod(jy - MY / 2, NY))] = cscale(tmp[u], __ldg(&deap_y[jy]) * dx);
+        for (int c = 0; c < kColCluster; ++c) dx[c] = __ldg(&deap_x[jx0 + c]);
+        cluster_wait();
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            const int j = tid + k * L::T;
+            if (j < IROWS) {
+                const int jy = rank * IROWS + j;
+                const float dy = __ldg(&deap_y[jy]);
+                const int o = L::pad(wrapmod(jy - MY / 2, NY));
+                peer[0][o] = cscale(make_float2(lo[k].x, lo[k].y), dy * dx[0]);
+                peer[1][o] = cscale(make_float2(lo[k].z, lo[k].w), dy * dx[1]);
+                peer[2][o] = cscale(make_float2(hi[k].x, hi[k].y), dy * dx[2]);
+                peer[3][o] = cscale(make_float2(hi[k].z, hi[k].w), dy * dx[3]);
+            }
         }
     }
     cluster.sync();
     fft_line_smem<LOGN, -1>(S.buf, tw);
     // transposed azimuth taps, per place q in fine-y order (a warp's lanes
     // read neighbouring cells of the line):
-    // F_q = sum_s phi_y(s - (w/2 - 1) - fy_q) line[ly_q - (w/2 - 1) + s]
+    // F_q = sum_s phi_y(s - (w/2 - 1) - fy_q) line[ly_q - (w/2 - 1) + s],
+    // pushed to the CTA that writes place q's row of F: CTA q / PQ keeps the
+    // cluster's 4 columns of its places in fcol, column c at c (PQ + kRecvPad)
+    const int PQ = (P + kColCluster - 1) / kColCluster;
+    float2* dst[kColCluster];
+#pragma unroll
+    for (int c = 0; c < kColCluster; ++c) dst[c] = cluster.map_shared_rank(fcol, c) + rank * (PQ + kRecvPad);
     const int h = w / 2;
     for (int base = 0; base < P; base += kPulseBatch * L::T) {
         int c0[kPulseBatch];
@@ -678,28 +704,18 @@ k_fwd_cols_pulse(const float2* __restrict__ img, int Mx, FftTables tab, const fl
                     a.y = fmaf(wy[b][s], g.y, a.y);
                 }
             }
-            fcol[p] = a;
+            const int o = p / PQ;
+            float2* d = o == 0 ? dst[0] : o == 1 ? dst[1] : o == 2 ? dst[2] : dst[3];
+            d[p - o * PQ] = a;
         }
     }
     cluster.sync();
-    float2* const peer_f = cluster.map_shared_rank(fcol, tid % kColCluster);
-    const int PQ = (P + kColCluster - 1) / kColCluster;
+    // this CTA's places [p0, p0 + PQ) of the 4 columns, from fcol, as 32-byte row pieces of F
     const int p0 = min(P, rank * PQ), nel = (min(P, p0 + PQ) - p0) * kColCluster;
-    for (int base = 0; base < nel; base += V * L::T) {
-        float2 tmp[V];
-#pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const int i = base + tid + u * L::T;
-            tmp[u] = (i < nel) ? peer_f[p0 + i / kColCluster] : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < V; ++u) {
-            const int i = base + tid + u * L::T;
-            if (i < nel) F[(size_t)(p0 + i / kColCluster) * Mx + jx0 + i % kColCluster] = tmp[u];
-        }
+    for (int i = tid; i < nel; i += L::T) {
+        const int r = i / kColCluster, c = i % kColCluster;
+        F[(size_t)(p0 + r) * Mx + jx0 + c] = fcol[c * (PQ + kRecvPad) + r];
     }
-    cluster_arrive_relaxed();                          // every remote load was consumed above
-    cluster_wait();
 }
 
 // Forward x-pass epilogue: line cell o goes to the row buffer at
