@@ -2,6 +2,8 @@
 // length 2^5 .. 2^13 (kept in their own translation unit so that the build
 // compiles them in parallel with the rest of the library).
 
+#include <algorithm>
+
 #include "line_kernels.cuh"
 #include "line_launch.h"
 
@@ -112,14 +114,23 @@ void launch_adj_rows_pulse(int lognx, int P, cudaStream_t s, const RowsView& rv,
 
 void launch_adj_cols_pulse(int logny, int Mx, int P, cudaStream_t s, const float2* F, FftTables tab,
                            const int* ell_first, const float4* ell_w, int K, const float* deap_y, float2* img) {
+    // clusters resident at once (two CTAs per SM): the prefetch distance in blocks
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 152;
+    }
+    const int ahead = std::max(1, sms * 2 / kColCluster);
     if (K <= 4) {
 #define L(LG) k_adj_cols_pulse<LG, 1><<<Mx, Line<LG>::T, line_smem_pulse_cols<LG>(), s>>>(F, P, Mx, tab, ell_first, \
-                                                                                         ell_w, deap_y, img)
+                                                                                         ell_w, deap_y, img, ahead)
         TFFR_LOGN_SWITCH(logny, L)
 #undef L
     } else {
 #define L(LG) k_adj_cols_pulse<LG, 2><<<Mx, Line<LG>::T, line_smem_pulse_cols<LG>(), s>>>(F, P, Mx, tab, ell_first, \
-                                                                                         ell_w, deap_y, img)
+                                                                                         ell_w, deap_y, img, ahead)
         TFFR_LOGN_SWITCH(logny, L)
 #undef L
     }

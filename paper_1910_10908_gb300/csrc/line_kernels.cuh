@@ -515,7 +515,8 @@ __device__ __forceinline__ float2 gather_taps(const float2* fcol, int q, const f
 template <int LOGN, int K4>
 __global__ void __cluster_dims__(kColCluster, 1, 1) __launch_bounds__(Line<LOGN>::T, (Line<LOGN>::T >= 256 ? 2 : 4))
 k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, const int* __restrict__ ell_first,
-                 const float4* __restrict__ ell_w, const float* __restrict__ deap_y, float2* __restrict__ img) {
+                 const float4* __restrict__ ell_w, const float* __restrict__ deap_y, float2* __restrict__ img,
+                 int ahead) {
     using L = Line<LOGN>;
     constexpr int NY = L::N, MY = NY / 2, V = L::V;
     constexpr int OROWS = MY / kColCluster;            // image rows each CTA of the cluster writes
@@ -544,6 +545,12 @@ k_adj_cols_pulse(const float2* __restrict__ F, int P, int Mx, FftTables tab, con
     const int ldq = pulse_ldq(P), PQ = ldq / kColCluster;
     const int p0 = rank * PQ, nq = max(0, min(P, p0 + PQ) - p0);
     const float4* const Fq = reinterpret_cast<const float4*>(F + ((size_t)(jx0 / kColCluster) * ldq + p0) * kColCluster);
+    // the same quarter of the block one wave of clusters ahead (`ahead` blocks
+    // later) into L2, so that its CTA's loads find it there
+    if (tid == 0 && nq > 0 && jx0 / kColCluster + ahead < Mx / kColCluster) {
+        const float2* nxt = F + ((size_t)(jx0 / kColCluster + ahead) * ldq + p0) * kColCluster;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(nxt), "r"((unsigned)nq * 32u) : "memory");
+    }
     float4 lo[KP], hi[KP];
 #pragma unroll
     for (int k = 0; k < KP; ++k) {
