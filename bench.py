@@ -37,7 +37,9 @@ WORKLOAD = "stripmap_4096"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a stage's
 # kernel on this workload, from one ncu capture of that kernel; an entry is removed
 # when its kernel changes, and a stage without one reports null.
-DRAM_TRAFFIC = {}
+DRAM_TRAFFIC = {
+    ("col_fft", "pulse_rows"): 227_163_136,     # k_adj_cols_pulse<13, 1>
+}
 
 
 def peaks():
