@@ -114,6 +114,34 @@ def test_points_on_cell_edges_and_grid_boundary():
     assert rel_l2(img, ref) <= TOL
 
 
+def test_pulse_rows_through_zero_and_at_special_magnitudes():
+    """Pulse rows whose lam_x runs through zero and through magnitudes where the
+    bit-pattern split changes form: exact zero, +-1e-9 and +-2^-12 (below the fast
+    split's range: deferred), +-2^-11 (its edge), half-integers (cell edges),
+    integers (truncation breakpoints: the FP64 decision) and powers of two (where
+    the exponent steps), in both pass orders and with the separable weights."""
+    M = 64
+    special = np.array([0.0, 1e-9, 2.0 ** -12, 2.0 ** -11, 0.25, 0.5, 1.0, 1.5, 2.0, 3.0, 4.0, 7.5, 8.0, 15.0,
+                        16.0, 24.0, 31.5])
+    base = np.unique(np.concatenate([special, -special, np.linspace(-31.9, 31.9, 97)]))
+    g = np.random.default_rng(12)
+    rows = 40
+    lam_y = np.linspace(-31.3, 30.7, rows)
+    lx = np.concatenate([base + (0.0 if r % 2 == 0 else g.uniform(-1e-3, 1e-3)) for r in range(rows)])
+    ly = np.repeat(lam_y, base.shape[0])
+    v = (g.standard_normal(lx.shape[0]) + 1j * g.standard_normal(lx.shape[0])).astype(np.complex64)
+    for order in ("auto", "fine_rows"):
+        for sep in (False, True):
+            img, D, kept, info = gpu_adjoint(lx, ly, v, M, width=8, layout="rows", order=order,
+                                             wkw=dict(separable=sep, tau=1.0))
+            assert info["layout"] == 2 and info["n_rows"] == rows
+            Dref = oracle.tffr_weights(lx, M, lam_y=ly, My=M, separable=sep, tau=1.0)
+            assert kept == np.count_nonzero(Dref)
+            assert d_err(D, Dref) < 3e-7
+            ref = oracle.adjoint_image(lx, ly, v, Dref, M, M)
+            assert rel_l2(img, ref) <= TOL
+
+
 def test_rows_layout_forced_on_short_rows():
     lx, ly, rp = stolt_points(48, 6, 64)       # 6 samples per pulse row
     g = np.random.default_rng(1)
