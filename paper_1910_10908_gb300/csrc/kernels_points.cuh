@@ -114,29 +114,11 @@ __device__ __forceinline__ float g_fitted(int cell, float f, int M, const Weight
     return horner(A.c1, A.n1, (2.0f * v - A.vb - 0.5f) / (0.5f - A.vb));
 }
 
-// 1/G (before the threshold) from the fine cell and offset: the direct fit
-// of 1/G on piece 0, else 1/G from the fitted G of piece 1; sets exact = true
-// on a truncation breakpoint (the grid edges are the caller's to check).
-__device__ __forceinline__ float d_fitted(int cell, float f, const WeightArgs& A, bool& exact) {
-    const float delta = 0.5f * ((float)(cell & 1) + f);          // lam - floor(lam)
-    const float v = fabsf(delta - 0.5f);
-    exact |= (v == A.vb) | (v == 0.5f);
-    if (v < A.vb) {
-        const float r = v * A.inv_vb;
-        const float s = fmaf(2.0f * r, r, -1.0f);
-        float d = A.d0[kD0Coefs - 1];
-#pragma unroll
-        for (int k = kD0Coefs - 2; k >= 0; --k) d = fmaf(d, s, A.d0[k]);
-        return d;
-    }
-    const float G = horner(A.c1, A.n1, (2.0f * v - A.vb - 0.5f) / (0.5f - A.vb));
-    return (G != 0.0f) ? __frcp_rn(G) : 0.0f;
-}
-
-// d_fitted's piece 0 from the fine cell and the fixed-point offset F
-// (fixed_coord_fast): lam - floor(lam) is the 0.32 fixed-point number
-// (cell & 1, F) >> 1.  No branch: a sample outside piece 0 (v >= vb, which
-// includes the truncation breakpoints) sets exact, and its value is not used.
+// 1/G (before the threshold) by its direct fit on piece 0, from the fine
+// cell and the fixed-point offset F (fixed_coord_fast): lam - floor(lam) is
+// the 0.32 fixed-point number (cell & 1, F) >> 1.  No branch: a sample outside
+// piece 0 (v >= vb, which includes the truncation breakpoints) sets exact, and
+// its value is not used.
 __device__ __forceinline__ float d_fixed0(int cell, unsigned F, const WeightArgs& A, bool& exact) {
     const unsigned D = __funnelshift_r(F, (unsigned)cell, 1);
     const float v = fabsf(fmaf(__uint2float_rn(D), 0x1p-32f, -0.5f));   // |lam - floor(lam) - 1/2|
