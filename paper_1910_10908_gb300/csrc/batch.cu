@@ -59,13 +59,31 @@ __device__ __forceinline__ int find_patch(const int* __restrict__ first, int n, 
 // ---------------------------------------------------------------------------
 // Spread of every pulse row of every patch
 // ---------------------------------------------------------------------------
+// The batch spread's own block shape: its rows are short (a few hundred to
+// 2048 samples), so 128 threads a row keep runs near kSpreadRun samples and let
+// more rows (blocks) share an SM to hide each row's setup latency.  The staging
+// pads every 32 elements: a warp's lanes walk runs 4 apart (32 samples).
+constexpr int kBatchThreads = 128;
+constexpr int kBatchTile = kBatchThreads * kSpreadRun;
+constexpr int kBatchPadEvery = (kBatchThreads / 32) * kSpreadRun;
+__host__ __device__ constexpr int batch_pad(int i) { return i + i / kBatchPadEvery; }
+constexpr int kBatchStageElems = (batch_pad(kBatchTile - 1) + 2) & ~1;   // even: the values start 16-byte aligned
+
+struct BatchStaged {
+    const double* s_lam;
+    const float2* s_val;
+    int t0;
+    __device__ __forceinline__ double lam(int i) const { return s_lam[batch_pad(i - t0)]; }
+    __device__ __forceinline__ float2 val(int i) const { return s_val[batch_pad(i - t0)]; }
+};
+
 template <int W>
-__global__ void __launch_bounds__(kSpreadThreads, 4)
+__global__ void __launch_bounds__(kBatchThreads, 8)
 k_batch_spread(BatchSpreadArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* s_lam = reinterpret_cast<double*>(smem_raw);
-    float2* s_val = reinterpret_cast<float2*>(s_lam + kSpreadStageElems);
-    float2* s_row = s_val + kSpreadStageElems;
+    float2* s_val = reinterpret_cast<float2*>(s_lam + kBatchStageElems);
+    float2* s_row = s_val + kBatchStageElems;
     constexpr int H = W / 2;
     const int tid = threadIdx.x;
     const BatchRow row = a.rows[blockIdx.x];
@@ -74,7 +92,7 @@ k_batch_spread(BatchSpreadArgs a) {
     const int64_t s0 = row.s0;
     const bool periodic = (len == n) && (clo == 0);
     const WeightArgs& wa = a.wa;
-    for (int i = tid; i < len; i += kSpreadThreads) s_row[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < len; i += kBatchThreads) s_row[i] = make_float2(0.f, 0.f);
     float dy = 1.0f;
     bool dy_exact = false, edges = true;
     if (wa.mode == 0) {
@@ -87,26 +105,26 @@ k_batch_spread(BatchSpreadArgs a) {
         const int mn = clo + (H - 1), mx = clo + len - H - 1;
         edges = periodic || (mn >> 1) - wa.reach < -(M / 2) || (mx >> 1) + wa.reach >= M - M / 2;
     }
-    const int run = (tid >> 5) + (kSpreadThreads / 32) * (tid & 31);
+    const int run = (tid >> 5) + (kBatchThreads / 32) * (tid & 31);
     const double* __restrict__ g_lam = row.lam;
     const float2* __restrict__ g_val = row.val;
     const float* user_D = wa.mode == 2 ? a.patches[tag >> 16].user_D : nullptr;
-    for (int t0 = 0; t0 < L; t0 += kSpreadTile) {
-        const int cnt = min(kSpreadTile, L - t0);
+    for (int t0 = 0; t0 < L; t0 += kBatchTile) {
+        const int cnt = min(kBatchTile, L - t0);
         __syncthreads();                                   // row zeroed / previous tile consumed
-        for (int e = tid; e < cnt; e += kSpreadThreads) {
-            cp_async_elem<8>(&s_lam[spread_pad(e)], &g_lam[t0 + e]);
-            cp_async_elem<8>(&s_val[spread_pad(e)], &g_val[t0 + e]);
+        for (int e = tid; e < cnt; e += kBatchThreads) {
+            cp_async_elem<8>(&s_lam[batch_pad(e)], &g_lam[t0 + e]);
+            cp_async_elem<8>(&s_val[batch_pad(e)], &g_val[t0 + e]);
         }
         cp_async_wait_all();
         __syncthreads();
         // a short tile spreads its samples over every thread: runs of
         // ceil(cnt / threads) samples (at most kSpreadRun)
-        const int rl = min(kSpreadRun, (cnt + kSpreadThreads - 1) / kSpreadThreads);
+        const int rl = min(kSpreadRun, (cnt + kBatchThreads - 1) / kBatchThreads);
         const int i0 = t0 + run * rl;
         const int i1 = min(t0 + cnt, i0 + rl);
         if (i0 >= i1) continue;
-        const StagedSamples<float2> src{s_lam, s_val, t0};
+        const BatchStaged src{s_lam, s_val, t0};
         if (wa.mode == 0)
             spread_run<float2, W, 0>(s0, i0, i1, tag, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp,
                                      a.defer, s_row, user_D);
@@ -118,7 +136,7 @@ k_batch_spread(BatchSpreadArgs a) {
                                      a.defer, s_row, user_D);
     }
     __syncthreads();
-    for (int i = tid; i < len; i += kSpreadThreads) row.out[i] = s_row[i];
+    for (int i = tid; i < len; i += kBatchThreads) row.out[i] = s_row[i];
 }
 
 // Each block's pulse row of the spread launch, from the row tags and the
@@ -443,7 +461,7 @@ int occupancy_one() {
 bool batch_class_supported(int logn, int w) { return logn >= 9 && logn <= 11 && w >= 2 && w <= 8 && !(w & 1); }
 
 size_t batch_spread_smem(int max_len) {
-    return (size_t)kSpreadStageElems * (sizeof(double) + sizeof(float2)) + (size_t)max_len * sizeof(float2);
+    return (size_t)kBatchStageElems * (sizeof(double) + sizeof(float2)) + (size_t)max_len * sizeof(float2);
 }
 
 cudaError_t batch_set_attributes() {
@@ -480,19 +498,19 @@ void launch_batch_spread(int w, int rows, int max_len, cudaStream_t s, const Bat
     const bool deferred = a.wa.mode == 0;                  // FP64 decisions exist in tFFR mode only
     switch (w) {
         case 2:
-            k_batch_spread<2><<<rows, kSpreadThreads, smem, s>>>(a);
+            k_batch_spread<2><<<rows, kBatchThreads, smem, s>>>(a);
             if (deferred) k_batch_spread_deferred<2><<<152 * 2, 256, 0, s>>>(a);
             break;
         case 4:
-            k_batch_spread<4><<<rows, kSpreadThreads, smem, s>>>(a);
+            k_batch_spread<4><<<rows, kBatchThreads, smem, s>>>(a);
             if (deferred) k_batch_spread_deferred<4><<<152 * 2, 256, 0, s>>>(a);
             break;
         case 6:
-            k_batch_spread<6><<<rows, kSpreadThreads, smem, s>>>(a);
+            k_batch_spread<6><<<rows, kBatchThreads, smem, s>>>(a);
             if (deferred) k_batch_spread_deferred<6><<<152 * 2, 256, 0, s>>>(a);
             break;
         default:
-            k_batch_spread<8><<<rows, kSpreadThreads, smem, s>>>(a);
+            k_batch_spread<8><<<rows, kBatchThreads, smem, s>>>(a);
             if (deferred) k_batch_spread_deferred<8><<<152 * 2, 256, 0, s>>>(a);
             break;
     }
