@@ -468,7 +468,7 @@ def run_gpu(args, world, rank, local):
                    "per_plan_8_streams_ms": timings["per_plan_8_streams"],
                    "persistent_ms": timings["persistent"], "persistent_tuned_ms": timings["persistent_tuned"],
                    "graph_ms": timings["graph"],
-                   "launches_per_step": 2 + tuned["n_classes"],
+                   "launches_per_step": 1 + tuned["n_classes"],
                    "spread_ms": tuned["spread_ms"],
                    "autotuned": [{k: c[k] for k in ("side", "patches", "blocks", "ms")} for c in tuned["classes"]],
                    "value": whole_job_rate(batch.samples, world, timings["graph"]), "unit": UNIT}

@@ -6,7 +6,7 @@
 // path with the patches' rows as one grid: block b looks up its patch and
 // pulse row, stages the row's samples in shared memory and writes the row
 // buffer R_p; the samples whose weight needs the FP64 decision are added by
-// k_batch_spread_deferred.
+// the same block after its runs, before it stores the row.
 //
 // The persistent FFT launch of a class (k_batch_fft) loops over work items
 // claimed from one device counter:
@@ -92,6 +92,8 @@ k_batch_spread(BatchSpreadArgs a) {
     const int64_t s0 = row.s0;
     const bool periodic = (len == n) && (clo == 0);
     const WeightArgs& wa = a.wa;
+    __shared__ int s_ndef;
+    if (tid == 0) s_ndef = 0;
     for (int i = tid; i < len; i += kBatchThreads) s_row[i] = make_float2(0.f, 0.f);
     float dy = 1.0f;
     bool dy_exact = false, edges = true;
@@ -125,17 +127,26 @@ k_batch_spread(BatchSpreadArgs a) {
         const int i1 = min(t0 + cnt, i0 + rl);
         if (i0 >= i1) continue;
         const BatchStaged src{s_lam, s_val, t0};
+        const RowDefer rd{&s_ndef, a.defer_item};
         if (wa.mode == 0)
-            spread_run<float2, W, 0>(s0, i0, i1, tag, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp,
-                                     a.defer, s_row, user_D);
+            spread_run<float2, W, 0>(row.d0, i0, i1, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp, rd,
+                                     s_row, user_D);
         else if (wa.mode == 1)
-            spread_run<float2, W, 1>(s0, i0, i1, tag, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp,
-                                     a.defer, s_row, user_D);
+            spread_run<float2, W, 1>(s0, i0, i1, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp, rd,
+                                     s_row, user_D);
         else
-            spread_run<float2, W, 2>(s0, i0, i1, tag, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp,
-                                     a.defer, s_row, user_D);
+            spread_run<float2, W, 2>(s0, i0, i1, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp, rd,
+                                     s_row, user_D);
     }
     __syncthreads();
+    const int ndef = s_ndef;
+    if (ndef > 0) {
+        const BatchPatch* __restrict__ bp = a.patches + (tag >> 16);
+        const int p = tag & 0xffff;
+        spread_deferred_row<float2, W>(ndef, a.defer_item + row.d0, g_lam, g_val, bp->row_lam_y[p], M, M, n, clo,
+                                       periodic, wa, a.tp, s_row);
+        __syncthreads();
+    }
     for (int i = tid; i < len; i += kBatchThreads) row.out[i] = s_row[i];
 }
 
@@ -158,54 +169,8 @@ static __global__ void k_batch_rows(BatchSpreadArgs a, int rows) {
         row.tag = tag;
         row.M = bp->M;
         row.n = bp->n;
-        row.pad = 0;
+        row.d0 = bp->defer_off + (int)s0;
         a.rows[r] = row;
-    }
-}
-
-// The deferred samples of k_batch_spread: D_n decided in FP64, then added into
-// their row buffers with global atomics (after k_batch_spread stored them).
-template <int W>
-__global__ void __launch_bounds__(256)
-k_batch_spread_deferred(BatchSpreadArgs a) {
-    constexpr int H = W / 2;
-    __shared__ int s_count;
-    const DeferList& defer = a.defer;
-    if (threadIdx.x == 0) s_count = *(volatile int*)defer.count;
-    __syncthreads();
-    const int count = min(s_count, defer.cap);
-    // the last block to have read the count puts both counters back to zero
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&defer.count[1], 1) == (int)gridDim.x - 1) {
-            defer.count[0] = 0;
-            defer.count[1] = 0;
-        }
-    }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-        const int2 e = defer.item[i];
-        const int n = e.x, k = (e.y >> 16) & 0x7fff, p = e.y & 0xffff;
-        const BatchPatch* __restrict__ bp = a.patches + k;
-        const int M = bp->M, nx = bp->n;
-        const double lam = bp->lam_x[n];
-        int cell;
-        float f;
-        fine_coord(lam, cell, f);
-        const float d = (e.y & kDeferCoordOnly)
-                            ? weight_tffr(lam, cell, f, bp->row_lam_y[p], bp->row_ly[p], bp->row_fy[p], M, M, a.wa)
-                            : weight_exact(lam, bp->row_lam_y[p], M, M, a.wa);
-        if (d == 0.0f) continue;
-        const float2 v = cscale(bp->values[n], d);
-        float wt[W];
-        taps_all<W>(a.tp, f, wt);
-        const int len = bp->row_len[p], clo = bp->row_clo[p];
-        const bool periodic = (len == nx) && (clo == 0);
-        float2* out = bp->R + bp->row_off[p];
-#pragma unroll
-        for (int s = 0; s < W; ++s) {
-            const int c = cell - (H - 1) + s;
-            atomicAdd(&out[periodic ? wrapmod(c, nx) : (c - clo)], cscale(v, wt[s]));
-        }
     }
 }
 
@@ -495,24 +460,11 @@ int batch_max_blocks_per_sm(int logn) {
 
 void launch_batch_spread(int w, int rows, int max_len, cudaStream_t s, const BatchSpreadArgs& a) {
     const size_t smem = batch_spread_smem(max_len);
-    const bool deferred = a.wa.mode == 0;                  // FP64 decisions exist in tFFR mode only
     switch (w) {
-        case 2:
-            k_batch_spread<2><<<rows, kBatchThreads, smem, s>>>(a);
-            if (deferred) k_batch_spread_deferred<2><<<152 * 2, 256, 0, s>>>(a);
-            break;
-        case 4:
-            k_batch_spread<4><<<rows, kBatchThreads, smem, s>>>(a);
-            if (deferred) k_batch_spread_deferred<4><<<152 * 2, 256, 0, s>>>(a);
-            break;
-        case 6:
-            k_batch_spread<6><<<rows, kBatchThreads, smem, s>>>(a);
-            if (deferred) k_batch_spread_deferred<6><<<152 * 2, 256, 0, s>>>(a);
-            break;
-        default:
-            k_batch_spread<8><<<rows, kBatchThreads, smem, s>>>(a);
-            if (deferred) k_batch_spread_deferred<8><<<152 * 2, 256, 0, s>>>(a);
-            break;
+        case 2: k_batch_spread<2><<<rows, kBatchThreads, smem, s>>>(a); break;
+        case 4: k_batch_spread<4><<<rows, kBatchThreads, smem, s>>>(a); break;
+        case 6: k_batch_spread<6><<<rows, kBatchThreads, smem, s>>>(a); break;
+        default: k_batch_spread<8><<<rows, kBatchThreads, smem, s>>>(a); break;
     }
 }
 

@@ -22,6 +22,7 @@ namespace tffr {
 struct BatchPatch {
     int pulse;                          // 1: pulse-row order, 0: fine-row order
     int M, n, P, ldq, K;                // image side (square), fine grid side 2M, pulse rows, F stride, tap slots
+    int defer_off;                      // the patch's first slot in the batch's deferred-sample list
     const int* row_start;
     const int* row_end;
     const int* row_clo;
@@ -57,7 +58,7 @@ struct BatchRow {
     int clo, len;                       // first fine cell and cells of the row buffer
     int tag;                            // (patch << 16) | pulse row
     int M, n;                           // the patch's image side and fine-grid side
-    int pad;
+    int d0;                             // the row's region of the deferred-sample list (defer_off + s0)
 };
 
 // The spread launch over every pulse row of every patch.
@@ -68,7 +69,7 @@ struct BatchSpreadArgs {
     int npatch;
     WeightArgs wa;                      // the batch's weight evaluation (the patch's M decides the edges)
     TapPoly tp;
-    DeferList defer;                    // samples for the FP64 decision: (sample, patch << 16 | row)
+    int* defer_item;                    // [samples] per-row regions of the samples for the FP64 decision
 };
 
 // Every launch-wide argument of one class's persistent FFT kernel.

@@ -20,18 +20,14 @@ constexpr int kSpreadTile = kSpreadThreads * kSpreadRun;
 
 // Samples whose weight needs the FP64 decision (1/G within the guard band of
 // tau, a grid edge or a truncation breakpoint; rare) are not spread inline:
-// k_spread_rows lists them and k_spread_deferred adds them afterwards.  The
-// FP64 closed form then stays out of the hot kernel (and its registers).
-// Flag in a deferred item's row field: the sample lacks only the fast
-// coordinate split; its weight is the fitted one unless that needs the FP64
-// decision too.
-constexpr int kDeferCoordOnly = (int)0x80000000u;
-
-struct DeferList {
-    int* count;                     // [0] listed samples, [1] finished blocks of k_spread_deferred;
-                                    // both zero before the spread, and left zero by k_spread_deferred
-    int2* item;                     // [cap] (sample, pulse row | kDeferCoordOnly flag)
-    int cap;                        // N: every sample is listed at most once per adjoint
+// the runs list them in their pulse row's own region of the list (one slot
+// per sample of the row), and the block that spreads the row adds them after
+// its runs, before it stores the row (spread_deferred_row), with D_n from
+// the FP64 closed form.  The closed form then stays out of the runs (and their
+// registers), and no other launch or global atomic is needed.
+struct RowDefer {
+    int* count;                     // shared memory: samples of the row listed so far, zero before its runs
+    int* item;                      // the whole list; the row's region starts at the run's n0 in MODE 0
 };
 
 // One thread's run of up to kSpreadRun consecutive samples of a pulse row
@@ -45,14 +41,16 @@ struct DeferList {
 // needs the FP64 decision (near tau, off the fit's first piece or on a
 // truncation breakpoint, near a grid edge for rows not inside the grid's
 // interior, or with |2 lam| outside the fast coordinate split) is listed for
-// k_spread_deferred and adds nothing here.  The per-sample path has two
+// the block's deferred samples and adds nothing here.  The per-sample path has two
 // branches, both rarely taken: the listing and the window flush.
 // Sample i of the run comes from src.lam(i), src.val(i) (the caller's arrays
-// or a staged copy in shared memory); n0 + i is its index in the caller's order.
+// or a staged copy in shared memory).  n0: in MODE 2 the index of the row's
+// first sample in user_D; in MODE 0 the first slot of the row's region of the
+// deferred list (a row of L samples owns L slots).
 template <typename VT, int W, int MODE, typename Src>
-__device__ __forceinline__ void spread_run(int64_t n0, int i0, int i1, int p, int nx, int clo, int len, bool periodic,
+__device__ __forceinline__ void spread_run(int64_t n0, int i0, int i1, int nx, int clo, int len, bool periodic,
                                            int Mx, bool edges, float dy, bool dy_exact, const Src& src,
-                                           const WeightArgs& wa, const TapPoly& tp, const DeferList& defer,
+                                           const WeightArgs& wa, const TapPoly& tp, const RowDefer& defer,
                                            float2* s_row, const float* __restrict__ user_D) {
     constexpr int H = W / 2;
     constexpr int kNoBase = -(1 << 30);                // below every cell (|cell| < 2^29), no overflow
@@ -97,10 +95,8 @@ __device__ __forceinline__ void spread_run(int64_t n0, int i0, int i1, int p, in
             bool exact = dy_exact | ((unsigned)((cell >> 1) - e_lo) >= e_span);
             d = d_fixed0(cell, F, wa, exact) * dy;
             if (!fast | exact | !(fabsf(d - wa.tau) > tau_band)) {
-                // listed with bit 31 of the row field set when only the
-                // coordinate split is missing (the fitted weight then decides)
                 const int slot = atomicAdd(defer.count, 1);
-                if (slot < defer.cap) defer.item[slot] = make_int2((int)n, fast ? p : (p | kDeferCoordOnly));
+                defer.item[n0 + slot] = i;
                 d = 0.0f;
             }
             d = (d >= wa.tau) ? d : 0.0f;
@@ -141,6 +137,38 @@ __device__ __forceinline__ float2 to_f2(const double2& v) { return make_float2((
 __device__ __forceinline__ float2 to_f2(const __half2& v) { return __half22float2(v); }
 __device__ __forceinline__ float2 to_f2(const __nv_bfloat162& v) { return __bfloat1622float2(v); }
 
+// The row's listed samples, after every run of the block and before the row
+// is stored: D_n from the FP64 closed form (the definition the fitted weight
+// approximates), then added into the shared row.  item: the row's region of
+// the list (indices of samples within the row); lam_row, val_row: the row's
+// coordinates and values in global memory; lam_y: its azimuth coordinate
+// (separable weights).  Not inlined, and without the fitted-weight path: the
+// runs' registers stay those of the runs.
+template <typename VT, int W>
+__device__ __noinline__ void spread_deferred_row(int count, const int* __restrict__ item,
+                                                 const double* __restrict__ lam_row, const VT* __restrict__ val_row,
+                                                 double lam_y, int Mx, int My, int nx, int clo, bool periodic,
+                                                 const WeightArgs& wa, const TapPoly& tp, float2* s_row) {
+    constexpr int H = W / 2;
+    for (int k = threadIdx.x; k < count; k += blockDim.x) {
+        const int i = item[k];
+        const double lam = lam_row[i];
+        const float d = weight_exact(lam, lam_y, Mx, My, wa);
+        if (d == 0.0f) continue;
+        int cell;
+        float f;
+        fine_coord(lam, cell, f);
+        const float2 v = cscale(to_f2(val_row[i]), d);
+        float wt[W];
+        taps_all<W>(tp, f, wt);
+#pragma unroll
+        for (int s = 0; s < W; ++s) {
+            const int c = cell - (H - 1) + s;
+            atomic_add_f2_shared(&s_row[periodic ? wrapmod(c, nx) : (c - clo)], cscale(v, wt[s]));
+        }
+    }
+}
+
 // A tile of samples staged in shared memory, element i at i + i / kSpreadPadEvery
 // (the runs a warp's lanes read at once then fall on different banks).
 constexpr int kSpreadPadEvery = 8 * kSpreadRun;
@@ -165,7 +193,8 @@ struct StagedSamples {
 template <typename VT, int W>
 __global__ void __launch_bounds__(kSpreadThreads, 4)
 k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __restrict__ lam_x,
-              const void* __restrict__ values, WeightArgs wa, TapPoly tp, DeferList defer, float2* __restrict__ R) {
+              const void* __restrict__ values, WeightArgs wa, TapPoly tp, int* __restrict__ defer_item,
+              float2* __restrict__ R) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* s_lam = reinterpret_cast<double*>(smem_raw);
     VT* s_val = reinterpret_cast<VT*>(s_lam + kSpreadStageElems);
@@ -178,6 +207,8 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
     const int64_t s0 = rv.row_start[p];
     const int L = (int)(rv.row_end[p] - s0);
     const int tid = threadIdx.x;
+    __shared__ int s_ndef;
+    if (tid == 0) s_ndef = 0;
     for (int i = tid; i < len; i += kSpreadThreads) s_row[i] = make_float2(0.f, 0.f);
     // row-wide weight facts: the azimuth factor of the separable variant, and
     // whether every sample of the row is at least q + 1 image cells inside the
@@ -213,64 +244,26 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
         const int i1 = min(t0 + cnt, i0 + rl);
         if (i0 >= i1) continue;
         const StagedSamples<VT> src{s_lam, s_val, t0};
+        const RowDefer rd{&s_ndef, defer_item};
         if (wa.mode == 0)
-            spread_run<VT, W, 0>(s0, i0, i1, p, nx, clo, len, periodic, Mx, edges, dy, dy_exact, src, wa, tp, defer,
+            spread_run<VT, W, 0>(s0, i0, i1, nx, clo, len, periodic, Mx, edges, dy, dy_exact, src, wa, tp, rd,
                                  s_row, wa.user_D);
         else if (wa.mode == 1)
-            spread_run<VT, W, 1>(s0, i0, i1, p, nx, clo, len, periodic, Mx, edges, dy, dy_exact, src, wa, tp, defer,
+            spread_run<VT, W, 1>(s0, i0, i1, nx, clo, len, periodic, Mx, edges, dy, dy_exact, src, wa, tp, rd,
                                  s_row, wa.user_D);
         else
-            spread_run<VT, W, 2>(s0, i0, i1, p, nx, clo, len, periodic, Mx, edges, dy, dy_exact, src, wa, tp, defer,
+            spread_run<VT, W, 2>(s0, i0, i1, nx, clo, len, periodic, Mx, edges, dy, dy_exact, src, wa, tp, rd,
                                  s_row, wa.user_D);
     }
     __syncthreads();
+    const int ndef = s_ndef;
+    if (ndef > 0) {
+        spread_deferred_row<VT, W>(ndef, defer_item + s0, g_lam, g_val, rv.row_lam_y[p], Mx, My, nx, clo, periodic,
+                                   wa, tp, s_row);
+        __syncthreads();
+    }
     float2* out = R + rv.row_off[p];
     for (int i = tid; i < len; i += kSpreadThreads) out[i] = s_row[i];
-}
-
-// The deferred samples of k_spread_rows: D_n decided in FP64, then added into
-// their pulse-row buffers with global atomics (after k_spread_rows stored them).
-template <typename VT, int W>
-__global__ void __launch_bounds__(256)
-k_spread_deferred(RowsView rv, int nx, int Mx, int My, const double* __restrict__ lam_x,
-                  const void* __restrict__ values, WeightArgs wa, TapPoly tp, DeferList defer,
-                  float2* __restrict__ R) {
-    constexpr int H = W / 2;
-    __shared__ int s_count;
-    if (threadIdx.x == 0) s_count = *(volatile int*)defer.count;
-    __syncthreads();
-    const int count = min(s_count, defer.cap);
-    // the last block to have read the count puts both counters back to zero
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&defer.count[1], 1) == (int)gridDim.x - 1) {
-            defer.count[0] = 0;
-            defer.count[1] = 0;
-        }
-    }
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
-        const int2 e = defer.item[i];
-        const int n = e.x, p = e.y & ~kDeferCoordOnly;
-        const double lam = lam_x[n];
-        int cell;
-        float f;
-        fine_coord(lam, cell, f);
-        const float d = (e.y & kDeferCoordOnly)
-                            ? weight_tffr(lam, cell, f, rv.row_lam_y[p], rv.row_ly[p], rv.row_fy[p], Mx, My, wa)
-                            : weight_exact(lam, rv.row_lam_y[p], Mx, My, wa);
-        if (d == 0.0f) continue;
-        const float2 v = cscale(ValueIO<VT>::load(values, n), d);
-        float wt[W];
-        taps_all<W>(tp, f, wt);
-        const int len = rv.row_len[p], clo = rv.row_clo[p];
-        const bool periodic = (len == nx) && (clo == 0);
-        float2* out = R + rv.row_off[p];
-#pragma unroll
-        for (int s = 0; s < W; ++s) {
-            const int c = cell - (H - 1) + s;
-            atomicAdd(&out[periodic ? wrapmod(c, nx) : (c - clo)], cscale(v, wt[s]));
-        }
-    }
 }
 
 // Forward, last step: y_n = D_n sum_s phi(c_s - u_n) R_p[c_s] (or without D_n).

@@ -56,10 +56,9 @@ struct tffr_plan_s {
     DevBuf<float> deap_x, deap_y;
     DevBuf<int> d_small;                   // [0] error bits, [1] rows, [2] longest row, [3] row overflow,
                                            // [4] most pulse rows reaching one fine row,
-                                           // [5], [6] deferred FP64 weight decisions: listed samples and
-                                           // finished blocks (zero between adjoints),
                                            // [8..9] total row-buffer cells (int64)
-    DevBuf<int2> defer;                    // [N] deferred (sample, pulse row)
+    DevBuf<int> defer;                     // [N] samples for the FP64 weight decision: the region of each
+                                           // pulse row (its samples' slots) lists samples of the row
     int* h_small = nullptr;                // pinned read-back of d_small[0..9]
     cudaEvent_t readback = nullptr;        // recorded after that read-back
     DevBuf<unsigned long long> d_kept;
@@ -639,13 +638,9 @@ WeightArgs spread_weights(const tffr_plan_s* p, bool weighted) {
 template <typename VT, int W>
 void launch_spread(tffr_plan_s* p, const RowsView& rv, const void* values, bool weighted) {
     const size_t smem = (size_t)kSpreadStageElems * (sizeof(double) + sizeof(VT)) + (size_t)p->max_len * sizeof(float2);
-    const DeferList defer{p->d_small.ptr + 5, p->defer.ptr, (int)p->N};
     const WeightArgs wa = spread_weights(p, weighted);
     k_spread_rows<VT, W><<<p->P, kSpreadThreads, smem, p->stream>>>(rv, p->N, p->nx, p->Mx, p->My, p->lam_x, values,
-                                                                     wa, p->taps, defer, p->R.ptr);
-    if (wa.mode == TFFR_WEIGHTS_TFFR)
-        k_spread_deferred<VT, W><<<152 * 2, 256, 0, p->stream>>>(rv, p->nx, p->Mx, p->My, p->lam_x, values, wa,
-                                                                  p->taps, defer, p->R.ptr);
+                                                                     wa, p->taps, p->defer.ptr, p->R.ptr);
 }
 
 template <typename VT>
@@ -1501,8 +1496,7 @@ struct tffr_batch_s {
     WeightArgs wa;
     TapPoly tp;
     int* d_err = nullptr;                              // [0] error bits, [1] abort flag
-    int* d_defer_count = nullptr;                      // the spread's deferred samples: count, finished blocks
-    int2* d_defer = nullptr;                           // [samples]
+    int* d_defer = nullptr;                            // [samples]
     int n = 0;
     int64_t samples = 0;
     unsigned long long wait_ns = 1000000000ull;
@@ -1523,7 +1517,6 @@ void batch_free(tffr_batch_s* b) {
     if (b->d_patches) cudaFree(b->d_patches);
     if (b->d_row_tag) cudaFree(b->d_row_tag);
     if (b->d_rows) cudaFree(b->d_rows);
-    if (b->d_defer_count) cudaFree(b->d_defer_count);
     if (b->d_defer) cudaFree(b->d_defer);
     if (b->d_err) cudaFree(b->d_err);
     delete b;
@@ -1558,7 +1551,7 @@ cudaError_t launch_spread(const tffr_batch_s* b) {
     a.npatch = b->n;
     a.wa = b->wa;
     a.tp = b->tp;
-    a.defer = DeferList{b->d_defer_count, b->d_defer, (int)b->samples};
+    a.defer_item = b->d_defer;
     launch_batch_spread(b->w, b->rows_total, b->max_len, b->stream, a);
     return cudaGetLastError();
 }
@@ -1625,7 +1618,7 @@ int tffr_batch_create(const tffr_plan_t* plans, int n, const void* const* values
         // one kernel shape and one weight rule for the whole batch
         if (p->w != plans[0]->w || p->beta != plans[0]->beta || !same_weights(p->wargs, plans[0]->wargs))
             return TFFR_ERR_INVALID_ARG;
-        if (p->P >= (1 << 16) || i >= (1 << 15)) return TFFR_ERR_INVALID_ARG;   // the deferred list's encoding
+        if (p->P >= (1 << 16) || i >= (1 << 15)) return TFFR_ERR_INVALID_ARG;   // the row tags' encoding
     }
     tffr_batch_s* b = new (std::nothrow) tffr_batch_s();
     if (!b) return TFFR_ERR_OOM;
@@ -1648,6 +1641,7 @@ int tffr_batch_create(const tffr_plan_t* plans, int n, const void* const* values
     for (int i = 0; i < n; ++i) {
         const tffr_plan_s* p = plans[i];
         all[i] = patch_desc(p, values[i], images[i]);
+        all[i].defer_off = (int)std::min<int64_t>(b->samples, 0x7fffffff);   // larger batches are rejected below
         row_first[i + 1] = row_first[i] + p->P;
         b->samples += p->N;
         b->max_len = std::max(b->max_len, p->max_len);
@@ -1711,9 +1705,7 @@ int tffr_batch_create(const tffr_plan_t* plans, int n, const void* const* values
     }
     e = cudaMalloc((void**)&b->d_err, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_defer_count, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(b->d_defer_count, 0, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_defer, std::max<int64_t>(1, b->samples) * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_defer, std::max<int64_t>(1, b->samples) * sizeof(int));
     if (e != cudaSuccess) return bail(e);
     if (b->samples >= (int64_t)0x7fffffff) {
         batch_free(b);
