@@ -389,6 +389,7 @@ static __global__ void k_row_finish(const int* __restrict__ runs, int cap, int64
         row_max[p] = kIntMin;
         const int s0 = row_start[p];
         const int t = s0 / kRowScanTile;
+        const double ly = lam_y[s0];                   // issued with the tile's load below
         if (tile[t].y == p) {
             int t2 = t + 1;
             int e = (int)N;
@@ -412,7 +413,6 @@ static __global__ void k_row_finish(const int* __restrict__ runs, int cap, int64
             row_clo[p] = mn - (h - 1);
             row_len[p] = (int)span;
         }
-        const double ly = lam_y[s0];
         int cy;
         float fy;
         fine_coord(ly, cy, fy);
@@ -428,31 +428,44 @@ static __global__ void k_row_finish(const int* __restrict__ runs, int cap, int64
 }
 
 constexpr int kScanItems = 8;                          // consecutive items per thread in a block pass
+constexpr int kScanPass = kScanThreads * kScanItems;
+__host__ __device__ constexpr int scan_pad(int i) { return i + (i >> 5); }
+constexpr int kScanStage = scan_pad(kScanPass);        // ints of the shared staging of one pass
 
-// Exclusive scan of in[0..n) into out[0..n) by one block, kScanItems
-// consecutive items per thread and pass; out may be in (each thread reads its
-// items before writing them).  Starts from carry and returns the carry after
-// the last item (to every thread); folds the items into mx.  The sum of one
-// pass must fit an int.
+// Exclusive scan of in[0..n) into out[0..n) by one block, kScanPass items a
+// pass.  A pass stages its items in shared memory with coalesced loads; each
+// thread scans kScanItems consecutive items (one spare word per 32 keeps a
+// warp's reads on distinct banks); the pass-relative results go back through
+// shared memory and leave with coalesced stores.  out may be in (a pass reads
+// all its items before writing any).  Starts from carry and returns the carry
+// after the last item (to every thread); folds the items into mx.  The sum of
+// one pass must fit an int.
 template <typename OutT>
-__device__ long long block_scan_items(const int* in, OutT* out, int n, long long carry, int* s_warp, int& mx) {
-    for (int base = 0; base < n; base += kScanThreads * kScanItems) {
-        const int i0 = base + (int)threadIdx.x * kScanItems;
+__device__ long long block_scan_items(const int* in, OutT* out, int n, long long carry, int* s_warp, int* s_items,
+                                      int& mx) {
+    for (int base = 0; base < n; base += kScanPass) {
+        const int cnt = min(kScanPass, n - base);
+        __syncthreads();                               // the previous pass's stores have read s_items
+        for (int i = threadIdx.x; i < kScanPass; i += kScanThreads) s_items[scan_pad(i)] = (i < cnt) ? in[base + i] : 0;
+        __syncthreads();
+        const int i0 = (int)threadIdx.x * kScanItems;
         int x[kScanItems];
         int sum = 0;
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
-            x[k] = (i0 + k < n) ? in[i0 + k] : 0;
+            x[k] = s_items[scan_pad(i0 + k)];
             mx = max(mx, x[k]);
             sum += x[k];
         }
         int tot;
-        int ex = block_exclusive_scan(sum, s_warp, &tot);
+        int ex = block_exclusive_scan(sum, s_warp, &tot);   // ends with a barrier: every x[] is read
 #pragma unroll
         for (int k = 0; k < kScanItems; ++k) {
-            if (i0 + k < n) out[i0 + k] = (OutT)(carry + ex);
+            s_items[scan_pad(i0 + k)] = ex;
             ex += x[k];
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt; i += kScanThreads) out[base + i] = (OutT)(carry + s_items[scan_pad(i)]);
         carry += tot;
     }
     return carry;
@@ -471,17 +484,18 @@ k_row_scans(const int* __restrict__ runs, int cap, const int* __restrict__ row_l
             long long* __restrict__ total, int ny, int* tap_count, int* __restrict__ tap_start,
             int* __restrict__ max_len, int* __restrict__ max_count, int* ly_count) {
     __shared__ int s_warp[32];
+    __shared__ int s_items[kScanStage];
     int mx = 0;
     if (blockIdx.x == 0) {
         const int P = min(*runs, cap);
-        const long long cells = block_scan_items(row_len, row_off, P, 0, s_warp, mx);
+        const long long cells = block_scan_items(row_len, row_off, P, 0, s_warp, s_items, mx);
         if (threadIdx.x == 0) *total = cells;
     } else if (blockIdx.x == 1) {
-        const long long taps = block_scan_items(tap_count, tap_start, ny, 0, s_warp, mx);
+        const long long taps = block_scan_items(tap_count, tap_start, ny, 0, s_warp, s_items, mx);
         if (threadIdx.x == 0) tap_start[ny] = (int)taps;
         for (int i = threadIdx.x; i < ny; i += kScanThreads) tap_count[i] = 0;   // every read is behind a barrier
     } else {
-        block_scan_items(ly_count, ly_count, ny, 0, s_warp, mx);
+        block_scan_items(ly_count, ly_count, ny, 0, s_warp, s_items, mx);
         return;
     }
 #pragma unroll
