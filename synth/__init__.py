@@ -13,5 +13,6 @@ from .stripmap import (  # noqa: F401
     make_workload,
     random_points,
     patch_batch,
+    edge_rows,
     WORKLOADS,
 )

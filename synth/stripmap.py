@@ -218,3 +218,16 @@ def patch_batch(n_patches: int = 64, seed: int = 191010908 + 5, sides=(256, 512,
         v = ((g.standard_normal(lx.shape[0]) + 1j * g.standard_normal(lx.shape[0])) / np.sqrt(2.0)).astype(np.complex64)
         out.append((M, lx, ly, v))
     return out
+
+
+def edge_rows(M: int, rows: int, per: int, seed: int):
+    """Pulse rows whose samples all lie within 4 image cells of the left or right edge of an
+    M-point grid (rows alternate sides; lam_x sorted along a row), with white complex64 samples:
+    the truncated sum G of every sample differs from its interior form there."""
+    g = np.random.default_rng(seed)
+    lam_y = np.linspace(-M / 2 + 7.3, M / 2 - 8.3, rows)
+    lx = np.concatenate([np.sort(g.uniform(0.0, 3.99, per)) + (-M / 2 if r % 2 == 0 else M / 2 - 4.0)
+                         for r in range(rows)])
+    ly = np.repeat(lam_y, per)
+    v = (g.standard_normal(lx.shape[0]) + 1j * g.standard_normal(lx.shape[0])).astype(np.complex64)
+    return lx, ly, v

@@ -9,7 +9,7 @@ import pytest
 import torch
 
 import oracle
-from synth import patch_batch
+from synth import edge_rows, patch_batch
 
 pytestmark = pytest.mark.gpu
 
@@ -101,6 +101,35 @@ def test_persistent_batch_matches_per_plan_path_and_oracle(width):
         jy = np.concatenate([g.integers(0, M, 56), bright // M])
         ref = oracle.adjoint_pixels(lx, ly, v, oracle.tffr_weights(lx, M), M, M, jx, jy)
         assert np.linalg.norm(got[jy, jx] - ref) / np.linalg.norm(ref) <= tol
+
+
+def test_batch_spread_rows_whose_every_sample_takes_the_fp64_decision():
+    """Patches whose pulse rows lie within q + 1 cells of the grid's edges: the batch spread lists
+    every sample of every row for the FP64 decision in that row's region of the batch's list and
+    decides them in the row's block; the images equal the per-plan images and the oracle's."""
+    from paper_1910_10908_gb300.batched import PatchBatch
+    M = 256
+    pts = [edge_rows(M, 30 + 10 * k, 100 + 20 * k, seed=40 + k) for k in range(3)]
+    dev = torch.device("cuda", 0)
+    patches = [(M, M, torch.from_numpy(lx).to(dev), torch.from_numpy(ly).to(dev)) for lx, ly, _ in pts]
+    with PatchBatch(patches, width=8, streams=2) as batch:
+        for k, (_, _, v) in enumerate(pts):
+            batch.load(k, torch.from_numpy(v).to(dev))
+        batch.adjoint_eager()
+        batch.stream.synchronize()
+        per_plan = [img.clone() for img in batch.images]
+        with torch.cuda.stream(batch.stream):
+            for img in batch.images:
+                img.fill_(float("nan"))
+        batch.adjoint()
+        batch.wait()
+        persistent = [img.clone() for img in batch.images]
+    for a, b in zip(persistent, per_plan):
+        assert rel(a, b) <= 1e-6
+    for (lx, ly, v), img in zip(pts, persistent):
+        ref = oracle.adjoint_image(lx, ly, v, oracle.tffr_weights(lx, M), M, M)
+        got = img.cpu().numpy().astype(np.complex128)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
 
 
 def test_persistent_batch_wait_runs_out_and_the_gpu_recovers():

@@ -14,7 +14,7 @@ import pytest
 import torch
 
 import oracle
-from synth import make_workload, random_points, scene_samples, stolt_points
+from synth import edge_rows, make_workload, random_points, scene_samples, stolt_points
 
 pytestmark = pytest.mark.gpu
 
@@ -140,6 +140,20 @@ def test_pulse_rows_through_zero_and_at_special_magnitudes():
             assert d_err(D, Dref) < 3e-7
             ref = oracle.adjoint_image(lx, ly, v, Dref, M, M)
             assert rel_l2(img, ref) <= TOL
+
+
+def test_rows_whose_every_sample_takes_the_fp64_decision():
+    """Every sample of every pulse row is listed for the FP64 decision, so each row's region of the
+    list fills to its capacity (one slot per sample): the image and the weights against the oracle."""
+    M = 256
+    lx, ly, v = edge_rows(M, 40, 120, seed=31)
+    img, D, kept, info = gpu_adjoint(lx, ly, v, M, width=8, layout="rows")
+    assert info["layout"] == 2 and info["n_rows"] == 40
+    Dref = oracle.tffr_weights(lx, M)
+    assert kept == np.count_nonzero(Dref)
+    assert d_err(D, Dref) < 3e-7
+    ref = oracle.adjoint_image(lx, ly, v, Dref, M, M)
+    assert rel_l2(img, ref) <= TOL
 
 
 def test_rows_layout_forced_on_short_rows():
