@@ -384,7 +384,9 @@ def run_gpu(args, world, rank, local):
     # Every step copies its inputs in from pinned host memory and its image out
     # to pinned host memory.  Two plans on two streams take the steps in turn,
     # so that one step's copies overlap the other plan's kernels (set_points
-    # waits for its own stream only); the events bracket both streams.
+    # waits for its own stream only), and the next step's input copies are
+    # enqueued before this step's call, which waits on the host for its scan's
+    # read-back; the events bracket both streams.
     h_lx = torch.from_numpy(wl.lam_x).pin_memory()
     h_ly = torch.from_numpy(wl.lam_y).pin_memory()
     h_v = torch.from_numpy(wl.values).pin_memory()
@@ -396,15 +398,17 @@ def run_gpu(args, world, rank, local):
     d_img = [img, torch.empty_like(img)]
     h_img = [torch.empty((M, M), dtype=torch.complex64).pin_memory() for _ in range(2)]
 
-    def e2e_step(k):
-        s, pl = streams[k], plans[k]
+    def e2e_copy_in(k):
         d_lx, d_ly, d_v = d_in[k]
-        with torch.cuda.stream(s):
+        with torch.cuda.stream(streams[k]):
             d_lx.copy_(h_lx, non_blocking=True)
             d_ly.copy_(h_ly, non_blocking=True)
             d_v.copy_(h_v, non_blocking=True)
-        pl.reconstruct(d_lx, d_ly, d_v, out=d_img[k])
-        with torch.cuda.stream(s):
+
+    def e2e_call_and_copy_out(k):
+        d_lx, d_ly, d_v = d_in[k]
+        plans[k].reconstruct(d_lx, d_ly, d_v, out=d_img[k])
+        with torch.cuda.stream(streams[k]):
             h_img[k].copy_(d_img[k], non_blocking=True)
 
     def e2e_run(k):
@@ -413,8 +417,11 @@ def run_gpu(args, world, rank, local):
         joined = torch.cuda.Event()
         ev_a.record(streams[0])
         streams[1].wait_event(ev_a)
+        e2e_copy_in(0)
         for i in range(k):
-            e2e_step(i % 2)
+            if i + 1 < k:
+                e2e_copy_in((i + 1) % 2)               # behind step i - 1 on its stream
+            e2e_call_and_copy_out(i % 2)
         joined.record(streams[1])
         streams[0].wait_event(joined)
         ev_b.record(streams[0])
@@ -427,6 +434,32 @@ def run_gpu(args, world, rank, local):
     e2e_ms = max_over_ranks(e2e_run(e2e_iters) / e2e_iters, world)
     h2d = int(h_lx.numel() * 8 + h_ly.numel() * 8 + h_v.numel() * 8)
     d2h = int(h_img[0].numel() * 8)
+
+    # the same copies alone (no kernels), inputs in on one stream while the
+    # previous step's image goes out on the other: the host link's floor for
+    # the end-to-end step
+    def copies_run(k):
+        ev_a, ev_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        joined = torch.cuda.Event()
+        ev_a.record(streams[0])
+        streams[1].wait_event(ev_a)
+        for i in range(k):
+            d_lx, d_ly, d_v = d_in[i % 2]
+            with torch.cuda.stream(streams[0]):
+                d_lx.copy_(h_lx, non_blocking=True)
+                d_ly.copy_(h_ly, non_blocking=True)
+                d_v.copy_(h_v, non_blocking=True)
+            with torch.cuda.stream(streams[1]):
+                h_img[i % 2].copy_(d_img[i % 2], non_blocking=True)
+        joined.record(streams[1])
+        streams[0].wait_event(joined)
+        ev_b.record(streams[0])
+        torch.cuda.synchronize()
+        return ev_a.elapsed_time(ev_b)
+
+    copies_run(4)
+    floor_iters = max(8, int(1e3 * SECTION_S / max(copies_run(8) / 8, 1e-3)))
+    copy_floor_ms = max_over_ranks(copies_run(floor_iters) / floor_iters, world)
     plan_b.close()
     del h_lx, h_ly, h_v, h_img, d_in
 
@@ -582,8 +615,11 @@ def run_gpu(args, world, rank, local):
             "fft_comparison": fft_compare,
             "e2e": {"value": whole_job_rate(N, world, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                     "steps": e2e_iters,
-                    "overlap": "two plans on two streams: one step's copies overlap the other's kernels",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "overlap": "two plans on two streams: one step's copies overlap the other's kernels; the next "
+                               "step's inputs are enqueued before this step's call",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "copy_floor_ms": copy_floor_ms, "of_copy_floor": copy_floor_ms / e2e_ms,
+                    "copy_floor": "the same copies with no kernels, in and out on two streams at once"},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
