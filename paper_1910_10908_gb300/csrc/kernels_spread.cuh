@@ -266,15 +266,49 @@ k_spread_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
     for (int i = tid; i < len; i += kSpreadThreads) out[i] = s_row[i];
 }
 
+// The interpolation's listed samples (after the block's loop): y_n from the
+// exact fine cell, its taps and D_n by the FP64 closed form.  Not inlined: the
+// loop's registers stay those of the loop.
+template <typename VT, int W>
+__device__ __noinline__ void interp_listed_row(int count, const int* __restrict__ item,
+                                               const double* __restrict__ lam_row, const float2* __restrict__ Rp,
+                                               int nx, int clo, bool periodic, double lam_y, int Mx, int My,
+                                               const WeightArgs& wa, const TapPoly& tp, void* __restrict__ out,
+                                               int64_t s0) {
+    constexpr int H = W / 2;
+    for (int k = threadIdx.x; k < count; k += blockDim.x) {
+        const int i = item[k];
+        const double lam = lam_row[i];
+        int cell;
+        float f;
+        fine_coord(lam, cell, f);
+        float wt[W];
+        taps_all<W>(tp, f, wt);
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int s = 0; s < W; ++s) {
+            const int c = cell - (H - 1) + s;
+            const float2 r = Rp[periodic ? wrapmod(c, nx) : (c - clo)];
+            acc.x = fmaf(wt[s], r.x, acc.x);
+            acc.y = fmaf(wt[s], r.y, acc.y);
+        }
+        ValueIO<VT>::store(out, s0 + i, cscale(acc, weight_exact(lam, lam_y, Mx, My, wa)));
+    }
+}
+
 // Forward, last step: y_n = D_n sum_s phi(c_s - u_n) R_p[c_s] (or without D_n).
 // GRAD: the gradient of a real loss with respect to real weights D instead,
 // grad[n] = Re(conj(a_n) y_n) with a_n the unweighted sum and y_n read from y_in
-// (in the value type VT).
+// (in the value type VT).  The sample's fine cell and offset come from the
+// branch-free fixed-point split; in tFFR mode D_n is the direct fit of 1/G
+// (times the row's azimuth factor), and a sample that needs the FP64 decision
+// (or lacks the fast split) is listed in its row's region of defer_item and
+// recomputed after the loop (interp_listed_row), as in the spread.
 template <typename VT, int W, bool GRAD = false>
 __global__ void __launch_bounds__(kSpreadThreads, 4)
 k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __restrict__ lam_x,
-              const float2* __restrict__ R, WeightArgs wa, TapPoly tp, int apply_weights, void* __restrict__ out,
-              const void* __restrict__ y_in = nullptr) {
+              const float2* __restrict__ R, WeightArgs wa, TapPoly tp, int apply_weights,
+              int* __restrict__ defer_item, void* __restrict__ out, const void* __restrict__ y_in = nullptr) {
     constexpr int H = W / 2;
     const int p = blockIdx.x;
     const int len = rv.row_len[p];
@@ -283,17 +317,50 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
     const int64_t s0 = rv.row_start[p];
     const int64_t s1 = rv.row_end[p];
     const float2* Rp = R + rv.row_off[p];
-    float gy = 1.0f;
-    bool gy_exact = false;
-    const double lam_y_row = rv.row_lam_y[p];
-    if (apply_weights && wa.mode == 0 && wa.separable) gy = g_fitted(rv.row_ly[p], rv.row_fy[p], My, wa, gy_exact);
-    // y_n for one sample of this row
-    auto interp = [&](int64_t n, double lam) -> float2 {
+    __shared__ int s_ndef;
+    if (threadIdx.x == 0) s_ndef = 0;
+    __syncthreads();
+    const bool fit = !GRAD && apply_weights && wa.mode == 0;
+    // row-wide facts of the fitted weight: the azimuth factor (separable
+    // variant) and the grid-edge test as one unsigned compare (rows inside
+    // the grid's interior: never)
+    float dy = 1.0f;
+    bool dy_exact = false;
+    int e_lo = -(1 << 30);
+    unsigned e_span = 1u << 31;
+    if (fit) {
+        if (wa.separable) {
+            const float gy = g_fitted(rv.row_ly[p], rv.row_fy[p], My, wa, dy_exact);
+            dy = (gy != 0.0f) ? __frcp_rn(gy) : 0.0f;
+        }
+        const int mn = clo + (H - 1), mx = clo + len - H - 1;
+        if (periodic || (mn >> 1) - wa.reach < -(Mx / 2) || (mx >> 1) + wa.reach >= Mx - Mx / 2) {
+            e_lo = wa.reach - Mx / 2;
+            e_span = (unsigned)max(0, (Mx - Mx / 2 - wa.reach) - e_lo);
+        }
+    }
+    const float tau_band = wa.guard * fabsf(wa.tau);
+    const int safe = clo + (H - 1);                    // a cell whose taps lie in the row
+    // y for sample n; listed: the sample is recomputed after the loop
+    auto interp = [&](int64_t n, double lam, bool& listed) -> float2 {
         int cell;
-        float f;
-        fine_coord(lam, cell, f);
+        unsigned F;
+        const bool fast = fixed_coord_fast(lam, cell, F);
+        float d = 1.0f;
+        listed = false;
+        if (fit) {
+            cell = fast ? cell : safe;
+            bool exact = dy_exact | ((unsigned)((cell >> 1) - e_lo) >= e_span);
+            d = d_fixed0(cell, F, wa, exact) * dy;
+            listed = !fast | exact | !(fabsf(d - wa.tau) > tau_band);
+            d = (d >= wa.tau) ? d : 0.0f;
+        } else {
+            if (!fast) fixed_coord_general(lam, cell, F);
+            if (!GRAD && apply_weights && wa.mode == 2) d = wa.user_D[n];
+        }
+        const float t = fmaf(__uint2float_rn(F), 0x1p-31f, -1.0f);   // 2 f - 1
         float wt[W];
-        taps_all<W>(tp, f, wt);
+        taps_all_t<W>(tp, t, wt);
         const int c0 = cell - (H - 1);
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -303,21 +370,11 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
             acc.x = fmaf(wt[s], r.x, acc.x);
             acc.y = fmaf(wt[s], r.y, acc.y);
         }
-        float d = 1.0f;
-        if (!GRAD && apply_weights) {
-            if (wa.mode == 2) {
-                d = wa.user_D[n];
-            } else if (wa.mode == 0) {
-                bool exact = gy_exact;
-                float G = g_fitted(cell, f, Mx, wa, exact) * gy;
-                d = (G != 0.0f) ? __frcp_rn(G) : 0.0f;
-                if (exact || !(fabsf(d - wa.tau) > wa.guard * fabsf(wa.tau)))
-                    d = weight_exact(lam, lam_y_row, Mx, My, wa);
-                else if (d < wa.tau)
-                    d = 0.0f;
-            }
-        }
         return cscale(acc, d);
+    };
+    auto list = [&](int64_t n) {
+        const int slot = atomicAdd(&s_ndef, 1);
+        defer_item[s0 + slot] = (int)(n - s0);
     };
     // two samples per thread and iteration (two independent chains of loads);
     // the next iteration's coordinates are loaded before this iteration's work
@@ -331,8 +388,9 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
         const int64_t m = n + 2 * step;
         const double next0 = (m < s1) ? lam_x[m] : 0.0;
         const double next1 = (m + step < s1) ? lam_x[m + step] : 0.0;
-        const float2 y0 = interp(n, lam0);
-        const float2 y1 = interp(two ? n1 : n, two ? lam1 : lam0);
+        bool l0, l1;
+        const float2 y0 = interp(n, lam0, l0);
+        const float2 y1 = interp(two ? n1 : n, two ? lam1 : lam0, l1);
         if constexpr (GRAD) {
             float* g = reinterpret_cast<float*>(out);
             const float2 v0 = ValueIO<VT>::load(y_in, n);
@@ -344,9 +402,18 @@ k_interp_rows(RowsView rv, int64_t N, int nx, int Mx, int My, const double* __re
         } else {
             ValueIO<VT>::store(out, n, y0);
             if (two) ValueIO<VT>::store(out, n1, y1);
+            if (l0) list(n);
+            if (two && l1) list(n1);
         }
         lam0 = next0;
         lam1 = next1;
+    }
+    if (fit) {
+        __syncthreads();                               // every listing and first store is done
+        const int nd = s_ndef;
+        if (nd > 0)
+            interp_listed_row<VT, W>(nd, defer_item + s0, lam_x + s0, Rp, nx, clo, periodic, rv.row_lam_y[p], Mx,
+                                     My, wa, tp, out, s0);
     }
 }
 

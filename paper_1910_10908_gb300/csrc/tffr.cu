@@ -694,11 +694,11 @@ template <typename VT, int W>
 void launch_interp(tffr_plan_s* p, const RowsView& rv, void* values, int apply_weights, const void* y_in) {
     if (y_in)
         k_interp_rows<VT, W, true><<<p->P, kSpreadThreads, 0, p->stream>>>(
-            rv, p->N, p->nx, p->Mx, p->My, p->lam_x, p->R.ptr, p->wargs, p->taps, 0, values, y_in);
+            rv, p->N, p->nx, p->Mx, p->My, p->lam_x, p->R.ptr, p->wargs, p->taps, 0, p->defer.ptr, values, y_in);
     else
         k_interp_rows<VT, W><<<p->P, kSpreadThreads, 0, p->stream>>>(rv, p->N, p->nx, p->Mx, p->My, p->lam_x,
                                                                       p->R.ptr, p->wargs, p->taps, apply_weights,
-                                                                      values);
+                                                                      p->defer.ptr, values);
 }
 
 // values = (D) E image; with y_in, values (float[N]) = Re(conj(E image) y) instead:
