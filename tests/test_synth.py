@@ -38,3 +38,20 @@ def test_workload_is_deterministic():
     b = make_workload("tiny_64")
     assert np.array_equal(a.values, b.values) and a.values.dtype == np.complex128
     assert a.N == 4096
+
+
+def test_edge_rows_lie_in_the_edge_band():
+    """Every sample of edge_rows is within 4 image cells of the left or right grid edge, rows
+    alternate sides, and each row shares one lam_y (bit-equal) with lam_x sorted along it."""
+    import numpy as np
+    from synth import edge_rows
+    M, rows, per = 256, 10, 50
+    lx, ly, v = edge_rows(M, rows, per, seed=3)
+    assert lx.shape == ly.shape == v.shape == (rows * per,)
+    j0 = np.floor(lx)
+    assert np.all((j0 - 4 < -(M // 2)) | (j0 + 4 >= M - M // 2))
+    assert np.all((lx >= -M / 2) & (lx < M / 2))
+    for r in range(rows):
+        x, y = lx[r * per:(r + 1) * per], ly[r * per:(r + 1) * per]
+        assert np.all(y == y[0]) and np.all(np.diff(x) >= 0)
+        assert (x[0] < 0) == (r % 2 == 0)
