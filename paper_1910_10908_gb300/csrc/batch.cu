@@ -128,6 +128,8 @@ k_batch_spread(BatchSpreadArgs a) {
         if (i0 >= i1) continue;
         const BatchStaged src{s_lam, s_val, t0};
         const RowDefer rd{&s_ndef, a.defer_item};
+        // n0: the row's first slot in the batch's list (tFFR weights), or its
+        // first sample in the patch's user_D (user weights)
         if (wa.mode == 0)
             spread_run<float2, W, 0>(row.d0, i0, i1, n, clo, len, periodic, M, edges, dy, dy_exact, src, wa, a.tp, rd,
                                      s_row, user_D);
